@@ -1,0 +1,548 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: the moment
+constraints of Eq. 10 and the closed-form moments of Eq. 16, the exact discrete
+anti-bounce-back solution of Eq. 71-72 (Sec. 3.6), closed-form solutions of the
+continuous problems (Eq. 45, Eq. 60, Eq. 68) with second-order convergence, an
+exact spectral solution of the linear periodic scheme, brute force by an
+independent numpy implementation on tiny grids, exact invariants, and the
+adjoint's dot-product and finite-difference identities.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+# Eq. 15
+M0 = np.array([
+    [1, 1, 1, 1, 1, 1, 1, 1, 1],
+    [-4, -1, -1, -1, -1, 2, 2, 2, 2],
+    [4, -2, -2, -2, -2, 1, 1, 1, 1],
+    [0, 1, 0, -1, 0, 1, -1, -1, 1],
+    [0, -2, 0, 2, 0, 1, -1, -1, 1],
+    [0, 0, 1, 0, -1, 1, 1, -1, -1],
+    [0, 0, -2, 0, 2, 1, 1, -1, -1],
+    [0, 1, -1, 1, -1, 0, 0, 0, 0],
+    [0, 0, 0, 0, 0, 1, -1, 1, -1]], dtype=np.float64)
+CS2 = 1.0 / 3.0
+
+
+def spec_of(name, **over):
+    p = W.params(name)
+    p.update(over)
+    return O.Spec(nx=p["nx"], ny=p["ny"], bc_x=p["bc"][0], bc_y=p["bc"][1],
+                  phi_wall=p["phi_wall"], conv=p["conv"], u=p["u"], diff=p["diff"],
+                  K=p["K"], s=W.s9(), r0=p["r0"], r1=p["r1"])
+
+
+def flux_def(conv, u, phi):
+    """B(phi) of the problem statement (Eq. 1 families)."""
+    u = np.asarray(u, dtype=np.float64)
+    return u * phi if conv == 0 else u * phi ** 2 / 2
+
+
+def C_def(conv, u, phi):
+    """C with C' = B' B'^T (Eq. 7), integrated by hand for each family."""
+    u = np.asarray(u, dtype=np.float64)
+    uu = np.outer(u, u)
+    return uu * phi if conv == 0 else uu * phi ** 3 / 3
+
+
+def g_def(diff, phi):
+    return [phi, phi + phi ** 2 / 2, phi + phi ** 3 / 3][diff]
+
+
+FAMILIES = [(c, d) for c in (0, 1) for d in (0, 1, 2)]
+
+
+# ---------------------------------------------------------------- Eq. 10 / 16
+
+@pytest.mark.parametrize("conv,diff", FAMILIES)
+def test_equilibrium_moment_constraints_eq10(conv, diff):
+    rng = np.random.default_rng(10 + 3 * conv + diff)
+    u = rng.uniform(-0.3, 0.3, 2)
+    sp = O.Spec(nx=1, ny=1, conv=conv, u=tuple(u), diff=diff, K=(0.01, 0.0, 0.01))
+    for phi in rng.uniform(-1.5, 1.5, 6):
+        f = O.feq(sp, phi)
+        assert abs(f.sum() - phi) <= 1e-14 * max(1, abs(phi))
+        B = flux_def(conv, u, phi)
+        assert np.allclose([(CX * f).sum(), (CY * f).sum()], B, rtol=0, atol=1e-14)
+        Cbar = C_def(conv, u, phi) + CS2 * g_def(diff, phi) * np.eye(2)   # d = 1
+        second = np.array([[(CX * CX * f).sum(), (CX * CY * f).sum()],
+                           [(CY * CX * f).sum(), (CY * CY * f).sum()]])
+        assert np.allclose(second, Cbar, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("conv,diff", FAMILIES)
+def test_equilibrium_moments_match_eq16(conv, diff):
+    rng = np.random.default_rng(20 + 3 * conv + diff)
+    u = rng.uniform(-0.3, 0.3, 2)
+    sp = O.Spec(nx=1, ny=1, conv=conv, u=tuple(u), diff=diff)
+    for phi in rng.uniform(-1.5, 1.5, 5):
+        m = M0 @ O.feq(sp, phi)
+        Bx, By = flux_def(conv, u, phi)
+        Cb = C_def(conv, u, phi) + CS2 * g_def(diff, phi) * np.eye(2)
+        C2 = Cb[0, 0] + Cb[1, 1]
+        c = 1.0
+        eq16 = [phi, -4 * phi * c ** 2 + 3 * C2, 3 * phi * c ** 4 - 3 * C2 * c ** 2, Bx,
+                -Bx * c ** 2, By, -By * c ** 2, Cb[0, 0] - Cb[1, 1], Cb[0, 1]]
+        assert np.allclose(m, eq16, rtol=0, atol=2e-14)
+
+
+@pytest.mark.parametrize("conv", [0, 1])
+def test_source_moments_eq10(conv):
+    rng = np.random.default_rng(30 + conv)
+    u = rng.uniform(-0.3, 0.3, 2)
+    sp = O.Spec(nx=1, ny=1, conv=conv, u=tuple(u))
+    for phi, R in rng.uniform(-1, 1, (5, 2)):
+        Rk = O.source_pop(sp, phi, R)
+        Bp = u if conv == 0 else u * phi          # Btilde = B' in Scheme B (Eq. 28)
+        assert abs(Rk.sum() - R) < 1e-15
+        assert np.allclose([(CX * Rk).sum(), (CY * Rk).sum()], Bp * R, rtol=0, atol=1e-15)
+
+
+def test_relaxation_block_eq26_and_eq30():
+    rng = np.random.default_rng(40)
+    for _ in range(10):
+        a, b = rng.uniform(0.001, 0.2, 2)
+        c = rng.uniform(-0.9, 0.9) * math.sqrt(a * b)
+        K = np.array([[a, c], [c, b]])
+        A = O.relax_block([a, c, b])
+        # Eq. 26 with d = 1, dt = 1
+        assert np.allclose(CS2 * (np.linalg.inv(A) - 0.5 * np.eye(2)), K, rtol=1e-13, atol=1e-16)
+    # diagonal K: Eq. 30b
+    A = O.relax_block([0.02, 0.0, 0.05])
+    assert A[0, 1] == 0.0 and A[1, 0] == 0.0
+    assert abs(CS2 * (1 / A[0, 0] - 0.5) - 0.02) < 1e-15
+    assert abs(CS2 * (1 / A[1, 1] - 0.5) - 0.05) < 1e-15
+    with pytest.raises(ValueError):
+        O.relax_block([0.01, 0.5, 0.01])   # not SPD
+
+
+# ------------------------------------------------ exact discrete slip, Eq. 72
+
+def slip_case(N, s1, s3, ux=0.0, bgk=False):
+    """Steady unidirectional problem of Sec. 3.6 in lattice units, walls at
+    y = 0 (phi0 = 0) and y = N (phi_L = 1), source R = 2 kappa dphi / N^2."""
+    kap = CS2 * (1.0 / s3 - 0.5)
+    if bgk:   # the single-rate loop needs S = s I bit for bit
+        s1 = s3 = O.relax_block([kap, 0.0, kap])[0, 0]
+    R = 2 * kap * 1.0 / N ** 2
+    s = (s1, s1, s1, s3, s1, s3, s1, s1, s1)
+    sp = O.Spec(nx=1, ny=N, bc_x=0, bc_y=1, phi_wall=(0, 0, 0.0, 1.0), conv=0, u=(ux, 0.0),
+                K=(kap, 0.0, kap), s=s, r0=R, collision=2 if bgk else 0)
+    F = O.init(sp, np.zeros((N, 1)))
+    nsteps = int(60 * N * N / kap) + 200
+    phi = None
+    for n in range(nsteps):
+        F, phi = O.step(sp, F, n)
+    return phi[:, 0]
+
+
+@pytest.mark.parametrize("N,s1,s3,ux", [(4, 1.0, 0.6, 0.0), (6, 0.8, 0.3, 0.0),
+                                         (8, 1.2, 1.5, 0.0), (8, 1.2, 1.5, 0.05), (5, 1.7, 1.0, 0.1)])
+def test_mrt_slip_exact_eq72b(N, s1, s3, ux):
+    phi = slip_case(N, s1, s3, ux)
+    yb = (np.arange(N) + 0.5) / N                # Eq. 71 node positions (0-based)
+    slip = 1.0 / (12 * N ** 2 * s1 * s3) * (s1 * s3 - 8 * (s1 + s3) + 16)
+    exact = yb * (2 - yb) + slip                 # Eq. 71 with the sign of Eq. 70
+    assert np.abs(phi - exact).max() < 1e-12
+
+
+@pytest.mark.parametrize("N,s", [(4, 0.7), (8, 1.3), (6, 1.9)])
+def test_bgk_slip_exact_eq72a(N, s):
+    phi = slip_case(N, s, s, bgk=True)
+    yb = (np.arange(N) + 0.5) / N
+    slip = 1.0 / (12 * N ** 2) * (4 * (2 / s - 1) ** 2 - 3)
+    assert np.abs(phi - (yb * (2 - yb) + slip)).max() < 1e-12
+
+
+@pytest.mark.parametrize("N,s3", [(4, 0.6), (8, 1.5)])
+def test_zero_slip_condition(N, s3):
+    # Eq. 72b vanishes for s1 = 8 (2 - s3) / (8 - s3) (Eq. 73 with its sign restored)
+    s1 = 8 * (2 - s3) / (8 - s3)
+    phi = slip_case(N, s1, s3)
+    yb = (np.arange(N) + 0.5) / N
+    assert np.abs(phi - yb * (2 - yb)).max() < 1e-12
+    # and BGK at s = 4 (2 - sqrt 3) has zero slip too
+    s = 4 * (2 - math.sqrt(3))
+    phi = slip_case(N, s, s, bgk=True)
+    assert np.abs(phi - yb * (2 - yb)).max() < 1e-12
+
+
+# ---------------------------------------------- exact spectral solution (C1)
+
+def spectral_linear_periodic(phi0, u, K, s9, nsteps):
+    """Exact solution of the linear periodic scheme: per Fourier mode the step is
+    F <- L D(k) F with D = diag(exp(-i k.c_j)) (pull) and L = I - P (I - a 1^T)."""
+    ny, nx = phi0.shape
+    A = np.linalg.inv(np.array([[K[0], K[1]], [K[1], K[2]]]) / CS2 + 0.5 * np.eye(2))
+    S = np.diag(np.array(s9, dtype=np.float64))
+    S[3, 3], S[3, 5], S[5, 3], S[5, 5] = A[0, 0], A[0, 1], A[1, 0], A[1, 1]
+    P = np.linalg.solve(M0, S @ M0)
+    # feq per unit phi, from Eq. 16 moments (closed form) mapped back with M0^-1
+    ux, uy = u
+    Cb = np.outer(u, u) + CS2 * np.eye(2)
+    C2 = Cb[0, 0] + Cb[1, 1]
+    meq = np.array([1, -4 + 3 * C2, 3 - 3 * C2, ux, -ux, uy, -uy, Cb[0, 0] - Cb[1, 1], Cb[0, 1]])
+    a = np.linalg.solve(M0, meq)
+    L = np.eye(9) - P @ (np.eye(9) - np.outer(a, np.ones(9)))
+    kx = 2 * np.pi * np.fft.fftfreq(nx)
+    ky = 2 * np.pi * np.fft.fftfreq(ny)
+    KX, KY = np.meshgrid(kx, ky)
+    ph = np.exp(-1j * (KX[..., None] * CX + KY[..., None] * CY))     # (ny, nx, 9)
+    T = L[None, None] * ph[:, :, None, :]                               # L @ diag(ph)
+    # phi_N = 1^T D (L D)^(N-1) a phi0
+    Pw = np.broadcast_to(np.eye(9, dtype=complex), T.shape).copy()
+    base, e = T, nsteps - 1
+    while e:
+        if e & 1:
+            Pw = Pw @ base
+        base = base @ base
+        e >>= 1
+    v = (Pw @ a.astype(complex))                                        # (ny, nx, 9)
+    g = (ph * v).sum(-1)
+    return np.real(np.fft.ifft2(g * np.fft.fft2(phi0)))
+
+
+def test_spectral_exact_gaussian_128():
+    p = W.params("gaussian_iso_128")
+    sp = spec_of("gaussian_iso_128")
+    phi0 = W.phi0_gaussian()
+    num = O.run(sp, phi0, p["steps"])
+    ref = spectral_linear_periodic(phi0, p["u"], p["K"], W.s9(), p["steps"])
+    assert np.linalg.norm(num - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_spectral_exact_anisotropic_small():
+    rng = np.random.default_rng(50)
+    phi0 = rng.random((12, 20))
+    u, K = (0.07, -0.04), (0.03, 0.012, 0.02)
+    sp = O.Spec(nx=20, ny=12, conv=0, u=u, K=K, s=W.s9())
+    num = O.run(sp, phi0, 37)
+    ref = spectral_linear_periodic(phi0, u, K, W.s9(), 37)
+    assert np.linalg.norm(num - ref) / np.linalg.norm(ref) < 1e-12
+
+
+# ------------------------------------------------ closed forms and order 2
+
+def gaussian_closed_form(n, xc, yc, sigma0, u, K, t, amp=1.0):
+    """Eq. 60 summed over periodic images, amplitude amp at t = 0."""
+    Sig = sigma0 ** 2 * np.eye(2) + 2 * np.array([[K[0], K[1]], [K[1], K[2]]]) * t
+    Si = np.linalg.inv(Sig)
+    x = np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(x, x)
+    out = np.zeros((n, n))
+    for mx in (-2, -1, 0, 1, 2):
+        for my in (-2, -1, 0, 1, 2):
+            dx = X - xc - u[0] * t + mx * n
+            dy = Y - yc - u[1] * t + my * n
+            q = Si[0, 0] * dx * dx + 2 * Si[0, 1] * dx * dy + Si[1, 1] * dy * dy
+            out += np.exp(-q / 2)
+    return amp * sigma0 ** 2 / math.sqrt(np.linalg.det(Sig)) * out
+
+
+def test_gaussian_closed_form_128():
+    p = W.params("gaussian_iso_128")
+    phi = O.run(spec_of("gaussian_iso_128"), W.phi0_gaussian(), p["steps"])
+    ref = gaussian_closed_form(128, 64, 64, 8.0, p["u"], p["K"], p["steps"])
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-2
+
+
+def gre(num, ana):
+    """Eq. 39."""
+    return np.abs(ana - num).sum() / np.abs(ana).sum()
+
+
+def test_gaussian_anisotropic_second_order():
+    K = (0.02, 0.008, 0.01)
+    errs = []
+    for n in (32, 64, 128):
+        r = n // 32
+        steps, sig, u = 50 * r * r, n / 8, (0.04 / r, 0.02 / r)
+        sp = O.Spec(nx=n, ny=n, conv=0, u=u, K=K, s=W.s9())
+        phi0 = gaussian_closed_form(n, n / 2, n / 2, sig, u, K, 0.0)
+        num = O.run(sp, phi0, steps)
+        errs.append(gre(num, gaussian_closed_form(n, n / 2, n / 2, sig, u, K, steps)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 <= o <= 2.2 for o in orders), (errs, orders)
+
+
+def test_sinusoid_with_source_eq45_second_order():
+    # Sec. 3.1: [0,2]^2 periodic, u = 0.1, Pe = L u / kappa = 100 (kappa = 0.002)
+    kap, ux, uy, T = 0.002, 0.1, 0.1, 0.5
+    klat = 0.01                                    # diffusive scaling, fixed rates
+    errs = []
+    for n in (40, 80, 160):
+        dx = 2.0 / n
+        dt = klat * dx * dx / kap
+        steps = int(round(T / dt))
+        sp = O.Spec(nx=n, ny=n, conv=0, u=(ux * dt / dx, uy * dt / dx), K=(klat, 0, klat), s=W.s9(),
+                    src=1, src_par=(0.0, 0.0, dx, dt, kap, ux, uy))
+        x = np.arange(n) * dx
+        X, Y = np.meshgrid(x, x)
+        phi0 = np.sin(np.pi * (X + Y))                                       # Eq. 44
+        num = O.run(sp, phi0, steps)
+        ana = math.exp((1 - 2 * np.pi ** 2 * kap) * steps * dt) * np.sin(np.pi * (X + Y))  # Eq. 45
+        errs.append(gre(num, ana))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 <= o <= 2.3 for o in orders), (errs, orders)
+
+
+def test_variable_tensor_with_source_eq68_second_order():
+    # Sec. 3.5: K = kappa diag(2 - sin 2pi x sin 2pi y, 1), [0,1]^2 periodic
+    kap, ux, uy, T = 1e-3, 0.1, 0.1, 1.0
+    klat = 0.02
+    errs = []
+    for n in (32, 64, 128):
+        dx = 1.0 / n
+        dt = klat * dx * dx / kap
+        steps = int(round(T / dt))
+        x = np.arange(n) * dx
+        X, Y = np.meshgrid(x, x)
+        scale = dt / dx ** 2
+        Kf = np.stack([kap * (2 - np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y)) * scale,
+                       np.zeros_like(X), kap * np.ones_like(X) * scale])     # Eq. 65
+        sp = O.Spec(nx=n, ny=n, conv=0, u=(ux * dt / dx, uy * dt / dx), Kfield=Kf, s=W.s9(),
+                    src=2, src_par=(0.0, 0.0, dx, dt, kap, ux, uy))
+        phi0 = np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y)                # Eq. 67
+        num = O.run(sp, phi0, steps)
+        ana = math.exp((1 - 12 * np.pi ** 2 * kap) * steps * dt) * phi0      # Eq. 68
+        errs.append(gre(num, ana))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 5e-3 and all(1.7 <= o <= 2.3 for o in orders), (errs, orders)
+
+
+# ------------------------------------------ independent brute force, tiny grid
+
+def brute_force(nx, ny, bcx, bcy, walls, conv, u, diff, K, s9, r0, r1, phi0, nsteps):
+    """Independent numpy restatement: population-space collision with
+    P = M0^-1 S M0 and Q = M0^-1 (I - S/2) M0 from numpy linear algebra."""
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+    A = np.linalg.inv(np.array([[K[0], K[1]], [K[1], K[2]]]) / CS2 + 0.5 * np.eye(2))
+    S = np.diag(np.array(s9, dtype=np.float64))
+    S[3, 3], S[3, 5], S[5, 3], S[5, 5] = A[0, 0], A[0, 1], A[1, 0], A[1, 1]
+    Mi = np.linalg.inv(M0)
+    P = Mi @ S @ M0
+    Qm = Mi @ (np.eye(9) - S / 2) @ M0
+    u = np.asarray(u, dtype=np.float64)
+
+    def feq(phi):
+        B = flux_def(conv, u, phi)
+        Qt = C_def(conv, u, phi) + (CS2 * g_def(diff, phi) - CS2 * phi) * np.eye(2)
+        out = np.empty(9)
+        for k in range(9):
+            c = np.array([CX[k], CY[k]], dtype=np.float64)
+            out[k] = w[k] * (phi + c @ B / CS2 + np.sum(Qt * (np.outer(c, c) - CS2 * np.eye(2))) / (2 * CS2 ** 2))
+        return out
+
+    def Rk(phi, R):
+        Bp = u if conv == 0 else u * phi
+        return np.array([w[k] * (1 + (CX[k] * Bp[0] + CY[k] * Bp[1]) / CS2) * R for k in range(9)])
+
+    def collide(f):
+        phi = (f.sum() + r0 / 2) / (1 - r1 / 2)
+        R = r0 + r1 * phi
+        return f - P @ (f - feq(phi)) + Qm @ Rk(phi, R), phi
+
+    F = np.zeros((9, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            ph = phi0[y, x]
+            F[:, y, x] = collide(feq(ph) - Rk(ph, r0 + r1 * ph) / 2)[0]
+    phi = None
+    for _ in range(nsteps):
+        G = np.zeros_like(F)
+        phi = np.zeros((ny, nx))
+        for y in range(ny):
+            for x in range(nx):
+                f = np.empty(9)
+                for k in range(9):
+                    xs, ys = x - CX[k], y - CY[k]
+                    ox = not (0 <= xs < nx)
+                    oy = not (0 <= ys < ny)
+                    if ox and not bcx:
+                        xs, ox = xs % nx, False
+                    if oy and not bcy:
+                        ys, oy = ys % ny, False
+                    if not ox and not oy:
+                        f[k] = F[k, ys, xs]
+                    else:
+                        wx = walls[0] if xs < 0 else walls[1]
+                        wy = walls[2] if ys < 0 else walls[3]
+                        pw = 0.5 * (wx + wy) if (ox and oy) else (wx if ox else wy)
+                        fe = feq(pw)
+                        f[k] = -F[opp[k], y, x] + fe[k] + fe[opp[k]]
+                G[:, y, x], phi[y, x] = collide(f)
+        F = G
+    return phi, F
+
+
+@pytest.mark.parametrize("bcx,bcy,conv,diff", [(1, 1, 1, 2), (0, 1, 0, 1), (1, 0, 1, 0), (0, 0, 0, 2)])
+def test_brute_force_tiny(bcx, bcy, conv, diff):
+    rng = np.random.default_rng(60 + 8 * bcx + 4 * bcy + 2 * conv + diff)
+    nx, ny = 5, 4
+    u = tuple(rng.uniform(-0.2, 0.2, 2))
+    K = (0.03, 0.01, 0.05)
+    walls = tuple(rng.uniform(0, 1, 4))
+    s9 = W.s9()
+    r0, r1 = 0.01, -0.1
+    phi0 = rng.uniform(0.1, 0.9, (ny, nx))
+    sp = O.Spec(nx=nx, ny=ny, bc_x=bcx, bc_y=bcy, phi_wall=walls, conv=conv, u=u, diff=diff, K=K,
+                s=s9, r0=r0, r1=r1)
+    phi_o, F_o = O.run(sp, phi0, 3, return_state=True)
+    phi_b, F_b = brute_force(nx, ny, bcx, bcy, walls, conv, u, diff, K, s9, r0, r1, phi0, 3)
+    assert np.abs(phi_o - phi_b).max() < 1e-13
+    assert np.abs(F_o - F_b).max() < 1e-13
+
+
+# ------------------------------------------------------------- invariants
+
+def test_mass_conservation_periodic():
+    p = W.params("gaussian_iso_128")
+    sp = spec_of("gaussian_iso_128", nx=64, ny=64)
+    phi0 = W.gaussian_hill(64, 64, 30, 33, 6.0)
+    phi = O.run(sp, phi0, 1000)
+    assert abs(phi.sum() - phi0.sum()) / phi0.sum() < 1e-13
+
+
+@pytest.mark.parametrize("conv,diff,bc", [(1, 2, 1), (0, 1, 0), (1, 0, 1)])
+def test_uniform_state_is_fixed_point(conv, diff, bc):
+    c = 0.37
+    sp = O.Spec(nx=7, ny=6, bc_x=bc, bc_y=bc, phi_wall=(c, c, c, c), conv=conv, u=(0.1, -0.05),
+                diff=diff, K=(0.02, 0.005, 0.03), s=W.s9())
+    phi = O.run(sp, np.full((6, 7), c), 25)
+    assert np.abs(phi - c).max() < 1e-15
+
+
+def test_mirror_symmetry_xy():
+    rng = np.random.default_rng(70)
+    phi0 = rng.uniform(0.1, 0.9, (9, 11))
+    kw = dict(bc_x=1, bc_y=0, phi_wall=(0.2, 0.6, 0.0, 0.0), conv=1, diff=2, s=W.s9(), r0=0.01, r1=-0.05)
+    a = O.run(O.Spec(nx=11, ny=9, u=(0.1, -0.03), K=(0.02, 0.004, 0.05), **kw), phi0, 20)
+    kw2 = dict(kw, bc_x=0, bc_y=1, phi_wall=(0.0, 0.0, 0.2, 0.6))
+    # transposed problem: swap x and y; p_xx changes sign, p_xy is symmetric,
+    # so with s7 = s8 the transposed run must equal the transpose of the run
+    b = O.run(O.Spec(nx=9, ny=11, u=(-0.03, 0.1), K=(0.05, 0.004, 0.02), **kw2), phi0.T.copy(), 20)
+    assert np.abs(a - b.T).max() < 1e-13
+
+
+def test_s0_is_immaterial_in_scheme_b():
+    phi0 = W.phi0_aniso(24, seed=1)
+    base = dict(nx=24, ny=24, bc_x=1, bc_y=1, conv=0, diff=2, K=(0.02, 0.008, 0.01), r1=-0.1, r0=0.02)
+    s_a = list(W.s9()); s_a[0] = 0.0
+    s_b = list(W.s9()); s_b[0] = 1.0
+    a = O.run(O.Spec(s=tuple(s_a), **base), phi0, 40)
+    b = O.run(O.Spec(s=tuple(s_b), **base), phi0, 40)
+    assert np.abs(a - b).max() < 1e-14
+
+
+def test_bgk_reduction_bitwise():
+    # S = s I: the P-form collision (P rounded once from exact rationals) and the
+    # single-relaxation loop agree bit for bit, nonlinear families, source, walls
+    kap = CS2 * (1 / 1.3 - 0.5)
+    s = O.relax_block([kap, 0.0, kap])[0, 0]
+    rng = np.random.default_rng(80)
+    phi0 = rng.uniform(0.0, 1.0, (10, 12))
+    kw = dict(nx=12, ny=10, bc_x=1, bc_y=0, phi_wall=(0.3, 0.1, 0, 0), conv=1, u=(0.1, 0.05), diff=1,
+              K=(kap, 0.0, kap), s=(s,) * 9, r0=0.01, r1=-0.2)
+    P, Qm = O.pform_matrices(O.Spec(**kw))
+    assert np.array_equal(P, s * np.eye(9)) and np.array_equal(Qm, (1 - 0.5 * s) * np.eye(9))
+    a, Fa = O.run(O.Spec(collision=1, **kw), phi0, 30, return_state=True)
+    b, Fb = O.run(O.Spec(collision=2, **kw), phi0, 30, return_state=True)
+    assert np.array_equal(Fa, Fb) and np.array_equal(a, b)
+    c = O.run(O.Spec(collision=0, **kw), phi0, 30)
+    assert np.abs(c - a).max() < 1e-14
+
+
+def test_pform_matches_moment_form():
+    phi0 = W.phi0_aniso(20, seed=2)
+    kw = dict(nx=20, ny=20, bc_x=1, bc_y=1, conv=1, u=(0.05, 0.08), diff=2, K=(0.02, 0.008, 0.01),
+              s=W.s9(), r1=-0.1)
+    a = O.run(O.Spec(collision=0, **kw), phi0, 50)
+    b = O.run(O.Spec(collision=1, **kw), phi0, 50)
+    assert np.abs(a - b).max() < 1e-14
+
+
+def test_phi_from_post_state():
+    phi0 = W.phi0_aniso(16, seed=3)
+    sp = O.Spec(nx=16, ny=16, bc_x=1, bc_y=1, conv=0, diff=2, K=(0.02, 0.008, 0.01), s=W.s9(),
+                r0=0.003, r1=-0.1)
+    phi, F = O.run(sp, phi0, 7, return_state=True)
+    assert np.abs(O.phi_from_post(sp, F, 7) - phi).max() < 1e-15
+    F0 = O.init(sp, phi0)
+    assert np.abs(O.phi_from_post(sp, F0, 0) - phi0).max() < 1e-15
+
+
+# ---------------------------------------------------------- maximum principle
+
+def test_burgers_stays_bounded_small():
+    # the Burgers workload at 64^2 with the same physical scaling (K = 0.005 * n)
+    n = 64
+    phi0 = W.phi0_burgers(n, seed=2)
+    sp = O.Spec(nx=n, ny=n, conv=1, u=W.WORKLOADS["burgers_1024"]["u"], K=(0.005 * n, 0, 0.005 * n),
+                s=W.s9())
+    phi = O.run(sp, phi0, 5 * n)
+    assert np.isfinite(phi).all() and np.abs(phi).max() <= 0.5 + 1e-3
+
+
+def test_aniso_dirichlet_bounded_small():
+    sp = spec_of("aniso_dirichlet_4096", nx=48, ny=40)
+    phi0 = W.phi0_aniso(48, seed=3, ny=40)
+    phi = O.run(sp, phi0, 300)
+    assert phi.min() >= -1e-9 and phi.max() <= 1.0
+    assert phi.sum() < phi0.sum()
+
+
+# ---------------------------------------------------------------- adjoint
+
+def adjoint_case(n=10, m=8, steps=12, seed=90):
+    rng = np.random.default_rng(seed)
+    Kf, phi0, tgt = W.adjoint_inputs(n, seed=seed, ny=m)
+    sp = O.Spec(nx=n, ny=m, conv=0, u=(0.03, -0.01), Kfield=Kf, s=W.s9())
+    return sp, Kf, phi0, tgt, rng
+
+
+def test_adjoint_dot_product():
+    sp, Kf, phi0, tgt, rng = adjoint_case()
+    r = rng.normal(size=phi0.shape)
+    d = rng.normal(size=phi0.shape)
+    Td = O.run(sp, d, 12)                           # linear map phi0 -> phi_N
+    _, g, _, _ = O.adjoint(sp, np.zeros_like(phi0), -r, 12)   # T^T r
+    lhs, rhs = float((r * Td).sum()), float((g * d).sum())
+    assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), 1.0)
+
+
+def test_adjoint_finite_differences():
+    sp, Kf, phi0, tgt, rng = adjoint_case()
+    L, dphi0, dK, du = O.adjoint(sp, phi0, tgt, 12)
+    h = 1e-6
+
+    def loss(phi0_=phi0, Kf_=Kf, u_=sp.u):
+        s2 = O.Spec(nx=sp.nx, ny=sp.ny, conv=0, u=u_, Kfield=Kf_, s=sp.s)
+        return O.adjoint(s2, phi0_, tgt, 12)[0]
+
+    for _ in range(4):
+        c, y, x = rng.integers(3), rng.integers(sp.ny), rng.integers(sp.nx)
+        Kp, Km = Kf.copy(), Kf.copy()
+        Kp[c, y, x] += h
+        Km[c, y, x] -= h
+        fd = (loss(Kf_=Kp) - loss(Kf_=Km)) / (2 * h)
+        assert abs(fd - dK[c, y, x]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(dK).max())
+        pp, pm = phi0.copy(), phi0.copy()
+        pp[y, x] += h
+        pm[y, x] -= h
+        fd = (loss(phi0_=pp) - loss(phi0_=pm)) / (2 * h)
+        assert abs(fd - dphi0[y, x]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(dphi0).max())
+    for a in range(2):
+        up, um = list(sp.u), list(sp.u)
+        up[a] += h
+        um[a] -= h
+        fd = (loss(u_=tuple(up)) - loss(u_=tuple(um))) / (2 * h)
+        assert abs(fd - du[a]) <= 1e-6 * max(abs(fd), 1e-6)

@@ -1,0 +1,146 @@
+"""Seeded synthetic inputs and problem parameters of the five workloads.
+
+This module holds no arithmetic of the lattice Boltzmann method: it only states
+each workload's physical parameters in lattice units (c = dx/dt = 1) and draws
+its seeded initial fields, so that the CPU oracle and the CUDA path receive
+bit-identical inputs. Each side derives its own relaxation rates from K.
+
+Workloads (sizes, parameters and seeds):
+  gaussian_iso_128     linear isotropic CDE, 128^2 periodic, u = (0.05, 0.02),
+                       K = 0.01 I, Gaussian hill sigma = 8 at the centre, 1000 steps
+  burgers_1024         Burgers flux B = a phi^2/2, a = (1,1)/sqrt2, 1024^2 periodic,
+                       0.5 sin sin + 1e-3 uniform noise (seed 2), 5000 steps
+  aniso_dirichlet_4096 D(phi) = (1 + phi^2) K, K = [[0.02,0.008],[0.008,0.01]],
+                       R = -0.1 phi, 4096^2 with phi = 0 walls, U[0,1) smoothed by
+                       three Jacobi passes (seed 3), 2000 steps
+  adjoint_512          linear anisotropic CDE with a per-cell K(x), 512^2 periodic,
+                       u = (0.03, 0), 500 steps, smooth seeded fields (seed 4)
+  ensemble_256         256 nonlinear CDE instances, sides log-uniform in [64, 1024],
+                       |u| <= 0.1, D(phi) = D0 (1 + phi), D0 in [0.001, 0.05] (seed 5)
+
+The Burgers workload reads the diffusivity D = 0.005 on the unit square with
+dx = dt = 1/1024, i.e. K = 0.005 * 1024 = 5.12 in lattice units, while the
+flux vector keeps |a| = 1 (c = 1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# relaxation rates of the non-diffusive moments (s0, s1, s2, s4, s6, s7, s8),
+# the values the 128^2 Gaussian-hill workload prescribes, used for every workload
+S_OTHER = (1.0, 1.2, 1.2, 1.0, 1.0, 1.1, 1.1)
+
+
+def s9(s_other=S_OTHER):
+    """s0..s8 with placeholders at the diffusive indices 3 and 5."""
+    s0, s1, s2, s4, s6, s7, s8 = s_other
+    return (s0, s1, s2, 0.0, s4, 0.0, s6, s7, s8)
+
+
+WORKLOADS = {
+    "gaussian_iso_128": dict(
+        nx=128, ny=128, bc=(0, 0), phi_wall=(0.0, 0.0, 0.0, 0.0), conv=0, u=(0.05, 0.02),
+        diff=0, K=(0.01, 0.0, 0.01), r0=0.0, r1=0.0, steps=1000),
+    "burgers_1024": dict(
+        nx=1024, ny=1024, bc=(0, 0), phi_wall=(0.0, 0.0, 0.0, 0.0), conv=1,
+        u=(1.0 / math.sqrt(2.0), 1.0 / math.sqrt(2.0)), diff=0, K=(5.12, 0.0, 5.12),
+        r0=0.0, r1=0.0, steps=5000),
+    "aniso_dirichlet_4096": dict(
+        nx=4096, ny=4096, bc=(1, 1), phi_wall=(0.0, 0.0, 0.0, 0.0), conv=0, u=(0.0, 0.0),
+        diff=2, K=(0.02, 0.008, 0.01), r0=0.0, r1=-0.1, steps=2000),
+    "adjoint_512": dict(
+        nx=512, ny=512, bc=(0, 0), phi_wall=(0.0, 0.0, 0.0, 0.0), conv=0, u=(0.03, 0.0),
+        diff=0, K=(0.01, 0.0, 0.01), r0=0.0, r1=0.0, steps=500, ckpt_every=50),
+}
+
+
+def params(name: str, **over) -> dict:
+    d = dict(WORKLOADS[name])
+    d.update(over)
+    return d
+
+
+# ---- initial fields ---------------------------------------------------------
+
+def gaussian_hill(nx: int, ny: int, xc: float, yc: float, sigma: float, amp: float = 1.0):
+    """Periodic Gaussian hill on integer nodes (nearest-image distance)."""
+    x = np.arange(nx, dtype=np.float64)
+    y = np.arange(ny, dtype=np.float64)
+    dx = (x - xc + nx / 2) % nx - nx / 2
+    dy = (y - yc + ny / 2) % ny - ny / 2
+    return amp * np.exp(-(dy[:, None] ** 2 + dx[None, :] ** 2) / (2.0 * sigma * sigma))
+
+
+def phi0_gaussian(n: int = 128, sigma: float = 8.0):
+    return gaussian_hill(n, n, n / 2, n / 2, sigma, 1.0)
+
+
+def phi0_burgers(n: int = 1024, seed: int = 2):
+    rng = np.random.default_rng(seed)
+    x = np.arange(n, dtype=np.float64) / n
+    base = 0.5 * np.sin(2 * np.pi * x)[None, :] * np.sin(2 * np.pi * x)[:, None]
+    return base + rng.uniform(-1e-3, 1e-3, size=(n, n))
+
+
+def jacobi_smooth(a, passes: int = 3):
+    """phi <- mean of the 4 neighbours, zero outside the domain."""
+    a = np.array(a, dtype=np.float64)
+    for _ in range(passes):
+        p = np.pad(a, 1)
+        a = 0.25 * (p[:-2, 1:-1] + p[2:, 1:-1] + p[1:-1, :-2] + p[1:-1, 2:])
+    return a
+
+
+def phi0_aniso(n: int = 4096, seed: int = 3, ny: int | None = None):
+    rng = np.random.default_rng(seed)
+    return jacobi_smooth(rng.random((ny or n, n)), 3)
+
+
+def smooth_field(nx: int, ny: int, rng, modes: int = 8, kmax: int = 4):
+    """Sum of random periodic Fourier modes with |k| <= kmax, scaled to unit max."""
+    x = np.arange(nx, dtype=np.float64) / nx
+    y = np.arange(ny, dtype=np.float64) / ny
+    f = np.zeros((ny, nx))
+    for _ in range(modes):
+        kx, ky = rng.integers(-kmax, kmax + 1, size=2)
+        if kx == 0 and ky == 0:
+            kx = 1
+        ph = rng.uniform(0, 2 * np.pi)
+        f += rng.normal() * np.cos(2 * np.pi * (kx * x[None, :] + ky * y[:, None]) + ph)
+    return f / max(np.abs(f).max(), 1e-300)
+
+
+def adjoint_inputs(n: int = 512, seed: int = 4, ny: int | None = None):
+    """Per-cell tensor field (3, ny, nx), initial phi and target phi."""
+    ny = ny or n
+    rng = np.random.default_rng(seed)
+    sig = lambda z: 1.0 / (1.0 + np.exp(-z))
+    kxx = 0.005 + 0.045 * sig(2.0 * smooth_field(n, ny, rng))
+    kyy = 0.005 + 0.045 * sig(2.0 * smooth_field(n, ny, rng))
+    kxy = 0.5 * np.sqrt(kxx * kyy) * np.tanh(smooth_field(n, ny, rng))
+    phi0 = 0.5 + 0.4 * smooth_field(n, ny, rng)
+    target = 0.5 + 0.4 * smooth_field(n, ny, rng)
+    return np.stack([kxx, kxy, kyy]), phi0, target
+
+
+def ensemble(count: int = 256, seed: int = 5, side_min: int = 64, side_max: int = 1024):
+    """Per-instance parameters of the batched ensemble."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        side = int(round(math.exp(rng.uniform(math.log(side_min), math.log(side_max)))))
+        r = 0.1 * math.sqrt(rng.uniform())
+        th = rng.uniform(0, 2 * math.pi)
+        D0 = rng.uniform(0.001, 0.05)
+        xc, yc = rng.uniform(0, side, size=2)
+        sigma = max(4.0, rng.uniform(side / 32, side / 8))
+        amp = rng.uniform(0.5, 1.0)
+        out.append(dict(nx=side, ny=side, u=(r * math.cos(th), r * math.sin(th)), D0=D0,
+                        K=(D0, 0.0, D0), diff=1, conv=0, xc=xc, yc=yc, sigma=sigma, amp=amp))
+    return out
+
+
+def ensemble_phi0(inst: dict):
+    return gaussian_hill(inst["nx"], inst["ny"], inst["xc"], inst["yc"], inst["sigma"], inst["amp"])
