@@ -1,0 +1,297 @@
+"""Throughput benchmark of the fused D2Q9 MRT stream-collide path.
+
+Workload: the anisotropic nonlinear diffusion problem with a source on a
+4096 x 4096 grid with phi = 0 anti-bounce-back walls (D(phi) = (1 + phi^2) K,
+K = [[0.02, 0.008], [0.008, 0.01]], R = -0.1 phi), 2000 time steps. One bench
+step is that whole job: initialisation from the resident initial field, 2000
+fused stream-collide steps and the FP64 mass reduction. The metric is MLUPS
+(million lattice-node updates per second) over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f32|bf16s|f64]
+                  [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (each
+step: one time step of the same 4096^2 workload).
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "aniso_dirichlet_4096"
+BYTES_PER_UPDATE = {"f32": 72, "bf16s": 44, "f64": 144}
+KERNEL_SRC = os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", "kernels_step.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prec", default="f32", choices=["f32", "bf16s", "f64"])
+    ap.add_argument("--spp", type=int, default=1, help="time steps per sweep (1 or 2)")
+    ap.add_argument("--lbm-steps", type=int, default=None, help="time steps per bench step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def config(args, lbm_steps):
+    p = W.params(WORKLOAD)
+    return {"workload": f"{WORKLOAD}: D2Q9 MRT, D(phi)=(1+phi^2)K, K=[[0.02,0.008],[0.008,0.01]], "
+                        f"R=-0.1 phi, 4096x4096, phi=0 anti-bounce-back walls, {lbm_steps} steps per job",
+            "nx": p["nx"], "ny": p["ny"], "lbm_steps_per_bench_step": lbm_steps,
+            "storage": args.prec, "steps_per_pass": args.spp,
+            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
+            "l2": "inputs larger than L2 (two population buffers of 604 MB each, FP32)"}
+
+
+def oracle_problem():
+    import oracle as O
+    p = W.params(WORKLOAD)
+    return O, O.Spec(nx=p["nx"], ny=p["ny"], bc_x=p["bc"][0], bc_y=p["bc"][1], phi_wall=p["phi_wall"],
+                     conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"], s=W.s9(), r0=p["r0"], r1=p["r1"])
+
+
+def cpu_sample(target_s=15.0):
+    """The oracle as it stands on the host cores: the full 4096^2 grid for as
+    many time steps as fit about target_s seconds."""
+    O, sp = oracle_problem()
+    phi0 = W.phi0_aniso(4096, seed=3)
+    t0 = time.perf_counter()
+    F = O.init(sp, phi0)
+    F, _ = O.step(sp, F, 0)
+    one = time.perf_counter() - t0
+    nsteps = int(max(1, min(40, target_s / max(one / 2, 1e-3))))
+    t0 = time.perf_counter()
+    for n in range(nsteps):
+        F, _ = O.step(sp, F, n + 1)
+    dt = time.perf_counter() - t0
+    cells = 4096 * 4096
+    return {"value": cells * nsteps / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"4096x4096 grid of the same workload, {nsteps} time steps ({dt:.1f} s), FP64"}
+
+
+def clocks_sampler():
+    try:
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        gpu = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        return subprocess.Popen(["nvidia-smi", "-i", gpu, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return None
+
+
+def clocks_summary(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except Exception:
+        return None
+    mhz, maxm, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            mhz.append(float(f[1]))
+            maxm = float(f[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not mhz:
+        return None
+    return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": maxm, "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_per_launch(kernel_sha):
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        if t.get("kernel_src_sha256") != kernel_sha:
+            return None
+        return t["dram_bytes_per_full_launch"]
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    O, sp = oracle_problem()
+    phi0 = W.phi0_aniso(4096, seed=3)
+    F = O.init(sp, phi0)
+    for n in range(args.warmup):
+        F, _ = O.step(sp, F, n)
+    times = []
+    for n in range(args.steps):
+        t0 = time.perf_counter()
+        F, _ = O.step(sp, F, args.warmup + n)
+        times.append(time.perf_counter() - t0)
+    cells = 4096 * 4096
+    ms = 1e3 * sum(times) / len(times)
+    val = cells / (ms / 1e3) / 1e6
+    out = {"metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": config(args, args.lbm_steps or W.params(WORKLOAD)["steps"]),
+           "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
+                            "sample": "one time step of the 4096x4096 workload per bench step"},
+           "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1603_09577_gb300 import Solver
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = W.params(WORKLOAD)
+    lbm_steps = args.lbm_steps or p["steps"]
+    nx, ny = p["nx"], p["ny"]
+    cells = nx * ny
+
+    phi0_np = W.phi0_aniso(4096, seed=3).astype(np.float32)
+    phi0 = torch.from_numpy(phi0_np).cuda()
+    s = Solver(nx, ny, prec=args.prec, bc=("abb", "abb"), phi_wall=p["phi_wall"], steps_per_pass=args.spp)
+    s.set_coeffs(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"], s=W.s9(), r0=p["r0"], r1=p["r1"])
+    red = torch.zeros(8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def job():
+        s.set_phi(phi0)
+        s.step(lbm_steps)
+        s.reduce_async(out=red)
+
+    for _ in range(args.warmup):
+        job()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clk = clocks_sampler()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for e0, e1, e2 in ev:
+        s.set_phi(phi0)
+        e0.record(stream)
+        s.step(lbm_steps)
+        e1.record(stream)
+        s.reduce_async(out=red)
+        e2.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = clocks_summary(clk)
+    total_ms = t_start.elapsed_time(t_end)
+    step_kernels_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+    mass = float(red[0].item())
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    ms_per_step = total_ms / args.steps
+    value = world * cells * lbm_steps / (ms_per_step / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    host_in = torch.from_numpy(phi0_np).pin_memory()
+    host_out = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
+    for _ in range(1):
+        s.set_phi_host(host_in)
+        s.step(lbm_steps)
+        s.phi_host(host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_phi_host(host_in)
+        s.step(lbm_steps)
+        s.phi_host(host_out)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * cells * lbm_steps / e2e_s / 1e6
+
+    if rank == 0:
+        launches_per_job = lbm_steps // args.spp + lbm_steps % args.spp
+        launch_ms = statistics.mean(step_kernels_ms) / launches_per_job
+        # one launch reads and writes every population once, whatever the
+        # number of time steps it advances
+        alg_bytes = BYTES_PER_UPDATE[args.prec] * cells
+        achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+        peak, src = measured_peak()
+        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+        out = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec, "data": "synthetic", "config": config(args, lbm_steps),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic_per_launch(sha),
+                         "kernel": "k_step (fused pull-stream + collide)",
+                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_ms,
+                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src},
+            "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": int(host_in.numel() * 4),
+                    "d2h_bytes_per_step": int(host_out.numel() * 4)},
+            "gpu_launches": args.steps * (1 + launches_per_job + 2),
+            "mass_after_job": mass,
+        }
+        if clocks is not None:
+            out["clocks"] = clocks
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_sample()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

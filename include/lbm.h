@@ -1,0 +1,142 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the D2Q9 multiple-
+ * relaxation-time lattice Boltzmann model of nonlinear anisotropic
+ * convection-diffusion equations (Chai, Shi & Guo, arXiv:1603.09577).
+ *
+ * The equation solved is Eq. 1,
+ *     d_t phi + div B(phi) = div[K . (div D(phi))] + R,
+ * with D(phi) = g(phi) I and the closed coefficient families of lbm_coeffs.
+ * Every time step is one fused pull-stream / collide sweep (Eq. 34, Scheme B)
+ * on the D2Q9 lattice (Eq. 5), in lattice units c = dx/dt = 1, c_s^2 = 1/3,
+ * d = 1.
+ *
+ * Conventions for every entry point:
+ *  - Return value: LBM_OK (0) or an error code; lbm_last_error() gives a
+ *    thread-local message. No C++ exception crosses this boundary.
+ *  - Memory: the caller owns all device memory. The library never allocates
+ *    device memory; lbm_create receives a workspace of lbm_workspace_size()
+ *    bytes (device, 256-byte aligned) and keeps pointers into it until
+ *    lbm_destroy. Host-side handle memory is the library's.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream). Calls are asynchronous on that stream unless stated.
+ *  - Fields: phi arrays are row-major (ny rows of nx), element (x, y) at
+ *    y * nx + x, no padding. Precision tags: LBM_F64 = double, LBM_F32 = float.
+ *  - State: after lbm_set_phi and after every lbm_step the stored state is the
+ *    post-collision shifted population fbar*(x, t_n) (Eq. 33-34).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_EINVAL 1        /* invalid argument or handle                       */
+#define LBM_ECUDA 2         /* a CUDA runtime call failed                        */
+#define LBM_ENONFINITE 3    /* a non-finite value was detected                   */
+#define LBM_ETIMEOUT 4      /* a bounded device-side wait ran out                */
+#define LBM_EUNSUPPORTED 5  /* valid request this build does not implement      */
+
+/* population storage precision */
+#define LBM_F64 0           /* double populations, double arithmetic            */
+#define LBM_F32 1           /* float populations, float arithmetic              */
+#define LBM_BF16S 2         /* bf16 equilibrium-shifted deviations g_k =
+                               fbar*_k - w_k phi plus a float phi plane; float
+                               arithmetic                                        */
+
+/* boundary kinds per axis */
+#define LBM_PERIODIC 0
+#define LBM_ABB 1           /* anti-bounce-back Dirichlet wall half-way between
+                               the boundary node and its missing neighbour
+                               (Sec. 3.6)                                        */
+
+typedef struct lbm_solver *lbm_handle;
+
+/* Grid, storage and boundaries. */
+typedef struct {
+    int nx, ny;             /* nodes per axis, each >= 2                          */
+    int prec;               /* LBM_F64, LBM_F32 or LBM_BF16S                      */
+    int bc_x, bc_y;         /* LBM_PERIODIC or LBM_ABB on the x and y walls       */
+    double phi_wall[4];     /* Dirichlet values: west, east, south, north         */
+    int steps_per_pass;     /* 1, or 2: two time steps per sweep through memory
+                               (F32 and BF16S with periodic or ABB walls)         */
+    int per_cell_K;         /* 1: K comes from lbm_set_K_field                    */
+} lbm_desc;
+
+/* Coefficient families of Eq. 1 (Sec. 2.1), source and relaxation rates. */
+typedef struct {
+    int conv;               /* 0: B = u phi, C = u u^T phi;
+                               1: B = a phi^2/2, C = a a^T phi^3/3 (Eq. 7)        */
+    double u[2];            /* u (conv 0) or a (conv 1)                          */
+    int diff;               /* D = g(phi) I, g = 0: phi, 1: phi + phi^2/2,
+                               2: phi + phi^3/3                                   */
+    double K[3];            /* constant tensor (Kxx, Kxy, Kyy), symmetric positive
+                               definite; the block A = [[s3, s35], [s53, s5]] of
+                               Eq. 17 follows from Eq. 26:
+                               A = (K / (d c_s^2) + I/2)^-1                       */
+    double s[9];            /* s0..s8 of Eq. 17; entries 3 and 5 are ignored
+                               (they come from K); all others in (0, 2)           */
+    double r0, r1;          /* source R = r0 + r1 phi; phi from Eq. 35 in closed
+                               form phi = (sum fbar + r0/2) / (1 - r1/2)          */
+} lbm_coeffs;
+
+/* Bytes of device workspace lbm_create needs for this description. */
+int lbm_workspace_size(const lbm_desc *desc, size_t *bytes);
+
+/* Create a solver. dev_workspace: device pointer, >= lbm_workspace_size bytes,
+   256-byte aligned, owned by the caller and kept alive until lbm_destroy. */
+int lbm_create(lbm_handle *h, const lbm_desc *desc, void *dev_workspace, size_t bytes);
+int lbm_destroy(lbm_handle h);
+
+/* Set the coefficient families, the constant tensor K, rates and source.
+   Validates s_i in (0, 2) and K positive definite (Eq. 26 needs A^-1 - I/2
+   positive definite). Host-only; takes effect for later launches. */
+int lbm_set_coeffs(lbm_handle h, const lbm_coeffs *c);
+
+/* Per-cell tensor field (requires desc.per_cell_K): dev_K holds three planes of
+   nx*ny doubles (Kxx, Kxy, Kyy). A kernel converts it by Eq. 26 into per-cell
+   relaxation blocks stored in the workspace. */
+int lbm_set_K_field(lbm_handle h, const double *dev_K, void *stream);
+
+/* Initial condition phi(x, 0) (Eq. 40): fbar = feq(phi0) - R_k/2 (Eq. 33), then
+   one collision, so that the stored state is fbar*(x, t_0). dev_phi: nx*ny
+   values of precision `prec` (LBM_F64 or LBM_F32). */
+int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream);
+
+/* Advance nsteps time steps (fused pull-stream + collide of Eq. 34 with the
+   boundaries of lbm_desc). Asynchronous; no host synchronisation. */
+int lbm_step(lbm_handle h, int nsteps, void *stream);
+
+/* phi(t_n) of the current state into dev_out (nx*ny values of `prec`). */
+int lbm_get_phi(lbm_handle h, void *dev_out, int prec, void *stream);
+
+/* Host-buffer variants of lbm_set_phi / lbm_get_phi: the copy between host
+   memory (pinned for asynchronous copies) and a staging area of the workspace
+   is part of the call. lbm_get_phi_host synchronises `stream` before returning. */
+int lbm_set_phi_host(lbm_handle h, const void *host_phi, int prec, void *stream);
+int lbm_get_phi_host(lbm_handle h, void *host_out, int prec, void *stream);
+
+/* Reductions over phi(t_n) (Eq. 39 and norms), FP64, deterministic order.
+   dev_ref: nx*ny doubles or NULL. dev_out: 8 doubles on the device:
+   [0] sum phi, [1] sum |phi - ref|, [2] sum |ref|, [3] sum (phi - ref)^2,
+   [4] sum ref^2, [5] max |phi|, [6] number of non-finite phi, [7] sum phi^2.
+   Entries 1-4 are 0 when dev_ref is NULL. GRE (Eq. 39) = out[1] / out[2]. */
+int lbm_reduce(lbm_handle h, const double *dev_ref, double *dev_out, void *stream);
+
+/* Checkpoint / resume: the state is lbm_state_bytes bytes (populations and, for
+   LBM_BF16S, the phi plane). dev_dst / dev_src: device buffers of that size. */
+int lbm_state_bytes(lbm_handle h, size_t *bytes);
+int lbm_save(lbm_handle h, void *dev_dst, void *stream);
+int lbm_load(lbm_handle h, const void *dev_src, void *stream);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

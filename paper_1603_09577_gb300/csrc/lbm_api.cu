@@ -1,0 +1,336 @@
+// lbm_api.cu -- the extern "C" boundary of liblbm: handle life cycle, workspace
+// layout, argument validation, coefficient set-up and dispatch to the kernels.
+// The library never allocates device memory: every buffer is a slice of the
+// caller's workspace.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return LBM_OK;
+    return fail(LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int make_layout(const lbm_desc *d, Layout *L)
+{
+    L->pitch = ((long long)d->nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+    L->plane = L->pitch * d->ny;
+    L->esize = d->prec == LBM_F64 ? 8 : (d->prec == LBM_F32 ? 4 : 2);
+    L->csize = d->prec == LBM_F64 ? 8 : 4;
+    L->pop_bytes = up256(9 * (size_t)L->plane * L->esize);
+    L->phi_bytes = d->prec == LBM_BF16S ? up256((size_t)L->plane * 4) : 0;
+    size_t off = 0;
+    for (int b = 0; b < 2; ++b) {
+        L->off_pop[b] = off;
+        off += L->pop_bytes;
+        L->off_phi[b] = off;
+        off += L->phi_bytes;
+    }
+    L->off_afield = off;
+    if (d->per_cell_K) off += up256(3 * (size_t)L->plane * L->csize);
+    L->off_staging = off;
+    off += up256((size_t)d->nx * d->ny * 8);
+    L->off_partials = off;
+    off += up256((size_t)kReduceBlocks * 8 * sizeof(double));
+    L->off_flag = off;
+    off += 256;
+    L->total = off;
+    return LBM_OK;
+}
+
+static int check_desc(const lbm_desc *d)
+{
+    if (!d) return fail(LBM_EINVAL, "null lbm_desc");
+    if (d->nx < 2 || d->ny < 2) return fail(LBM_EINVAL, "nx and ny must be >= 2");
+    if ((long long)d->nx * d->ny > (1LL << 31)) return fail(LBM_EINVAL, "grid larger than 2^31 nodes");
+    if (d->prec != LBM_F64 && d->prec != LBM_F32 && d->prec != LBM_BF16S) return fail(LBM_EINVAL, "unknown precision");
+    if ((d->bc_x != LBM_PERIODIC && d->bc_x != LBM_ABB) || (d->bc_y != LBM_PERIODIC && d->bc_y != LBM_ABB))
+        return fail(LBM_EINVAL, "unknown boundary kind");
+    for (int i = 0; i < 4; ++i)
+        if (!isfinite(d->phi_wall[i])) return fail(LBM_EINVAL, "non-finite wall value");
+    if (d->steps_per_pass != 1 && d->steps_per_pass != 2) return fail(LBM_EINVAL, "steps_per_pass must be 1 or 2");
+    if (d->steps_per_pass == 2) return fail(LBM_EUNSUPPORTED, "two steps per pass is not built yet");
+    return LBM_OK;
+}
+
+// Eq. 26 solved for the relaxation block: A = (K / (d c_s^2) + I/2)^-1, d = 1.
+static bool relax_block(const double K[3], double *A3, double *A35, double *A5)
+{
+    if (!(K[0] > 0.0) || !(K[0] * K[2] - K[1] * K[1] > 0.0)) return false;
+    const double a = 3.0 * K[0] + 0.5, b = 3.0 * K[1], c = 3.0 * K[2] + 0.5;
+    const double det = a * c - b * b;
+    *A3 = c / det;
+    *A35 = -b / det;
+    *A5 = a / det;
+    return true;
+}
+
+template <class C>
+Params<C> make_params(const lbm_solver *s)
+{
+    Params<C> p;
+    const lbm_coeffs &c = s->c;
+    p.nx = s->d.nx;
+    p.ny = s->d.ny;
+    p.pitch = s->L.pitch;
+    p.plane = s->L.plane;
+    p.abb_x = s->d.bc_x == LBM_ABB;
+    p.abb_y = s->d.bc_y == LBM_ABB;
+    p.s1 = (C)c.s[1]; p.s2 = (C)c.s[2]; p.s4 = (C)c.s[4];
+    p.s6 = (C)c.s[6]; p.s7 = (C)c.s[7]; p.s8 = (C)c.s[8];
+    p.h1 = (C)(1.0 - 0.5 * c.s[1]); p.h2 = (C)(1.0 - 0.5 * c.s[2]);
+    p.h4 = (C)(1.0 - 0.5 * c.s[4]); p.h6 = (C)(1.0 - 0.5 * c.s[6]);
+    double A3 = 1, A35 = 0, A5 = 1;
+    relax_block(c.K, &A3, &A35, &A5);
+    p.A3 = (C)A3; p.A35 = (C)A35; p.A5 = (C)A5;
+    p.ux = (C)c.u[0]; p.uy = (C)c.u[1];
+    p.uxx = (C)(c.u[0] * c.u[0]); p.uxy = (C)(c.u[0] * c.u[1]); p.uyy = (C)(c.u[1] * c.u[1]);
+    p.r0 = (C)c.r0; p.r1 = (C)c.r1;
+    p.half_r0 = (C)(0.5 * c.r0);
+    p.inv_den = (C)(1.0 / (1.0 - 0.5 * c.r1));
+    p.inv_post = (C)(1.0 / (1.0 + 0.5 * c.r1));
+    p.has_src = (c.r0 != 0.0 || c.r1 != 0.0);
+    for (int i = 0; i < 4; ++i) p.phi_wall[i] = (C)s->d.phi_wall[i];
+    p.Afield = s->d.per_cell_K ? (const C *)s->afield : nullptr;
+    return p;
+}
+
+template Params<float> make_params<float>(const lbm_solver *);
+template Params<double> make_params<double>(const lbm_solver *);
+
+static int check_handle(lbm_handle h)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    return LBM_OK;
+}
+
+static int check_ready(lbm_handle h)
+{
+    if (check_handle(h)) return LBM_EINVAL;
+    if (!h->coeffs_set) return fail(LBM_EINVAL, "lbm_set_coeffs has not been called");
+    if (h->d.per_cell_K && !h->kfield_set) return fail(LBM_EINVAL, "lbm_set_K_field has not been called");
+    return LBM_OK;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err.c_str(); }
+
+int lbm_workspace_size(const lbm_desc *desc, size_t *bytes)
+{
+    if (int rc = check_desc(desc)) return rc;
+    if (!bytes) return fail(LBM_EINVAL, "null size pointer");
+    Layout L;
+    make_layout(desc, &L);
+    *bytes = L.total;
+    return LBM_OK;
+}
+
+int lbm_create(lbm_handle *h, const lbm_desc *desc, void *dev_workspace, size_t bytes)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle pointer");
+    *h = nullptr;
+    if (int rc = check_desc(desc)) return rc;
+    Layout L;
+    make_layout(desc, &L);
+    if (!dev_workspace) return fail(LBM_EINVAL, "null workspace");
+    if (((uintptr_t)dev_workspace & 255) != 0) return fail(LBM_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < L.total) return fail(LBM_EINVAL, "workspace smaller than lbm_workspace_size");
+    lbm_solver *s = new (std::nothrow) lbm_solver();
+    if (!s) return fail(LBM_EINVAL, "out of host memory");
+    s->d = *desc;
+    s->L = L;
+    s->ws = (char *)dev_workspace;
+    s->ws_bytes = bytes;
+    for (int b = 0; b < 2; ++b) {
+        s->pop[b] = s->ws + L.off_pop[b];
+        s->phi[b] = L.phi_bytes ? (float *)(s->ws + L.off_phi[b]) : nullptr;
+    }
+    s->afield = desc->per_cell_K ? (void *)(s->ws + L.off_afield) : nullptr;
+    s->staging = s->ws + L.off_staging;
+    s->partials = (double *)(s->ws + L.off_partials);
+    s->flag = (int *)(s->ws + L.off_flag);
+    *h = s;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle h)
+{
+    delete h;
+    return LBM_OK;
+}
+
+int lbm_set_coeffs(lbm_handle h, const lbm_coeffs *c)
+{
+    if (check_handle(h)) return LBM_EINVAL;
+    if (!c) return fail(LBM_EINVAL, "null lbm_coeffs");
+    if (c->conv != 0 && c->conv != 1) return fail(LBM_EINVAL, "conv must be 0 or 1");
+    if (c->diff < 0 || c->diff > 2) return fail(LBM_EINVAL, "diff must be 0, 1 or 2");
+    for (int i = 0; i < 9; ++i) {
+        if (i == 3 || i == 5) continue;
+        if (!(c->s[i] > 0.0 && c->s[i] < 2.0) && !(i == 0 && c->s[i] == 0.0))
+            return fail(LBM_EINVAL, "relaxation rates must lie in (0, 2)");
+    }
+    if (!isfinite(c->u[0]) || !isfinite(c->u[1]) || !isfinite(c->r0) || !isfinite(c->r1))
+        return fail(LBM_EINVAL, "non-finite coefficient");
+    if (!(c->r1 < 2.0 && c->r1 > -2.0)) return fail(LBM_EINVAL, "|r1| must be < 2 for Eq. 35 to be solvable");
+    if (!h->d.per_cell_K) {
+        double a, b, d;
+        if (!relax_block(c->K, &a, &b, &d)) return fail(LBM_EINVAL, "K is not symmetric positive definite");
+    }
+    h->c = *c;
+    h->coeffs_set = 1;
+    return LBM_OK;
+}
+
+int lbm_set_K_field(lbm_handle h, const double *dev_K, void *stream)
+{
+    if (check_handle(h)) return LBM_EINVAL;
+    if (!h->d.per_cell_K) return fail(LBM_EINVAL, "solver was created without per_cell_K");
+    if (!dev_K) return fail(LBM_EINVAL, "null tensor field");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(cudaMemsetAsync(h->flag, 0, sizeof(int), st), "lbm_set_K_field memset")) return rc;
+    if (int rc = cuda_check(launch_kfield(h, dev_K, st), "lbm_set_K_field launch")) return rc;
+    int bad = 0;
+    if (int rc = cuda_check(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "lbm_set_K_field copy"))
+        return rc;
+    if (int rc = cuda_check(cudaStreamSynchronize(st), "lbm_set_K_field sync")) return rc;
+    if (bad) return fail(LBM_EINVAL, std::to_string(bad) + " nodes have a tensor that is not positive definite");
+    h->kfield_set = 1;
+    return LBM_OK;
+}
+
+int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream)
+{
+    if (int rc = check_ready(h)) return rc;
+    if (!dev_phi) return fail(LBM_EINVAL, "null phi");
+    if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "phi must be LBM_F64 or LBM_F32");
+    if (int rc = cuda_check(launch_init(h, dev_phi, prec, (cudaStream_t)stream), "lbm_set_phi")) return rc;
+    h->phi_set = 1;
+    h->t = 0;
+    return LBM_OK;
+}
+
+int lbm_set_phi_host(lbm_handle h, const void *host_phi, int prec, void *stream)
+{
+    if (int rc = check_ready(h)) return rc;
+    if (!host_phi) return fail(LBM_EINVAL, "null phi");
+    if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "phi must be LBM_F64 or LBM_F32");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)h->d.nx * h->d.ny * (prec == LBM_F64 ? 8 : 4);
+    if (int rc = cuda_check(cudaMemcpyAsync(h->staging, host_phi, n, cudaMemcpyHostToDevice, st), "lbm_set_phi_host copy"))
+        return rc;
+    return lbm_set_phi(h, h->staging, prec, stream);
+}
+
+int lbm_step(lbm_handle h, int nsteps, void *stream)
+{
+    if (int rc = check_ready(h)) return rc;
+    if (!h->phi_set) return fail(LBM_EINVAL, "lbm_set_phi has not been called");
+    if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
+    cudaStream_t st = (cudaStream_t)stream;
+    int done = 0;
+    if (h->d.steps_per_pass == 2) {
+        for (; done + 2 <= nsteps; done += 2) {
+            if (int rc = cuda_check(launch_step2(h, h->cur, st), "lbm_step (two steps per pass)")) return rc;
+            h->cur ^= 1;
+            h->t += 2;
+        }
+    }
+    for (; done < nsteps; ++done) {
+        if (int rc = cuda_check(launch_step(h, h->cur, st), "lbm_step")) return rc;
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_phi(lbm_handle h, void *dev_out, int prec, void *stream)
+{
+    if (int rc = check_ready(h)) return rc;
+    if (!h->phi_set) return fail(LBM_EINVAL, "lbm_set_phi has not been called");
+    if (!dev_out) return fail(LBM_EINVAL, "null output");
+    if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "output must be LBM_F64 or LBM_F32");
+    return cuda_check(launch_get_phi(h, dev_out, prec, (cudaStream_t)stream), "lbm_get_phi");
+}
+
+int lbm_get_phi_host(lbm_handle h, void *host_out, int prec, void *stream)
+{
+    if (!host_out) return fail(LBM_EINVAL, "null output");
+    if (int rc = lbm_get_phi(h, h ? h->staging : nullptr, prec, stream)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)h->d.nx * h->d.ny * (prec == LBM_F64 ? 8 : 4);
+    if (int rc = cuda_check(cudaMemcpyAsync(host_out, h->staging, n, cudaMemcpyDeviceToHost, st), "lbm_get_phi_host copy"))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(st), "lbm_get_phi_host sync");
+}
+
+int lbm_reduce(lbm_handle h, const double *dev_ref, double *dev_out, void *stream)
+{
+    if (int rc = check_ready(h)) return rc;
+    if (!h->phi_set) return fail(LBM_EINVAL, "lbm_set_phi has not been called");
+    if (!dev_out) return fail(LBM_EINVAL, "null output");
+    return cuda_check(launch_reduce(h, dev_ref, dev_out, (cudaStream_t)stream), "lbm_reduce");
+}
+
+int lbm_state_bytes(lbm_handle h, size_t *bytes)
+{
+    if (check_handle(h)) return LBM_EINVAL;
+    if (!bytes) return fail(LBM_EINVAL, "null size pointer");
+    *bytes = h->L.pop_bytes + h->L.phi_bytes;
+    return LBM_OK;
+}
+
+int lbm_save(lbm_handle h, void *dev_dst, void *stream)
+{
+    if (check_handle(h)) return LBM_EINVAL;
+    if (!dev_dst) return fail(LBM_EINVAL, "null destination");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(cudaMemcpyAsync(dev_dst, h->pop[h->cur], h->L.pop_bytes, cudaMemcpyDeviceToDevice, st), "lbm_save"))
+        return rc;
+    if (h->L.phi_bytes)
+        return cuda_check(cudaMemcpyAsync((char *)dev_dst + h->L.pop_bytes, h->phi[h->cur], h->L.phi_bytes,
+                                          cudaMemcpyDeviceToDevice, st), "lbm_save phi");
+    return LBM_OK;
+}
+
+int lbm_load(lbm_handle h, const void *dev_src, void *stream)
+{
+    if (check_handle(h)) return LBM_EINVAL;
+    if (!dev_src) return fail(LBM_EINVAL, "null source");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(cudaMemcpyAsync(h->pop[h->cur], dev_src, h->L.pop_bytes, cudaMemcpyDeviceToDevice, st), "lbm_load"))
+        return rc;
+    if (h->L.phi_bytes)
+        if (int rc = cuda_check(cudaMemcpyAsync(h->phi[h->cur], (const char *)dev_src + h->L.pop_bytes, h->L.phi_bytes,
+                                                cudaMemcpyDeviceToDevice, st), "lbm_load phi"))
+            return rc;
+    h->phi_set = 1;
+    return LBM_OK;
+}
+
+}  // extern "C"

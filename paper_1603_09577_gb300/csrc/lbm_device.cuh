@@ -1,0 +1,220 @@
+// lbm_device.cuh -- device-side building blocks of the fused D2Q9 MRT
+// stream-collide update (arXiv:1603.09577, Sec. 2): lattice constants (Eq. 5),
+// storage traits for the three population precisions, the per-cell collision
+// in moment space (Eq. 15-17, 34-35) and the anti-bounce-back wall term.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// ---- D2Q9 lattice (Eq. 5): rest, E, N, W, S, NE, NW, SW, SE -------------
+__host__ __device__ constexpr int cx(int k) { return k == 1 || k == 5 || k == 8 ? 1 : (k == 3 || k == 6 || k == 7 ? -1 : 0); }
+__host__ __device__ constexpr int cy(int k) { return k == 2 || k == 5 || k == 6 ? 1 : (k == 4 || k == 7 || k == 8 ? -1 : 0); }
+__host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : (k <= 4 ? (k + 1) % 4 + 1 : (k + 1) % 4 + 5); }
+template <class C>
+__host__ __device__ constexpr C wgt(int k) { return k == 0 ? C(4) / C(9) : (k <= 4 ? C(1) / C(9) : C(1) / C(36)); }
+
+// ---- kernel parameters (passed by value) -----------------------------------
+// Relaxation rates, flux and source coefficients in the compute type C.
+template <class C>
+struct Params {
+    int nx, ny;
+    long long pitch;        // elements per row of a population plane
+    long long plane;        // elements per plane (ny * pitch)
+    int abb_x, abb_y;       // 1: anti-bounce-back walls on that axis
+    C s1, s2, s4, s6, s7, s8;
+    C h1, h2, h4, h6;       // 1 - s_i / 2
+    C A3, A35, A5;          // constant relaxation block (Eq. 17, 26)
+    C ux, uy, uxx, uxy, uyy;
+    C r0, r1, half_r0, inv_den, inv_post;   // inv_den = 1/(1 - r1/2), inv_post = 1/(1 + r1/2)
+    int has_src;
+    C phi_wall[4];          // west, east, south, north
+    const C *Afield;        // per-cell blocks: 3 planes (A3, A35, A5) or null
+};
+
+// ---- storage traits ---------------------------------------------------------
+// Populations are structure-of-arrays: plane k at base + k * plane, element
+// (x, y) at y * pitch + x. LBM_BF16S keeps g_k = fbar_k - w_k phi in bf16 and
+// phi in a float plane of the same shape.
+template <int PREC> struct Store;
+
+template <> struct Store<LBM_F64> {
+    using T = double;
+    using C = double;
+    static constexpr bool kPhiPlane = false;
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
+    __device__ static __forceinline__ void st(T *__restrict__ f, long long i, C v, C, C) { __stcs(f + i, v); }
+};
+
+template <> struct Store<LBM_F32> {
+    using T = float;
+    using C = float;
+    static constexpr bool kPhiPlane = false;
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
+    __device__ static __forceinline__ void st(T *__restrict__ f, long long i, C v, C, C) { __stcs(f + i, v); }
+};
+
+template <> struct Store<LBM_BF16S> {
+    using T = __nv_bfloat16;
+    using C = float;
+    static constexpr bool kPhiPlane = true;
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *__restrict__ phi, C w)
+    {
+        return fmaf(w, __ldg(phi + i), __bfloat162float(f[i]));
+    }
+    __device__ static __forceinline__ void st(T *__restrict__ f, long long i, C v, C w, C phi)
+    {
+        f[i] = __float2bfloat16_rn(fmaf(-w, phi, v));
+    }
+};
+
+// ---- coefficient families (Eq. 1, Eq. 7) ------------------------------------
+// Second-moment tensor Cbar = C(phi) + d c_s^2 g(phi) I, flux B and B'.
+template <class C, int CONV, int DIFF>
+struct Coef {
+    C Bx, By, Bpx, Bpy, Cbxx, Cbxy, Cbyy;
+    __device__ __forceinline__ Coef(const Params<C> &p, C phi)
+    {
+        C Cxx, Cxy, Cyy;
+        if (CONV == 0) {
+            Bx = p.ux * phi; By = p.uy * phi;
+            Bpx = p.ux; Bpy = p.uy;
+            Cxx = p.uxx * phi; Cxy = p.uxy * phi; Cyy = p.uyy * phi;
+        } else {
+            const C phi2 = phi * phi;
+            Bx = C(0.5) * p.ux * phi2; By = C(0.5) * p.uy * phi2;
+            Bpx = p.ux * phi; Bpy = p.uy * phi;
+            const C p3 = phi2 * phi * (C(1) / C(3));
+            Cxx = p.uxx * p3; Cxy = p.uxy * p3; Cyy = p.uyy * p3;
+        }
+        C g;
+        if (DIFF == 0) g = phi;
+        else if (DIFF == 1) g = phi + C(0.5) * phi * phi;
+        else g = phi + phi * phi * phi * (C(1) / C(3));
+        const C cg = g * (C(1) / C(3));      // d c_s^2 g with d = 1
+        Cbxx = Cxx + cg; Cbyy = Cyy + cg; Cbxy = Cxy;
+    }
+};
+
+// Even part of the equilibrium at a wall value (anti-bounce-back source term):
+// feq_k(phi_w) + feq_opp(k)(phi_w) = 2 w_k [phi_w + Q : (c c - c_s^2 I) / (2 c_s^4)],
+// Q = Cbar(phi_w) - c_s^2 phi_w I.
+template <class C, int CONV, int DIFF>
+__device__ __forceinline__ C wall_term(const Params<C> &p, int k, C phiw)
+{
+    Coef<C, CONV, DIFF> q(p, phiw);
+    const C third = C(1) / C(3);
+    const C Qxx = q.Cbxx - third * phiw, Qyy = q.Cbyy - third * phiw, Qxy = q.Cbxy;
+    const C ex = C(cx(k) * cx(k)) - third, ey = C(cy(k) * cy(k)) - third;
+    const C qc = Qxx * ex + C(2 * cx(k) * cy(k)) * Qxy + Qyy * ey;
+    return C(2) * wgt<C>(k) * (phiw + C(4.5) * qc);
+}
+
+// ---- the collision (Eq. 34 in moment space) ---------------------------------
+// In: pre-collision shifted populations f (pulled). Out: f overwritten with the
+// post-collision fbar*, phi = Eq. 35. A3, A35, A5: relaxation block of the cell.
+template <class C, int CONV, int DIFF>
+__device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35, C A5, C &phi_out)
+{
+    // moments m = M0 f (Eq. 15): rho, e, eps, jx, qx, jy, qy, pxx, pxy
+    const C ax = f[1] + f[3], ay = f[2] + f[4];
+    const C axis = ax + ay;
+    const C dg = (f[5] + f[7]) + (f[6] + f[8]);
+    const C rho = f[0] + axis + dg;
+    const C e = C(2) * dg - axis - C(4) * f[0];
+    const C eps = C(4) * f[0] - C(2) * axis + dg;
+    const C dx1 = f[1] - f[3], dy1 = f[2] - f[4];
+    const C dxd = (f[5] - f[7]) + (f[8] - f[6]);
+    const C dyd = (f[5] - f[7]) + (f[6] - f[8]);
+    const C jx = dx1 + dxd, qx = dxd - C(2) * dx1;
+    const C jy = dy1 + dyd, qy = dyd - C(2) * dy1;
+    const C pxx = ax - ay;
+    const C pxy = (f[5] + f[7]) - (f[6] + f[8]);
+
+    // Eq. 35 for R = r0 + r1 phi
+    const C phi = (rho + p.half_r0) * p.inv_den;
+    phi_out = phi;
+    const Coef<C, CONV, DIFF> q(p, phi);
+
+    // equilibrium moments (Eq. 16 with c = 1)
+    const C C2 = q.Cbxx + q.Cbyy;
+    const C e_eq = C(3) * C2 - C(4) * phi;
+    const C eps_eq = C(3) * phi - C(3) * C2;
+    const C pxx_eq = q.Cbxx - q.Cbyy;
+
+    // relaxation (Eq. 17) plus (I - S/2) M0 R (Eq. 34), M0 R = (R, -2R, R,
+    // Bt_x R, -Bt_x R, Bt_y R, -Bt_y R, 0, 0) with Bt = B' (Scheme B)
+    C es = e - p.s1 * (e - e_eq);
+    C epss = eps - p.s2 * (eps - eps_eq);
+    C qxs = qx - p.s4 * (qx + q.Bx);
+    C qys = qy - p.s6 * (qy + q.By);
+    const C pxxs = pxx - p.s7 * (pxx - pxx_eq);
+    const C pxys = pxy - p.s8 * (pxy - q.Cbxy);
+    const C d3 = jx - q.Bx, d5 = jy - q.By;
+    C jxs = jx - (A3 * d3 + A35 * d5);
+    C jys = jy - (A35 * d3 + A5 * d5);
+    C rhos = phi;
+    if (p.has_src) {
+        const C R = p.r0 + p.r1 * phi;
+        const C sx = q.Bpx * R, sy = q.Bpy * R;
+        rhos += C(0.5) * R;                      // rho* = phi + R/2 for every s0
+        es -= C(2) * p.h1 * R;
+        epss += p.h2 * R;
+        qxs -= p.h4 * sx;
+        qys -= p.h6 * sy;
+        jxs += sx - C(0.5) * (A3 * sx + A35 * sy);
+        jys += sy - C(0.5) * (A35 * sx + A5 * sy);
+    }
+
+    // back-transform f* = M0^-1 m* = M0^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m*
+    const C r = rhos * (C(1) / C(9));
+    const C ee = es * (C(1) / C(36));
+    const C pp = epss * (C(1) / C(36));
+    const C jxn = jxs * (C(1) / C(6)), qxn = qxs * (C(1) / C(12));
+    const C jyn = jys * (C(1) / C(6)), qyn = qys * (C(1) / C(12));
+    const C pxxn = pxxs * C(0.25), pxyn = pxys * C(0.25);
+    f[0] = r - C(4) * ee + C(4) * pp;
+    const C base_a = r - ee - C(2) * pp;
+    const C X1 = jxn - C(2) * qxn, Y1 = jyn - C(2) * qyn;
+    f[1] = base_a + X1 + pxxn;
+    f[3] = base_a - X1 + pxxn;
+    f[2] = base_a + Y1 - pxxn;
+    f[4] = base_a - Y1 - pxxn;
+    const C base_d = r + C(2) * ee + pp;
+    const C X2 = jxn + qxn, Y2 = jyn + qyn;
+    f[5] = base_d + X2 + Y2 + pxyn;
+    f[6] = base_d - X2 + Y2 - pxyn;
+    f[7] = base_d - X2 - Y2 + pxyn;
+    f[8] = base_d + X2 - Y2 - pxyn;
+}
+
+// Equilibrium populations of Eq. 3 (used only at initialisation).
+template <class C, int CONV, int DIFF>
+__device__ __forceinline__ void equilibrium(const Params<C> &p, C phi, C feq[9])
+{
+    const Coef<C, CONV, DIFF> q(p, phi);
+    const C third = C(1) / C(3);
+    const C Qxx = q.Cbxx - third * phi, Qyy = q.Cbyy - third * phi, Qxy = q.Cbxy;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const C cB = C(cx(k)) * q.Bx + C(cy(k)) * q.By;
+        const C qc = Qxx * (C(cx(k) * cx(k)) - third) + C(2 * cx(k) * cy(k)) * Qxy + Qyy * (C(cy(k) * cy(k)) - third);
+        feq[k] = wgt<C>(k) * (phi + C(3) * cB + C(4.5) * qc);
+    }
+}
+
+// Source populations of Eq. 9 with Btilde = B'.
+template <class C, int CONV, int DIFF>
+__device__ __forceinline__ void source_pop(const Params<C> &p, C phi, C R, C Rk[9])
+{
+    const Coef<C, CONV, DIFF> q(p, phi);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rk[k] = wgt<C>(k) * (C(1) + C(3) * (C(cx(k)) * q.Bpx + C(cy(k)) * q.Bpy)) * R;
+}
+
+}  // namespace lbm

@@ -1,0 +1,65 @@
+// lbm_internal.h -- host-side solver state, workspace layout and the kernel
+// launchers shared by the translation units of liblbm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <string>
+
+#include "lbm.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kReduceBlocks = 1024;     // fixed: deterministic reduction order
+constexpr int kReduceThreads = 256;
+constexpr int kPitchAlign = 64;         // row pitch in elements (>= 128 B rows)
+
+struct Layout {
+    long long pitch = 0, plane = 0;
+    size_t esize = 0, csize = 0;
+    size_t off_pop[2] = {0, 0}, off_phi[2] = {0, 0};
+    size_t off_afield = 0, off_staging = 0, off_partials = 0, off_flag = 0;
+    size_t pop_bytes = 0, phi_bytes = 0, total = 0;
+};
+
+int make_layout(const lbm_desc *d, Layout *L);
+
+}  // namespace lbm
+
+struct lbm_solver {
+    lbm_desc d;
+    lbm_coeffs c;
+    lbm::Layout L;
+    int coeffs_set = 0, phi_set = 0, kfield_set = 0;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *pop[2] = {nullptr, nullptr};
+    float *phi[2] = {nullptr, nullptr};
+    void *afield = nullptr;
+    void *staging = nullptr;
+    double *partials = nullptr;
+    int *flag = nullptr;
+    int cur = 0;
+    long long t = 0;
+};
+
+namespace lbm {
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_check(cudaError_t e, const char *what);
+
+// kernel parameters in the compute type of the solver
+template <class C>
+Params<C> make_params(const lbm_solver *s);
+
+cudaError_t launch_init(const lbm_solver *s, const void *phi, int in_prec, cudaStream_t st);
+cudaError_t launch_step(const lbm_solver *s, int src, cudaStream_t st);
+cudaError_t launch_step2(const lbm_solver *s, int src, cudaStream_t st);
+cudaError_t launch_get_phi(const lbm_solver *s, void *out, int out_prec, cudaStream_t st);
+cudaError_t launch_reduce(const lbm_solver *s, const double *ref, double *out, cudaStream_t st);
+cudaError_t launch_kfield(const lbm_solver *s, const double *K, cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,144 @@
+"""Python front end of one lattice: torch provides device memory and streams,
+every computation runs in liblbm's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as C
+
+BC = {"periodic": C.LBM_PERIODIC, "abb": C.LBM_ABB, 0: C.LBM_PERIODIC, 1: C.LBM_ABB}
+REDUCE_KEYS = ("sum", "abs_err", "abs_ref", "sq_err", "sq_ref", "max_abs", "nonfinite", "sum_sq")
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return C.LBM_F64
+    if t.dtype == torch.float32:
+        return C.LBM_F32
+    raise TypeError("phi must be float64 or float32")
+
+
+class Solver:
+    """One D2Q9 lattice of nx x ny nodes (see include/lbm.h for the contract).
+
+    prec: "f64", "f32" or "bf16s"; bc: (x, y) boundary kinds "periodic"/"abb";
+    phi_wall: (west, east, south, north) Dirichlet values.
+    """
+
+    def __init__(self, nx: int, ny: int, prec: str = "f32", bc=("periodic", "periodic"),
+                 phi_wall=(0.0, 0.0, 0.0, 0.0), steps_per_pass: int = 1, per_cell_K: bool = False,
+                 device=None):
+        self.lib = C.lib()
+        self.nx, self.ny, self.prec = int(nx), int(ny), prec
+        self.device = torch.device(device if device is not None else "cuda")
+        d = C.Desc()
+        d.nx, d.ny, d.prec = self.nx, self.ny, C.PREC[prec]
+        d.bc_x, d.bc_y = BC[bc[0]], BC[bc[1]]
+        d.phi_wall[:] = [float(v) for v in phi_wall]
+        d.steps_per_pass = int(steps_per_pass)
+        d.per_cell_K = int(bool(per_cell_K))
+        self.desc = d
+        size = ctypes.c_size_t()
+        C.check(self.lib.lbm_workspace_size(ctypes.byref(d), ctypes.byref(size)))
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self.h = ctypes.c_void_p()
+        C.check(self.lib.lbm_create(ctypes.byref(self.h), ctypes.byref(d), _ptr(self.workspace), size.value))
+        self._out = torch.zeros(8, dtype=torch.float64, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.lib.lbm_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    # -- set-up ------------------------------------------------------------
+    def set_coeffs(self, conv: int = 0, u=(0.0, 0.0), diff: int = 0, K=(0.0, 0.0, 0.0),
+                   s=(1.0, 1.2, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1), r0: float = 0.0, r1: float = 0.0):
+        c = C.Coeffs()
+        c.conv, c.diff = int(conv), int(diff)
+        c.u[:] = [float(v) for v in u]
+        c.K[:] = [float(v) for v in K]
+        c.s[:] = [float(v) for v in s]
+        c.r0, c.r1 = float(r0), float(r1)
+        C.check(self.lib.lbm_set_coeffs(self.h, ctypes.byref(c)))
+        self.coeffs = c
+        return self
+
+    def set_K_field(self, K: torch.Tensor, stream=None):
+        K = K.to(device=self.device, dtype=torch.float64).contiguous()
+        assert K.shape == (3, self.ny, self.nx)
+        self._K = K
+        C.check(self.lib.lbm_set_K_field(self.h, _ptr(K), _stream(stream)))
+        return self
+
+    def set_phi(self, phi0: torch.Tensor, stream=None):
+        assert phi0.shape == (self.ny, self.nx) and phi0.is_cuda and phi0.is_contiguous()
+        C.check(self.lib.lbm_set_phi(self.h, _ptr(phi0), _prec_of(phi0), _stream(stream)))
+        return self
+
+    def set_phi_host(self, phi0: torch.Tensor, stream=None):
+        assert phi0.shape == (self.ny, self.nx) and not phi0.is_cuda and phi0.is_contiguous()
+        C.check(self.lib.lbm_set_phi_host(self.h, _ptr(phi0), _prec_of(phi0), _stream(stream)))
+        return self
+
+    # -- time stepping -------------------------------------------------------
+    def step(self, n: int = 1, stream=None):
+        C.check(self.lib.lbm_step(self.h, int(n), _stream(stream)))
+        return self
+
+    # -- read-out ------------------------------------------------------------
+    def phi(self, dtype=torch.float64, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.ny, self.nx), dtype=dtype, device=self.device)
+        C.check(self.lib.lbm_get_phi(self.h, _ptr(out), _prec_of(out), _stream(stream)))
+        return out
+
+    def phi_host(self, out: torch.Tensor, stream=None) -> torch.Tensor:
+        assert not out.is_cuda and out.shape == (self.ny, self.nx) and out.is_contiguous()
+        C.check(self.lib.lbm_get_phi_host(self.h, _ptr(out), _prec_of(out), _stream(stream)))
+        return out
+
+    def reduce_async(self, ref: torch.Tensor | None = None, out: torch.Tensor | None = None, stream=None):
+        out = self._out if out is None else out
+        if ref is not None:
+            ref = ref.to(device=self.device, dtype=torch.float64).contiguous()
+            self._ref = ref
+        C.check(self.lib.lbm_reduce(self.h, _ptr(ref) if ref is not None else None, _ptr(out), _stream(stream)))
+        return out
+
+    def reduce(self, ref: torch.Tensor | None = None) -> dict:
+        v = self.reduce_async(ref).cpu().tolist()
+        return dict(zip(REDUCE_KEYS, v))
+
+    # -- checkpoints -----------------------------------------------------------
+    def state_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        C.check(self.lib.lbm_state_bytes(self.h, ctypes.byref(n)))
+        return n.value
+
+    def save(self, dst: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if dst is None:
+            dst = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        C.check(self.lib.lbm_save(self.h, _ptr(dst), _stream(stream)))
+        return dst
+
+    def load(self, src: torch.Tensor, stream=None):
+        assert src.numel() * src.element_size() >= self.state_bytes()
+        C.check(self.lib.lbm_load(self.h, _ptr(src), _stream(stream)))
+        return self

@@ -1,0 +1,144 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol that
+include/*.h declares, and validates its arguments on the host (no device work)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1603_09577_gb300 import _lib as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:int|const char \*|void)\s*\**\s*(lbm_\w+)\s*\(", txt, flags=re.M))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = C.lib()
+    names = declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(C.declared_symbols()) <= set(names) | {"lbm_last_error"}
+
+
+def desc(**kw):
+    d = C.Desc()
+    d.nx, d.ny, d.prec, d.bc_x, d.bc_y = 16, 12, C.LBM_F32, 0, 0
+    d.steps_per_pass, d.per_cell_K = 1, 0
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def ws_size(d):
+    n = ctypes.c_size_t()
+    rc = C.lib().lbm_workspace_size(ctypes.byref(d), ctypes.byref(n))
+    return rc, n.value
+
+
+def test_workspace_size_and_layout():
+    rc, n32 = ws_size(desc())
+    assert rc == 0
+    # two buffers of 9 planes, rows padded to 64 elements
+    assert n32 >= 2 * 9 * 12 * 64 * 4
+    rc, n64 = ws_size(desc(prec=C.LBM_F64))
+    assert rc == 0 and n64 > n32
+    rc, nb = ws_size(desc(prec=C.LBM_BF16S))
+    assert rc == 0 and nb < n32
+    rc, nk = ws_size(desc(per_cell_K=1))
+    assert rc == 0 and nk > n32
+
+
+@pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(prec=7), dict(bc_x=3), dict(steps_per_pass=3)])
+def test_invalid_descriptions_rejected(bad):
+    rc, _ = ws_size(desc(**bad))
+    assert rc == C.LBM_EINVAL
+    assert C.lib().lbm_last_error()
+
+
+class FakeWorkspace:
+    """A host buffer that stands in for the device workspace: lbm_create only
+    records pointers, and the tests below make no device calls."""
+
+    def __init__(self, n):
+        self.buf = ctypes.create_string_buffer(n + 512)
+        a = ctypes.addressof(self.buf)
+        self.ptr = (a + 255) & ~255
+
+
+def make(d=None):
+    d = d or desc()
+    rc, n = ws_size(d)
+    ws = FakeWorkspace(n)
+    h = ctypes.c_void_p()
+    assert C.lib().lbm_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(ws.ptr), n) == 0
+    return h, ws
+
+
+def coeffs(**kw):
+    c = C.Coeffs()
+    c.conv, c.diff = 0, 0
+    c.u[:] = [0.05, 0.02]
+    c.K[:] = [0.01, 0.0, 0.01]
+    c.s[:] = [1.0, 1.2, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1]
+    for k, v in kw.items():
+        if k in ("u", "K", "s"):
+            getattr(c, k)[:] = v
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def test_create_rejects_bad_workspace():
+    d = desc()
+    rc, n = ws_size(d)
+    ws = FakeWorkspace(n)
+    h = ctypes.c_void_p()
+    L = C.lib()
+    assert L.lbm_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(ws.ptr + 8), n) == C.LBM_EINVAL
+    assert L.lbm_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(ws.ptr), n - 1) == C.LBM_EINVAL
+    assert L.lbm_create(ctypes.byref(h), ctypes.byref(d), None, n) == C.LBM_EINVAL
+
+
+@pytest.mark.parametrize("bad", [
+    dict(K=[0.01, 0.02, 0.01]),         # not positive definite
+    dict(K=[-0.01, 0.0, 0.01]),
+    dict(s=[1.0, 2.5, 1.2, 0, 1, 0, 1, 1.1, 1.1]),
+    dict(s=[1.0, 1.2, 0.0, 0, 1, 0, 1, 1.1, 1.1]),
+    dict(conv=5), dict(diff=-1), dict(r1=2.0), dict(u=[float("nan"), 0.0])])
+def test_coefficient_validation(bad):
+    h, ws = make()
+    L = C.lib()
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(**bad))) == C.LBM_EINVAL
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs())) == 0
+    L.lbm_destroy(h)
+
+
+def test_calls_in_wrong_order_are_rejected_before_any_device_work():
+    h, ws = make()
+    L = C.lib()
+    assert L.lbm_step(h, 1, None) == C.LBM_EINVAL          # no coefficients
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs())) == 0
+    assert L.lbm_step(h, 1, None) == C.LBM_EINVAL          # no initial phi
+    assert L.lbm_set_phi(h, None, C.LBM_F64, None) == C.LBM_EINVAL
+    assert L.lbm_step(None, 1, None) == C.LBM_EINVAL
+    assert b"lbm_set_phi" in L.lbm_last_error() or L.lbm_last_error()
+    L.lbm_destroy(h)
+
+
+def test_per_cell_field_required():
+    h, ws = make(desc(per_cell_K=1))
+    L = C.lib()
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(K=[0.0, 0.0, 0.0]))) == 0
+    assert L.lbm_set_phi(h, ctypes.c_void_p(16), C.LBM_F64, None) == C.LBM_EINVAL
+    assert b"K_field" in L.lbm_last_error()
+    L.lbm_destroy(h)

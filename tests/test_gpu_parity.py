@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (relative L2 of phi against the oracle): FP64 <= 1e-12, FP32 <= 1e-5,
+BF16-shifted storage <= 2e-3. Sizes span several 32 x 8 thread blocks and
+ragged tails; every coefficient family, both wall kinds, sources and per-cell
+tensors are covered. Full-size workloads are compared on all elements after a
+bounded number of steps and, at the full step count, on a reduced grid.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from paper_1603_09577_gb300 import LBMError, Solver
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16s": 2e-3}
+BCN = {0: "periodic", 1: "abb"}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_gpu(prec, nx, ny, phi0, steps, bc=(0, 0), walls=(0, 0, 0, 0), Kfield=None, spp=1, **coef):
+    s = Solver(nx, ny, prec=prec, bc=(BCN[bc[0]], BCN[bc[1]]), phi_wall=walls, steps_per_pass=spp,
+               per_cell_K=Kfield is not None)
+    s.set_coeffs(s=W.s9(), **coef)
+    if Kfield is not None:
+        s.set_K_field(torch.from_numpy(Kfield).cuda())
+    s.set_phi(torch.from_numpy(np.ascontiguousarray(phi0)).cuda())
+    s.step(steps)
+    return s.phi().cpu().numpy(), s
+
+
+_ORACLE_CACHE = {}
+
+
+def run_oracle(nx, ny, phi0, steps, bc=(0, 0), walls=(0, 0, 0, 0), Kfield=None, **coef):
+    key = (nx, ny, steps, tuple(bc), tuple(walls), tuple(sorted(coef.items())),
+           hash(np.ascontiguousarray(phi0).tobytes()), None if Kfield is None else hash(Kfield.tobytes()))
+    if key not in _ORACLE_CACHE:
+        sp = O.Spec(nx=nx, ny=ny, bc_x=bc[0], bc_y=bc[1], phi_wall=walls, Kfield=Kfield, s=W.s9(), **coef)
+        _ORACLE_CACHE[key] = O.run(sp, phi0, steps)
+    return _ORACLE_CACHE[key]
+
+
+CASES = [
+    # nx, ny, bc, conv, diff, u, K, r0, r1
+    (37, 29, (0, 0), 0, 0, (0.05, 0.02), (0.01, 0.0, 0.01), 0.0, 0.0),
+    (70, 41, (1, 1), 0, 2, (0.0, 0.0), (0.02, 0.008, 0.01), 0.0, -0.1),
+    (64, 24, (0, 1), 1, 0, (0.3, 0.2), (0.05, 0.0, 0.05), 0.0, 0.0),
+    (33, 65, (1, 0), 1, 2, (0.1, -0.2), (0.03, -0.01, 0.02), 0.01, -0.2),
+    (48, 48, (0, 0), 0, 1, (-0.08, 0.06), (0.004, 0.001, 0.006), 0.0, 0.0),
+    (40, 31, (1, 1), 1, 1, (0.05, 0.05), (0.1, 0.02, 0.08), 0.002, 0.0),
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16s"])
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}-c{c[3]}d{c[4]}" for c in CASES])
+def test_parity_families_and_walls(prec, case):
+    nx, ny, bc, conv, diff, u, K, r0, r1 = case
+    rng = np.random.default_rng(nx * 131 + ny)
+    phi0 = W.jacobi_smooth(rng.uniform(0.05, 0.95, (ny, nx)), 2)
+    walls = (0.3, 0.7, 0.1, 0.5) if bc != (0, 0) else (0, 0, 0, 0)
+    coef = dict(conv=conv, u=u, diff=diff, K=K, r0=r0, r1=r1)
+    ref = run_oracle(nx, ny, phi0, 60, bc, walls, **coef)
+    got, _ = run_gpu(prec, nx, ny, phi0, 60, bc, walls, **coef)
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_parity_per_cell_tensor(prec):
+    nx, ny = 45, 38
+    Kf, phi0, _ = W.adjoint_inputs(nx, seed=7, ny=ny)
+    coef = dict(conv=0, u=(0.03, 0.0), diff=0, K=(0.0, 0.0, 0.0))
+    ref = run_oracle(nx, ny, phi0, 80, Kfield=Kf, **coef)
+    got, _ = run_gpu(prec, nx, ny, phi0, 80, Kfield=Kf, **coef)
+    assert rel(got, ref) <= TOL[prec]
+
+
+def test_tiny_and_zero_steps():
+    phi0 = np.array([[0.1, 0.4], [0.8, 0.3]])
+    coef = dict(conv=1, u=(0.1, 0.2), diff=2, K=(0.02, 0.005, 0.03), r0=0.0, r1=-0.1)
+    for bc in [(0, 0), (1, 1), (1, 0)]:
+        walls = (0.2, 0.4, 0.6, 0.8)
+        ref = run_oracle(2, 2, phi0, 7, bc, walls, **coef)
+        got, _ = run_gpu("f64", 2, 2, phi0, 7, bc, walls, **coef)
+        assert rel(got, ref) <= 1e-12
+    got, _ = run_gpu("f64", 2, 2, phi0, 0, **coef)
+    assert np.abs(got - phi0).max() < 1e-15
+
+
+def test_gaussian_128_full_f64():
+    """The 128^2 isotropic Gaussian hill, all 1000 steps, FP64."""
+    p = W.params("gaussian_iso_128")
+    phi0 = W.phi0_gaussian()
+    coef = dict(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"])
+    ref = run_oracle(128, 128, phi0, p["steps"], **coef)
+    got, _ = run_gpu("f64", 128, 128, phi0, p["steps"], **coef)
+    assert rel(got, ref) <= 1e-12
+    got, _ = run_gpu("f32", 128, 128, phi0, p["steps"], **coef)
+    assert rel(got, ref) <= 1e-5
+
+
+def aniso_coef():
+    p = W.params("aniso_dirichlet_4096")
+    return dict(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"], r0=p["r0"], r1=p["r1"]), p
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16s"])
+def test_aniso_dirichlet_full_grid_short(prec):
+    """4096^2 with phi = 0 walls, every element, after 12 steps."""
+    coef, p = aniso_coef()
+    phi0 = W.phi0_aniso(4096, seed=3)
+    ref = run_oracle(4096, 4096, phi0, 12, p["bc"], p["phi_wall"], **coef)
+    got, _ = run_gpu(prec, 4096, 4096, phi0, 12, p["bc"], p["phi_wall"], **coef)
+    assert rel(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16s"])
+def test_aniso_dirichlet_full_steps_reduced_grid(prec):
+    """All 2000 steps of the anisotropic Dirichlet workload on a 512^2 grid."""
+    coef, p = aniso_coef()
+    phi0 = W.phi0_aniso(512, seed=3)
+    ref = run_oracle(512, 512, phi0, p["steps"], p["bc"], p["phi_wall"], **coef)
+    got, _ = run_gpu(prec, 512, 512, phi0, p["steps"], p["bc"], p["phi_wall"], **coef)
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
+def test_aniso_dirichlet_full_size_properties():
+    """Full 4096^2 x 2000 steps in FP32: finite, 0 <= phi <= 1, decaying mass,
+    and within the FP32 bar of the FP64 CUDA path (itself pinned to the oracle)."""
+    coef, p = aniso_coef()
+    phi0 = W.phi0_aniso(4096, seed=3)
+    f32, s32 = run_gpu("f32", 4096, 4096, phi0, p["steps"], p["bc"], p["phi_wall"], **coef)
+    r = s32.reduce()
+    assert r["nonfinite"] == 0 and f32.min() >= -1e-6 and f32.max() <= 1.0
+    assert r["sum"] < phi0.sum()
+    f64, _ = run_gpu("f64", 4096, 4096, phi0, p["steps"], p["bc"], p["phi_wall"], **coef)
+    assert rel(f32, f64) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16s"])
+def test_burgers_short(prec):
+    p = W.params("burgers_1024")
+    phi0 = W.phi0_burgers()
+    coef = dict(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"])
+    ref = run_oracle(1024, 1024, phi0, 50, **coef)
+    got, _ = run_gpu(prec, 1024, 1024, phi0, 50, **coef)
+    assert rel(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16s"])
+def test_burgers_full_steps_reduced_grid(prec):
+    """All 5000 steps of the Burgers workload on 256^2 (same scaling, K = 0.005 n)."""
+    p = W.params("burgers_1024")
+    n = 256
+    phi0 = W.phi0_burgers(n)
+    coef = dict(conv=p["conv"], u=p["u"], diff=p["diff"], K=(0.005 * n, 0.0, 0.005 * n))
+    ref = run_oracle(n, n, phi0, p["steps"], **coef)
+    got, _ = run_gpu(prec, n, n, phi0, p["steps"], **coef)
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
+def test_reductions_match_numpy():
+    nx, ny = 97, 61
+    rng = np.random.default_rng(3)
+    phi0 = rng.uniform(0, 1, (ny, nx))
+    ref_field = rng.uniform(0, 1, (ny, nx))
+    got, s = run_gpu("f64", nx, ny, phi0, 5, (1, 0), (0.2, 0.3, 0, 0), conv=0, u=(0.05, 0.0), diff=1,
+                     K=(0.02, 0.0, 0.03), r0=0.01, r1=-0.05)
+    r = s.reduce(torch.from_numpy(ref_field))
+    d = got - ref_field
+    assert abs(r["sum"] - got.sum()) <= 1e-12 * abs(got.sum())
+    assert abs(r["abs_err"] - np.abs(d).sum()) <= 1e-12 * np.abs(d).sum()
+    assert abs(r["abs_ref"] - np.abs(ref_field).sum()) <= 1e-12 * np.abs(ref_field).sum()
+    assert abs(r["sq_err"] - (d * d).sum()) <= 1e-12 * (d * d).sum()
+    assert abs(r["max_abs"] - np.abs(got).max()) <= 1e-15
+    assert r["nonfinite"] == 0
+    assert abs(r["sum_sq"] - (got * got).sum()) <= 1e-12 * (got * got).sum()
+    # deterministic: identical bits on a repeat
+    assert s.reduce(torch.from_numpy(ref_field)) == r
+
+
+def test_save_load_roundtrip_and_host_path():
+    nx, ny = 50, 34
+    phi0 = W.phi0_aniso(nx, seed=4, ny=ny)
+    coef = dict(conv=0, u=(0.04, 0.01), diff=2, K=(0.02, 0.008, 0.01), r1=-0.1)
+    for prec in ("f32", "bf16s"):
+        s = Solver(nx, ny, prec=prec, bc=("abb", "abb"))
+        s.set_coeffs(s=W.s9(), **coef)
+        host = torch.from_numpy(phi0).pin_memory()
+        s.set_phi_host(host)
+        s.step(10)
+        ck = s.save()
+        s.step(10)
+        a = s.phi().cpu()
+        s.load(ck)
+        s.step(10)
+        b = s.phi().cpu()
+        assert torch.equal(a, b)
+        out = torch.empty((ny, nx), dtype=torch.float64).pin_memory()
+        s.phi_host(out)
+        assert torch.equal(out, b)
+
+
+def test_invalid_tensor_field_reported():
+    nx, ny = 20, 10
+    Kf = np.zeros((3, ny, nx))
+    Kf[0] = Kf[2] = 0.01
+    Kf[1, 3, 4] = 0.05          # |Kxy| > sqrt(Kxx Kyy): not positive definite
+    s = Solver(nx, ny, prec="f32", per_cell_K=True)
+    s.set_coeffs(s=W.s9())
+    with pytest.raises(LBMError):
+        s.set_K_field(torch.from_numpy(Kf).cuda())
+
+
+def test_nonfinite_detected():
+    nx, ny = 32, 16
+    phi0 = np.full((ny, nx), 0.5)
+    phi0[3, 7] = np.nan
+    _, s = run_gpu("f32", nx, ny, phi0, 3, conv=0, u=(0.0, 0.0), diff=0, K=(0.01, 0.0, 0.01))
+    assert s.reduce()["nonfinite"] > 0
