@@ -45,8 +45,9 @@ extern "C" {
 #define LBM_F64 0           /* double populations, double arithmetic            */
 #define LBM_F32 1           /* float populations, float arithmetic              */
 #define LBM_BF16S 2         /* bf16 equilibrium-shifted deviations g_k =
-                               fbar*_k - w_k phi plus a float phi plane; float
-                               arithmetic                                        */
+                               fbar*_k - w_k phi plus a float shift plane h with
+                               sum_k (w_k h + g_k) = the node's post-collision
+                               mass; float arithmetic                            */
 
 /* boundary kinds per axis */
 #define LBM_PERIODIC 0

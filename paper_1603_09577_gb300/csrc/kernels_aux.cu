@@ -34,9 +34,7 @@ k_init(const Params<typename Store<PREC>::C> p, const void *__restrict__ phi_in,
     }
     C phi;
     collide<C, CONV, DIFF>(p, f, A3, A35, A5, phi);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) S::st(dst + k * p.plane, own, f[k], wgt<C>(k), phi);
-    if (S::kPhiPlane) dst_phi[own] = (float)phi;
+    S::store_cell(dst, dst_phi, p.plane, own, f, phi);
 }
 
 template <int PREC, int CONV, int DIFF>
@@ -77,7 +75,7 @@ cudaError_t launch_init(const lbm_solver *s, const void *phi, int in_prec, cudaS
 
 // ---- phi(t_n) of the stored post-collision state ---------------------------
 // The collision raises the zeroth moment by R/2 (Eq. 34-35): sum fbar* = phi + R/2,
-// so phi = (sum fbar* - r0/2) / (1 + r1/2). BF16S keeps phi in its own plane.
+// so phi = (sum fbar* - r0/2) / (1 + r1/2).
 template <int PREC>
 __device__ __forceinline__ double node_phi(const Params<typename Store<PREC>::C> &p,
                                            const typename Store<PREC>::T *__restrict__ f,
@@ -85,7 +83,6 @@ __device__ __forceinline__ double node_phi(const Params<typename Store<PREC>::C>
 {
     using S = Store<PREC>;
     using C = typename S::C;
-    if (S::kPhiPlane) return (double)phiplane[own];
     C sum = S::ld(f, own, phiplane, wgt<C>(0));
 #pragma unroll
     for (int k = 1; k < 9; ++k) sum += S::ld(f + k * p.plane, own, phiplane, wgt<C>(k));

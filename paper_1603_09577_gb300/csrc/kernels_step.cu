@@ -67,9 +67,7 @@ k_step(const Params<typename Store<PREC>::C> p, const typename Store<PREC>::T *_
     }
     C phi;
     collide<C, CONV, DIFF>(p, f, A3, A35, A5, phi);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) S::st(dst + k * P, own, f[k], wgt<C>(k), phi);
-    if (S::kPhiPlane) dst_phi[own] = (float)phi;
+    S::store_cell(dst, dst_phi, P, own, f, phi);
 }
 
 template <int PREC, int CONV, int DIFF>

@@ -39,8 +39,14 @@ struct Params {
 
 // ---- storage traits ---------------------------------------------------------
 // Populations are structure-of-arrays: plane k at base + k * plane, element
-// (x, y) at y * pitch + x. LBM_BF16S keeps g_k = fbar_k - w_k phi in bf16 and
-// phi in a float plane of the same shape.
+// (x, y) at y * pitch + x.
+//
+// LBM_BF16S stores g_k = bf16(fbar*_k - w_k phi) and a float shift plane h.
+// A population is read back as w_k h + g_k. The shift is written as
+// h = M* - sum_k g_k, M* = sum_k fbar*_k, so the nine stored populations of a
+// node sum to its post-collision mass up to float rounding: the bf16 rounding
+// of the deviations then moves no mass, it only redistributes it over the
+// directions of that node in proportion to w_k.
 template <int PREC> struct Store;
 
 template <> struct Store<LBM_F64> {
@@ -48,7 +54,12 @@ template <> struct Store<LBM_F64> {
     using C = double;
     static constexpr bool kPhiPlane = false;
     __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
-    __device__ static __forceinline__ void st(T *__restrict__ f, long long i, C v, C, C) { __stcs(f + i, v); }
+    __device__ static __forceinline__ void store_cell(T *__restrict__ f, float *, long long P, long long i,
+                                                      const C v[9], C)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) __stcs(f + k * P + i, v[k]);
+    }
 };
 
 template <> struct Store<LBM_F32> {
@@ -56,21 +67,36 @@ template <> struct Store<LBM_F32> {
     using C = float;
     static constexpr bool kPhiPlane = false;
     __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
-    __device__ static __forceinline__ void st(T *__restrict__ f, long long i, C v, C, C) { __stcs(f + i, v); }
+    __device__ static __forceinline__ void store_cell(T *__restrict__ f, float *, long long P, long long i,
+                                                      const C v[9], C)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) __stcs(f + k * P + i, v[k]);
+    }
 };
 
 template <> struct Store<LBM_BF16S> {
     using T = __nv_bfloat16;
     using C = float;
     static constexpr bool kPhiPlane = true;
-    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *__restrict__ phi, C w)
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *__restrict__ h, C w)
     {
-        return fmaf(w, __ldg(phi + i), __bfloat162float(f[i]));
+        return fmaf(w, __ldg(h + i), __bfloat162float(f[i]));
     }
-    __device__ static __forceinline__ void st(T *__restrict__ f, long long i, C v, C w, C phi)
+    __device__ static __forceinline__ void store_cell(T *__restrict__ f, float *__restrict__ h, long long P,
+                                                      long long i, const C v[9], C phi)
     {
-        f[i] = __float2bfloat16_rn(fmaf(-w, phi, v));
+        C mass = C(0), gsum = C(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const T g = __float2bfloat16_rn(fmaf(-wgt_f(k), phi, v[k]));
+            mass += v[k];
+            gsum += __bfloat162float(g);
+            f[k * P + i] = g;
+        }
+        h[i] = mass - gsum;
     }
+    __device__ static __forceinline__ C wgt_f(int k) { return k == 0 ? 4.0f / 9.0f : (k <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f); }
 };
 
 // ---- coefficient families (Eq. 1, Eq. 7) ------------------------------------
@@ -148,49 +174,52 @@ __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35,
     const C pxx_eq = q.Cbxx - q.Cbyy;
 
     // relaxation (Eq. 17) plus (I - S/2) M0 R (Eq. 34), M0 R = (R, -2R, R,
-    // Bt_x R, -Bt_x R, Bt_y R, -Bt_y R, 0, 0) with Bt = B' (Scheme B)
-    C es = e - p.s1 * (e - e_eq);
-    C epss = eps - p.s2 * (eps - eps_eq);
-    C qxs = qx - p.s4 * (qx + q.Bx);
-    C qys = qy - p.s6 * (qy + q.By);
-    const C pxxs = pxx - p.s7 * (pxx - pxx_eq);
-    const C pxys = pxy - p.s8 * (pxy - q.Cbxy);
+    // Bt_x R, -Bt_x R, Bt_y R, -Bt_y R, 0, 0) with Bt = B' (Scheme B), written
+    // as the change dm = m* - m of every moment. Adding M0^-1 dm to f (instead
+    // of rebuilding f from m*) keeps rounding proportional to the departure
+    // from equilibrium; with R = 0 the mass change is exactly zero.
+    C de = -p.s1 * (e - e_eq);
+    C deps = -p.s2 * (eps - eps_eq);
+    C dqx = -p.s4 * (qx + q.Bx);
+    C dqy = -p.s6 * (qy + q.By);
+    const C dpxx = -p.s7 * (pxx - pxx_eq);
+    const C dpxy = -p.s8 * (pxy - q.Cbxy);
     const C d3 = jx - q.Bx, d5 = jy - q.By;
-    C jxs = jx - (A3 * d3 + A35 * d5);
-    C jys = jy - (A35 * d3 + A5 * d5);
-    C rhos = phi;
+    C djx = -(A3 * d3 + A35 * d5);
+    C djy = -(A35 * d3 + A5 * d5);
+    C drho = C(0);
     if (p.has_src) {
         const C R = p.r0 + p.r1 * phi;
         const C sx = q.Bpx * R, sy = q.Bpy * R;
-        rhos += C(0.5) * R;                      // rho* = phi + R/2 for every s0
-        es -= C(2) * p.h1 * R;
-        epss += p.h2 * R;
-        qxs -= p.h4 * sx;
-        qys -= p.h6 * sy;
-        jxs += sx - C(0.5) * (A3 * sx + A35 * sy);
-        jys += sy - C(0.5) * (A35 * sx + A5 * sy);
+        drho = R;                                // rho* = phi + R/2 = rho + R for every s0
+        de -= C(2) * p.h1 * R;
+        deps += p.h2 * R;
+        dqx -= p.h4 * sx;
+        dqy -= p.h6 * sy;
+        djx += sx - C(0.5) * (A3 * sx + A35 * sy);
+        djy += sy - C(0.5) * (A35 * sx + A5 * sy);
     }
 
-    // back-transform f* = M0^-1 m* = M0^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m*
-    const C r = rhos * (C(1) / C(9));
-    const C ee = es * (C(1) / C(36));
-    const C pp = epss * (C(1) / C(36));
-    const C jxn = jxs * (C(1) / C(6)), qxn = qxs * (C(1) / C(12));
-    const C jyn = jys * (C(1) / C(6)), qyn = qys * (C(1) / C(12));
-    const C pxxn = pxxs * C(0.25), pxyn = pxys * C(0.25);
-    f[0] = r - C(4) * ee + C(4) * pp;
+    // f* = f + M0^-1 dm, M0^-1 = M0^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    const C r = drho * (C(1) / C(9));
+    const C ee = de * (C(1) / C(36));
+    const C pp = deps * (C(1) / C(36));
+    const C jxn = djx * (C(1) / C(6)), qxn = dqx * (C(1) / C(12));
+    const C jyn = djy * (C(1) / C(6)), qyn = dqy * (C(1) / C(12));
+    const C pxxn = dpxx * C(0.25), pxyn = dpxy * C(0.25);
+    f[0] += r - C(4) * ee + C(4) * pp;
     const C base_a = r - ee - C(2) * pp;
     const C X1 = jxn - C(2) * qxn, Y1 = jyn - C(2) * qyn;
-    f[1] = base_a + X1 + pxxn;
-    f[3] = base_a - X1 + pxxn;
-    f[2] = base_a + Y1 - pxxn;
-    f[4] = base_a - Y1 - pxxn;
+    f[1] += base_a + X1 + pxxn;
+    f[3] += base_a - X1 + pxxn;
+    f[2] += base_a + Y1 - pxxn;
+    f[4] += base_a - Y1 - pxxn;
     const C base_d = r + C(2) * ee + pp;
     const C X2 = jxn + qxn, Y2 = jyn + qyn;
-    f[5] = base_d + X2 + Y2 + pxyn;
-    f[6] = base_d - X2 + Y2 - pxyn;
-    f[7] = base_d - X2 - Y2 + pxyn;
-    f[8] = base_d + X2 - Y2 - pxyn;
+    f[5] += base_d + X2 + Y2 + pxyn;
+    f[6] += base_d - X2 + Y2 - pxyn;
+    f[7] += base_d - X2 - Y2 + pxyn;
+    f[8] += base_d + X2 - Y2 - pxyn;
 }
 
 // Equilibrium populations of Eq. 3 (used only at initialisation).

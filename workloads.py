@@ -11,7 +11,7 @@ Workloads (sizes, parameters and seeds):
   burgers_1024         Burgers flux B = a phi^2/2, a = (1,1)/sqrt2, 1024^2 periodic,
                        0.5 sin sin + 1e-3 uniform noise (seed 2), 5000 steps
   aniso_dirichlet_4096 D(phi) = (1 + phi^2) K, K = [[0.02,0.008],[0.008,0.01]],
-                       R = -0.1 phi, 4096^2 with phi = 0 walls, U[0,1) smoothed by
+                       R = -0.1 phi (t in [0,1]), 4096^2 with phi = 0 walls, U[0,1) smoothed by
                        three Jacobi passes (seed 3), 2000 steps
   adjoint_512          linear anisotropic CDE with a per-cell K(x), 512^2 periodic,
                        u = (0.03, 0), 500 steps, smooth seeded fields (seed 4)
@@ -21,6 +21,11 @@ Workloads (sizes, parameters and seeds):
 The Burgers workload reads the diffusivity D = 0.005 on the unit square with
 dx = dt = 1/1024, i.e. K = 0.005 * 1024 = 5.12 in lattice units, while the
 flux vector keeps |a| = 1 (c = 1).
+
+The anisotropic Dirichlet workload keeps K in lattice units and reads the
+source R = -0.1 phi per unit of physical time with the 2000 steps spanning
+t in [0, 1] (dt = 1/2000), i.e. r1 = -0.1 / 2000 per step: taken per lattice
+step the rate would shrink phi by e^-200 over the run, below FP32's range.
 """
 from __future__ import annotations
 
@@ -49,7 +54,7 @@ WORKLOADS = {
         r0=0.0, r1=0.0, steps=5000),
     "aniso_dirichlet_4096": dict(
         nx=4096, ny=4096, bc=(1, 1), phi_wall=(0.0, 0.0, 0.0, 0.0), conv=0, u=(0.0, 0.0),
-        diff=2, K=(0.02, 0.008, 0.01), r0=0.0, r1=-0.1, steps=2000),
+        diff=2, K=(0.02, 0.008, 0.01), r0=0.0, r1=-0.1 / 2000, steps=2000),
     "adjoint_512": dict(
         nx=512, ny=512, bc=(0, 0), phi_wall=(0.0, 0.0, 0.0, 0.0), conv=0, u=(0.03, 0.0),
         diff=0, K=(0.01, 0.0, 0.01), r0=0.0, r1=0.0, steps=500, ckpt_every=50),
