@@ -134,6 +134,23 @@ int lbm_state_bytes(lbm_handle h, size_t *bytes);
 int lbm_save(lbm_handle h, void *dev_dst, void *stream);
 int lbm_load(lbm_handle h, const void *dev_src, void *stream);
 
+/* The reductions of lbm_reduce over a caller-given field, for callers that
+   cannot allocate device memory (the paper has no counterpart: this serves
+   programs whose host application owns the whole device memory pool, or that
+   may not call cudaMalloc/cudaFree because those calls synchronise the device,
+   and so cannot provide a solver workspace).
+   dev_phi: n doubles on the device; dev_ref: n doubles or NULL; dev_out: 8
+   doubles on the device, same meaning as lbm_reduce's. n <= 67,108,864.
+   No device memory is allocated: the partial sums use a fixed 512 KiB array in
+   the library's device image, present on every device that loads the library
+   until the process exits. The first call on a device looks up that array's
+   address (cudaGetSymbolAddress) with the device current; make the first call
+   on each device before any stream capture. All calls share the array, so calls
+   whose kernels overlap on the GPU race: order them on one stream. Returns
+   LBM_EINVAL for n < 1, n > 67,108,864 or a null field or output. */
+int lbm_reduce_field_noalloc(const double *dev_phi, const double *dev_ref, long long n, double *dev_out,
+                             void *stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char *lbm_last_error(void);
 

@@ -57,6 +57,7 @@ SIGNATURES = {
     "lbm_state_bytes": [_VP, ctypes.POINTER(_SZ)],
     "lbm_save": [_VP, _VP, _VP],
     "lbm_load": [_VP, _VP, _VP],
+    "lbm_reduce_field_noalloc": [_VP, _VP, ctypes.c_longlong, _VP, _VP],
 }
 
 
