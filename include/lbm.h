@@ -66,6 +66,11 @@ typedef struct {
     int steps_per_pass;     /* 1, or 2: two time steps per sweep through memory
                                (F32 and BF16S with periodic or ABB walls)         */
     int per_cell_K;         /* 1: K comes from lbm_set_K_field                    */
+    int kernel_variant;     /* 0: automatic; 1: one node per thread; 2: four
+                               x-adjacent nodes per thread with vector loads
+                               (LBM_F32 / LBM_BF16S, nx % 4 == 0)                 */
+    int block_rows;         /* rows of 32-thread warps per thread block: 0 (= 8),
+                               1, 2, 4 or 8                                       */
 } lbm_desc;
 
 /* Coefficient families of Eq. 1 (Sec. 2.1), source and relaxation rates. */
@@ -133,6 +138,37 @@ int lbm_reduce(lbm_handle h, const double *dev_ref, double *dev_out, void *strea
 int lbm_state_bytes(lbm_handle h, size_t *bytes);
 int lbm_save(lbm_handle h, void *dev_dst, void *stream);
 int lbm_load(lbm_handle h, const void *dev_src, void *stream);
+
+/* ---- discrete adjoint (gradients through the time steps) --------------------
+   Built for LBM_F64 and LBM_F32 with periodic boundaries and the linear family
+   (conv 0, diff 0, r0 = r1 = 0), constant or per-node K; other solvers return
+   LBM_EUNSUPPORTED. The forward step is F_{n+1} = collide(pull(F_n)) (Eq. 34);
+   one reverse step applies the transposed collision Jacobian in moment space
+   (Eq. 15-17, 19) and the transposed pull, and accumulates in FP64 the gradient
+   with respect to the relaxation block A of every node (Eq. 17, 21) and to u
+   (through m_eq, Eq. 16). lbm_adjoint_end chains A to K by Eq. 26.
+   Usage: lbm_adjoint_begin with dL/dphi(t_N); then for n = N-1 down to 0 one
+   lbm_adjoint_step with the forward state F_n (lbm_save layout, e.g. restored
+   from checkpoints and recomputed); then lbm_adjoint_end. */
+
+/* Bytes of the adjoint's own device workspace (two adjoint population buffers
+   of the solver's precision, FP64 gradient planes, FP64 per-block partials). */
+int lbm_adjoint_workspace_size(lbm_handle h, size_t *bytes);
+
+/* Start a reverse sweep: dev_ws (device, 256-byte aligned, caller-owned, kept
+   until lbm_adjoint_end) holds the adjoint state; dev_dphiN: nx*ny values of
+   dL/dphi(t_N) in precision `prec`. Zeroes the gradient accumulators. */
+int lbm_adjoint_begin(lbm_handle h, void *dev_ws, size_t bytes, const void *dev_dphiN, int prec, void *stream);
+
+/* One reverse step through the update F_{n+1} = collide(pull(F_n)); dev_state_n
+   is the forward post-collision state F_n in lbm_save layout. */
+int lbm_adjoint_step(lbm_handle h, const void *dev_state_n, void *stream);
+
+/* Finish at the initial condition F_0 = feq(phi0) (Eq. 40): dev_phi0 (nx*ny of
+   `prec`); outputs dL/dphi0 (nx*ny doubles), dL/dK (3 planes of nx*ny doubles:
+   dKxx, dKxy, dKyy per node, Kxy counted once) and dL/du (2 doubles). */
+int lbm_adjoint_end(lbm_handle h, const void *dev_phi0, int prec, double *dev_dphi0, double *dev_dK, double *dev_du,
+                    void *stream);
 
 /* The reductions of lbm_reduce over a caller-given field, for callers that
    cannot allocate device memory (the paper has no counterpart: this serves

@@ -28,7 +28,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("prec", ctypes.c_int),
                 ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
                 ("phi_wall", ctypes.c_double * 4), ("steps_per_pass", ctypes.c_int),
-                ("per_cell_K", ctypes.c_int)]
+                ("per_cell_K", ctypes.c_int), ("kernel_variant", ctypes.c_int),
+                ("block_rows", ctypes.c_int)]
 
 
 class Coeffs(ctypes.Structure):
@@ -58,6 +59,10 @@ SIGNATURES = {
     "lbm_save": [_VP, _VP, _VP],
     "lbm_load": [_VP, _VP, _VP],
     "lbm_reduce_field_noalloc": [_VP, _VP, ctypes.c_longlong, _VP, _VP],
+    "lbm_adjoint_workspace_size": [_VP, ctypes.POINTER(_SZ)],
+    "lbm_adjoint_begin": [_VP, _VP, _SZ, _VP, _I, _VP],
+    "lbm_adjoint_step": [_VP, _VP, _VP],
+    "lbm_adjoint_end": [_VP, _VP, _I, _VP, _VP, _VP, _VP],
 }
 
 

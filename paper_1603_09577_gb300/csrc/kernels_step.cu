@@ -77,8 +77,9 @@ static cudaError_t step_t(const lbm_solver *s, int src, cudaStream_t st)
     using T = typename S::T;
     using C = typename S::C;
     const Params<C> p = make_params<C>(s);
-    dim3 block(32, 8);
-    dim3 grid((s->d.nx + 31) / 32, (s->d.ny + 7) / 8);
+    const int by = s->d.block_rows > 0 ? s->d.block_rows : 8;
+    dim3 block(32, by);
+    dim3 grid((s->d.nx + 31) / 32, (s->d.ny + by - 1) / by);
     k_step<PREC, CONV, DIFF><<<grid, block, 0, st>>>(p, (const T *)s->pop[src], s->phi[src], (T *)s->pop[src ^ 1],
                                                       s->phi[src ^ 1]);
     return cudaGetLastError();

@@ -70,6 +70,14 @@ static int check_desc(const lbm_desc *d)
         if (!isfinite(d->phi_wall[i])) return fail(LBM_EINVAL, "non-finite wall value");
     if (d->steps_per_pass != 1 && d->steps_per_pass != 2) return fail(LBM_EINVAL, "steps_per_pass must be 1 or 2");
     if (d->steps_per_pass == 2) return fail(LBM_EUNSUPPORTED, "two steps per pass is not built yet");
+    if (d->kernel_variant < 0 || d->kernel_variant > 2) return fail(LBM_EINVAL, "kernel_variant must be 0, 1 or 2");
+    if (d->kernel_variant == 2 && !(d->prec != LBM_F64 && d->nx % 4 == 0))
+        return fail(LBM_EUNSUPPORTED, "kernel_variant 2 needs LBM_F32 or LBM_BF16S and nx % 4 == 0");
+    {
+        const int b = d->block_rows;
+        if (!(b == 0 || b == 1 || b == 2 || b == 4 || b == 8))
+            return fail(LBM_EINVAL, "block_rows must be 0, 1, 2, 4 or 8");
+    }
     return LBM_OK;
 }
 
@@ -261,8 +269,9 @@ int lbm_step(lbm_handle h, int nsteps, void *stream)
             h->t += 2;
         }
     }
+    const bool vec = h->d.kernel_variant == 2 || (h->d.kernel_variant == 0 && step_v4_preferred(h));
     for (; done < nsteps; ++done) {
-        if (int rc = cuda_check(launch_step(h, h->cur, st), "lbm_step")) return rc;
+        if (int rc = cuda_check(vec ? launch_step_v4(h, h->cur, st) : launch_step(h, h->cur, st), "lbm_step")) return rc;
         h->cur ^= 1;
         h->t += 1;
     }
@@ -330,6 +339,82 @@ int lbm_load(lbm_handle h, const void *dev_src, void *stream)
                                                 cudaMemcpyDeviceToDevice, st), "lbm_load phi"))
             return rc;
     h->phi_set = 1;
+    return LBM_OK;
+}
+
+// ---- adjoint -----------------------------------------------------------------
+
+static int adjoint_supported(lbm_handle h)
+{
+    if (check_ready(h)) return LBM_EINVAL;
+    if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "the adjoint is built for LBM_F64 and LBM_F32");
+    if (h->d.bc_x != LBM_PERIODIC || h->d.bc_y != LBM_PERIODIC)
+        return fail(LBM_EUNSUPPORTED, "the adjoint is built for periodic boundaries");
+    if (h->c.conv != 0 || h->c.diff != 0 || h->c.r0 != 0.0 || h->c.r1 != 0.0)
+        return fail(LBM_EUNSUPPORTED, "the adjoint is built for the linear family (conv 0, diff 0) without source");
+    return LBM_OK;
+}
+
+static size_t adj_lam_bytes(lbm_handle h) { return up256(9 * (size_t)h->L.plane * h->L.csize); }
+
+int lbm_adjoint_workspace_size(lbm_handle h, size_t *bytes)
+{
+    if (int rc = adjoint_supported(h)) return rc;
+    if (!bytes) return fail(LBM_EINVAL, "null size pointer");
+    *bytes = 2 * adj_lam_bytes(h) + up256(3 * (size_t)h->L.plane * 8) + up256((size_t)adjoint_blocks(h) * 2 * 8);
+    return LBM_OK;
+}
+
+int lbm_adjoint_begin(lbm_handle h, void *dev_ws, size_t bytes, const void *dev_dphiN, int prec, void *stream)
+{
+    if (int rc = adjoint_supported(h)) return rc;
+    size_t need = 0;
+    lbm_adjoint_workspace_size(h, &need);
+    if (!dev_ws || ((uintptr_t)dev_ws & 255) != 0) return fail(LBM_EINVAL, "adjoint workspace null or not 256-byte aligned");
+    if (bytes < need) return fail(LBM_EINVAL, "adjoint workspace smaller than lbm_adjoint_workspace_size");
+    if (!dev_dphiN) return fail(LBM_EINVAL, "null dL/dphi");
+    if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "dL/dphi must be LBM_F64 or LBM_F32");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)dev_ws;
+    const size_t lb = adj_lam_bytes(h), gb = up256(3 * (size_t)h->L.plane * 8);
+    h->adj = w;
+    h->lam[0] = w;
+    h->lam[1] = w + lb;
+    h->gA = (double *)(w + 2 * lb);
+    h->adj_partials = (double *)(w + 2 * lb + gb);
+    h->adj_cur = 0;
+    if (int rc = cuda_check(cudaMemsetAsync(h->gA, 0, gb + up256((size_t)adjoint_blocks(h) * 16), st), "lbm_adjoint_begin"))
+        return rc;
+    if (int rc = cuda_check(launch_adjoint_begin(h, dev_dphiN, prec, h->lam[0], st), "lbm_adjoint_begin")) return rc;
+    h->adj_active = 1;
+    return LBM_OK;
+}
+
+int lbm_adjoint_step(lbm_handle h, const void *dev_state_n, void *stream)
+{
+    if (int rc = adjoint_supported(h)) return rc;
+    if (!h->adj_active) return fail(LBM_EINVAL, "lbm_adjoint_begin has not been called");
+    if (!dev_state_n) return fail(LBM_EINVAL, "null forward state");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(launch_adjoint_step(h, dev_state_n, h->lam[h->adj_cur], h->lam[h->adj_cur ^ 1], h->gA,
+                                                h->adj_partials, st), "lbm_adjoint_step"))
+        return rc;
+    h->adj_cur ^= 1;
+    return LBM_OK;
+}
+
+int lbm_adjoint_end(lbm_handle h, const void *dev_phi0, int prec, double *dev_dphi0, double *dev_dK, double *dev_du,
+                    void *stream)
+{
+    if (int rc = adjoint_supported(h)) return rc;
+    if (!h->adj_active) return fail(LBM_EINVAL, "lbm_adjoint_begin has not been called");
+    if (!dev_phi0 || !dev_dphi0 || !dev_dK || !dev_du) return fail(LBM_EINVAL, "null argument");
+    if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "phi0 must be LBM_F64 or LBM_F32");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(launch_adjoint_end(h, dev_phi0, prec, h->lam[h->adj_cur], h->gA, dev_dphi0, dev_dK, dev_du,
+                                               h->adj_partials, st), "lbm_adjoint_end"))
+        return rc;
+    h->adj_active = 0;
     return LBM_OK;
 }
 

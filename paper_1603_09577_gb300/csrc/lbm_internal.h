@@ -43,6 +43,12 @@ struct lbm_solver {
     int *flag = nullptr;
     int cur = 0;
     long long t = 0;
+    // adjoint (caller-provided second workspace)
+    char *adj = nullptr;
+    void *lam[2] = {nullptr, nullptr};
+    double *gA = nullptr;
+    double *adj_partials = nullptr;
+    int adj_cur = 0, adj_active = 0;
 };
 
 namespace lbm {
@@ -58,8 +64,18 @@ Params<C> make_params(const lbm_solver *s);
 cudaError_t launch_init(const lbm_solver *s, const void *phi, int in_prec, cudaStream_t st);
 cudaError_t launch_step(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2(const lbm_solver *s, int src, cudaStream_t st);
+bool step_v4_supported(const lbm_solver *s);
+bool step_v4_preferred(const lbm_solver *s);
+cudaError_t launch_step_v4(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_get_phi(const lbm_solver *s, void *out, int out_prec, cudaStream_t st);
 cudaError_t launch_reduce(const lbm_solver *s, const double *ref, double *out, cudaStream_t st);
 cudaError_t launch_kfield(const lbm_solver *s, const double *K, cudaStream_t st);
+
+int adjoint_blocks(const lbm_solver *s);
+cudaError_t launch_adjoint_begin(const lbm_solver *s, const void *dphi, int in_prec, void *lam, cudaStream_t st);
+cudaError_t launch_adjoint_step(const lbm_solver *s, const void *F, const void *lam_in, void *lam_out, double *gA,
+                                double *partials, cudaStream_t st);
+cudaError_t launch_adjoint_end(const lbm_solver *s, const void *phi0, int in_prec, const void *lam, const double *gA,
+                               double *dphi0, double *dK, double *du, double *partials, cudaStream_t st);
 
 }  // namespace lbm

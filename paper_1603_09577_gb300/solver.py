@@ -39,7 +39,7 @@ class Solver:
 
     def __init__(self, nx: int, ny: int, prec: str = "f32", bc=("periodic", "periodic"),
                  phi_wall=(0.0, 0.0, 0.0, 0.0), steps_per_pass: int = 1, per_cell_K: bool = False,
-                 device=None):
+                 kernel_variant: int = 0, block_rows: int = 0, device=None):
         self.lib = C.lib()
         self.nx, self.ny, self.prec = int(nx), int(ny), prec
         self.device = torch.device(device if device is not None else "cuda")
@@ -49,6 +49,7 @@ class Solver:
         d.phi_wall[:] = [float(v) for v in phi_wall]
         d.steps_per_pass = int(steps_per_pass)
         d.per_cell_K = int(bool(per_cell_K))
+        d.kernel_variant, d.block_rows = int(kernel_variant), int(block_rows)
         self.desc = d
         size = ctypes.c_size_t()
         C.check(self.lib.lbm_workspace_size(ctypes.byref(d), ctypes.byref(size)))

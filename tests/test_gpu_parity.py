@@ -24,9 +24,10 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def run_gpu(prec, nx, ny, phi0, steps, bc=(0, 0), walls=(0, 0, 0, 0), Kfield=None, spp=1, **coef):
+def run_gpu(prec, nx, ny, phi0, steps, bc=(0, 0), walls=(0, 0, 0, 0), Kfield=None, spp=1, variant=0,
+            block_rows=0, **coef):
     s = Solver(nx, ny, prec=prec, bc=(BCN[bc[0]], BCN[bc[1]]), phi_wall=walls, steps_per_pass=spp,
-               per_cell_K=Kfield is not None)
+               per_cell_K=Kfield is not None, kernel_variant=variant, block_rows=block_rows)
     s.set_coeffs(s=W.s9(), **coef)
     if Kfield is not None:
         s.set_K_field(torch.from_numpy(Kfield).cuda())
@@ -55,29 +56,47 @@ CASES = [
     (33, 65, (1, 0), 1, 2, (0.1, -0.2), (0.03, -0.01, 0.02), 0.01, -0.2),
     (48, 48, (0, 0), 0, 1, (-0.08, 0.06), (0.004, 0.001, 0.006), 0.0, 0.0),
     (40, 31, (1, 1), 1, 1, (0.05, 0.05), (0.1, 0.02, 0.08), 0.002, 0.0),
+    (132, 19, (1, 1), 1, 2, (0.12, 0.07), (0.03, 0.01, 0.02), 0.0, -0.1),
+    (260, 13, (0, 0), 0, 1, (-0.05, 0.09), (0.02, -0.005, 0.01), 0.0, 0.0),
+    (8, 5, (1, 0), 0, 0, (0.1, 0.0), (0.05, 0.0, 0.05), 0.01, 0.0),
 ]
+VARIANTS = [("f64", 1), ("f32", 1), ("f32", 2), ("bf16s", 1), ("bf16s", 2)]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "bf16s"])
+@pytest.mark.parametrize("prec,variant", VARIANTS, ids=[f"{p}-v{v}" for p, v in VARIANTS])
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}-c{c[3]}d{c[4]}" for c in CASES])
-def test_parity_families_and_walls(prec, case):
+def test_parity_families_and_walls(prec, variant, case):
     nx, ny, bc, conv, diff, u, K, r0, r1 = case
+    if variant == 2 and nx % 4:
+        pytest.skip("four-node kernel needs nx % 4 == 0")
     rng = np.random.default_rng(nx * 131 + ny)
     phi0 = W.jacobi_smooth(rng.uniform(0.05, 0.95, (ny, nx)), 2)
     walls = (0.3, 0.7, 0.1, 0.5) if bc != (0, 0) else (0, 0, 0, 0)
     coef = dict(conv=conv, u=u, diff=diff, K=K, r0=r0, r1=r1)
     ref = run_oracle(nx, ny, phi0, 60, bc, walls, **coef)
-    got, _ = run_gpu(prec, nx, ny, phi0, 60, bc, walls, **coef)
+    got, _ = run_gpu(prec, nx, ny, phi0, 60, bc, walls, variant=variant, block_rows=4, **coef)
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_parity_per_cell_tensor(prec):
-    nx, ny = 45, 38
+@pytest.mark.parametrize("variant", [1, 2])
+def test_block_shapes(variant):
+    nx, ny = 196, 45
+    phi0 = W.phi0_aniso(nx, seed=9, ny=ny)
+    coef = dict(conv=0, u=(0.03, -0.02), diff=2, K=(0.02, 0.008, 0.01), r1=-0.05)
+    ref = run_oracle(nx, ny, phi0, 30, (1, 1), (0.1, 0.2, 0.3, 0.4), **coef)
+    for by in (1, 2, 4, 8):
+        got, _ = run_gpu("f32", nx, ny, phi0, 30, (1, 1), (0.1, 0.2, 0.3, 0.4), variant=variant, block_rows=by,
+                         **coef)
+        assert rel(got, ref) <= 1e-5, (by, rel(got, ref))
+
+
+@pytest.mark.parametrize("prec,variant", [("f64", 1), ("f32", 1), ("f32", 2)])
+def test_parity_per_cell_tensor(prec, variant):
+    nx, ny = 44, 38
     Kf, phi0, _ = W.adjoint_inputs(nx, seed=7, ny=ny)
     coef = dict(conv=0, u=(0.03, 0.0), diff=0, K=(0.0, 0.0, 0.0))
     ref = run_oracle(nx, ny, phi0, 80, Kfield=Kf, **coef)
-    got, _ = run_gpu(prec, nx, ny, phi0, 80, Kfield=Kf, **coef)
+    got, _ = run_gpu(prec, nx, ny, phi0, 80, Kfield=Kf, variant=variant, **coef)
     assert rel(got, ref) <= TOL[prec]
 
 
