@@ -170,6 +170,37 @@ int lbm_adjoint_step(lbm_handle h, const void *dev_state_n, void *stream);
 int lbm_adjoint_end(lbm_handle h, const void *dev_phi0, int prec, double *dev_dphi0, double *dev_dK, double *dev_du,
                     void *stream);
 
+/* ---- batched ensemble of independent lattices ---------------------------------
+   Many lattices of different sizes and coefficients advanced together with one
+   persistent launch per time step over a work list of 32 x 32 tiles taken from
+   every instance (each step is Eq. 34 per instance, FP32 storage, periodic
+   walls). All instances share the coefficient family; u, K and the relaxation
+   rates are per instance; no source term. Fields of all instances are
+   packed one after another (instance i's nx_i*ny_i values, row-major). */
+typedef struct lbm_ensemble_s *lbm_ensemble;
+
+/* Device workspace bytes for `count` instances of sizes nx[i] x ny[i]. */
+int lbm_ensemble_workspace_size(int count, const int *nx, const int *ny, size_t *bytes);
+/* Create; coeffs: `count` entries (per-instance u and K). Copies the instance and
+   tile tables into the caller's workspace (synchronous). */
+int lbm_ensemble_create(lbm_ensemble *e, int count, const int *nx, const int *ny, const lbm_coeffs *coeffs,
+                        void *dev_workspace, size_t bytes);
+int lbm_ensemble_destroy(lbm_ensemble e);
+/* Total nodes, number of tiles and the persistent grid size (blocks). */
+int lbm_ensemble_info(lbm_ensemble e, long long *nodes, int *tiles, int *grid);
+/* Initial condition of every instance (Eq. 40) from the packed phi array. */
+int lbm_ensemble_set_phi(lbm_ensemble e, const void *dev_phi, int prec, void *stream);
+/* nsteps time steps; mode 0: one persistent launch per step over all tiles;
+   mode 1: one launch per instance per step (same arithmetic, for comparison). */
+int lbm_ensemble_step(lbm_ensemble e, int nsteps, int mode, void *stream);
+/* Capture nsteps (even, >= 2) persistent steps on a non-default stream into a
+   CUDA graph held by the ensemble; lbm_ensemble_replay launches it (advancing
+   the state by nsteps). */
+int lbm_ensemble_capture(lbm_ensemble e, int nsteps, void *stream);
+int lbm_ensemble_replay(lbm_ensemble e, void *stream);
+/* phi(t_n) of every instance into the packed array dev_out. */
+int lbm_ensemble_get_phi(lbm_ensemble e, void *dev_out, int prec, void *stream);
+
 /* The reductions of lbm_reduce over a caller-given field, for callers that
    cannot allocate device memory (the paper has no counterpart: this serves
    programs whose host application owns the whole device memory pool, or that

@@ -63,6 +63,15 @@ SIGNATURES = {
     "lbm_adjoint_begin": [_VP, _VP, _SZ, _VP, _I, _VP],
     "lbm_adjoint_step": [_VP, _VP, _VP],
     "lbm_adjoint_end": [_VP, _VP, _I, _VP, _VP, _VP, _VP],
+    "lbm_ensemble_workspace_size": [_I, _VP, _VP, ctypes.POINTER(_SZ)],
+    "lbm_ensemble_create": [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, _SZ],
+    "lbm_ensemble_destroy": [_VP],
+    "lbm_ensemble_info": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "lbm_ensemble_set_phi": [_VP, _VP, _I, _VP],
+    "lbm_ensemble_step": [_VP, _I, _I, _VP],
+    "lbm_ensemble_capture": [_VP, _I, _VP],
+    "lbm_ensemble_replay": [_VP, _VP],
+    "lbm_ensemble_get_phi": [_VP, _VP, _I, _VP],
 }
 
 

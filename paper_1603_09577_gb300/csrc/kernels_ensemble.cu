@@ -1,0 +1,166 @@
+// kernels_ensemble.cu -- many independent lattices advanced together: one
+// persistent launch per time step over a work list of 32 x 32 tiles drawn from
+// every instance (FP32 storage, periodic walls, one coefficient family shared,
+// per-instance u, K and relaxation rates). Blocks take tiles round-robin (t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...): tiles have equal shape, so the static split is
+// balanced and no block ever waits on another.
+#include "lbm_ensemble.h"
+
+namespace lbm {
+
+template <int CONV, int DIFF>
+__device__ __forceinline__ void ens_tile(const EnsInst &I, int tx0, int ty0, int parity)
+{
+    const Params<float> p = ens_params(I);
+    const float *__restrict__ src = I.pop[parity];
+    float *__restrict__ dst = I.pop[parity ^ 1];
+    const int x = tx0 + threadIdx.x;
+    if (x >= p.nx) return;
+    const int xm = x == 0 ? p.nx - 1 : x - 1;
+    const int xp = x == p.nx - 1 ? 0 : x + 1;
+    const long long P = p.plane;
+#pragma unroll 1
+    for (int r = threadIdx.y; r < kEnsTile; r += blockDim.y) {
+        const int y = ty0 + r;
+        if (y >= p.ny) break;
+        const int ym = y == 0 ? p.ny - 1 : y - 1;
+        const int yp = y == p.ny - 1 ? 0 : y + 1;
+        const long long r0 = (long long)y * p.pitch, rm = (long long)ym * p.pitch, rp = (long long)yp * p.pitch;
+        const long long own = r0 + x;
+        float f[9];
+        f[0] = __ldg(src + own);
+        f[1] = __ldg(src + 1 * P + r0 + xm);
+        f[2] = __ldg(src + 2 * P + rm + x);
+        f[3] = __ldg(src + 3 * P + r0 + xp);
+        f[4] = __ldg(src + 4 * P + rp + x);
+        f[5] = __ldg(src + 5 * P + rm + xm);
+        f[6] = __ldg(src + 6 * P + rm + xp);
+        f[7] = __ldg(src + 7 * P + rp + xp);
+        f[8] = __ldg(src + 8 * P + rp + xm);
+        float phi;
+        collide<float, CONV, DIFF>(p, f, p.A3, p.A35, p.A5, phi);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) __stcs(dst + k * P + own, f[k]);
+    }
+}
+
+template <int CONV, int DIFF>
+__global__ void __launch_bounds__(kEnsThreads)
+k_ens_step(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int t_begin,
+           int t_end, int parity)
+{
+    for (int t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
+        const int4 tl = __ldg(tiles + t);
+        const EnsInst I = inst[tl.x];
+        ens_tile<CONV, DIFF>(I, tl.y, tl.z, parity);
+    }
+}
+
+// initial condition of every instance (Eq. 40, no source): fbar = feq(phi0),
+// then one collision, as for a single lattice
+template <int CONV, int DIFF>
+__global__ void __launch_bounds__(kEnsThreads)
+k_ens_init(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int ntiles,
+           const void *__restrict__ phi, int in_prec, int parity)
+{
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = __ldg(tiles + t);
+        const EnsInst I = inst[tl.x];
+        const Params<float> p = ens_params(I);
+        const int x = tl.y + threadIdx.x;
+        if (x >= I.nx) continue;
+        for (int r = threadIdx.y; r < kEnsTile; r += blockDim.y) {
+            const int y = tl.z + r;
+            if (y >= I.ny) break;
+            const long long i = I.phi_off + (long long)y * I.nx + x;
+            const float ph = in_prec == LBM_F64 ? (float)((const double *)phi)[i] : ((const float *)phi)[i];
+            float f[9], phi_c;
+            equilibrium<float, CONV, DIFF>(p, ph, f);
+            collide<float, CONV, DIFF>(p, f, p.A3, p.A35, p.A5, phi_c);
+            const long long own = (long long)y * I.pitch + x;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) I.pop[parity][k * I.plane + own] = f[k];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kEnsThreads)
+k_ens_get_phi(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int ntiles, int parity,
+              void *__restrict__ out, int out_prec)
+{
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = __ldg(tiles + t);
+        const EnsInst I = inst[tl.x];
+        const int x = tl.y + threadIdx.x;
+        if (x >= I.nx) continue;
+        for (int r = threadIdx.y; r < kEnsTile; r += blockDim.y) {
+            const int y = tl.z + r;
+            if (y >= I.ny) break;
+            const long long own = (long long)y * I.pitch + x;
+            const float *f = I.pop[parity];
+            float s = f[own];
+#pragma unroll
+            for (int k = 1; k < 9; ++k) s += f[k * I.plane + own];
+            const long long o = I.phi_off + (long long)y * I.nx + x;
+            if (out_prec == LBM_F64) ((double *)out)[o] = (double)s;
+            else ((float *)out)[o] = s;
+        }
+    }
+}
+
+#define LBM_ENS_DISPATCH(KEY, CALL)                    \
+    switch (KEY) {                                     \
+    case 0: CALL(0, 0); break;                         \
+    case 1: CALL(0, 1); break;                         \
+    case 2: CALL(0, 2); break;                         \
+    case 3: CALL(1, 0); break;                         \
+    case 4: CALL(1, 1); break;                         \
+    case 5: CALL(1, 2); break;                         \
+    default: return cudaErrorInvalidValue;             \
+    }
+
+cudaError_t ens_launch_step(const lbm_ensemble_s *e, int t_begin, int t_end, int blocks, cudaStream_t st)
+{
+    dim3 block(kEnsTile, kEnsThreads / kEnsTile);
+#define CALL(A, B) k_ens_step<A, B><<<blocks, block, 0, st>>>(e->d_inst, e->d_tiles, t_begin, t_end, e->parity)
+    LBM_ENS_DISPATCH(e->family, CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t ens_launch_init(const lbm_ensemble_s *e, const void *phi, int in_prec, cudaStream_t st)
+{
+    dim3 block(kEnsTile, kEnsThreads / kEnsTile);
+#define CALL(A, B) k_ens_init<A, B><<<e->grid, block, 0, st>>>(e->d_inst, e->d_tiles, e->ntiles, phi, in_prec, e->parity)
+    LBM_ENS_DISPATCH(e->family, CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t ens_launch_get_phi(const lbm_ensemble_s *e, void *out, int out_prec, cudaStream_t st)
+{
+    dim3 block(kEnsTile, kEnsThreads / kEnsTile);
+    k_ens_get_phi<<<e->grid, block, 0, st>>>(e->d_inst, e->d_tiles, e->ntiles, e->parity, out, out_prec);
+    return cudaGetLastError();
+}
+
+int ens_occupancy_blocks(int family)
+{
+    int per_sm = 1;
+    const int threads = kEnsThreads;
+    cudaError_t err;
+#define CALL(A, B) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<A, B>, threads, 0)
+    switch (family) {
+    case 0: CALL(0, 0); break;
+    case 1: CALL(0, 1); break;
+    case 2: CALL(0, 2); break;
+    case 3: CALL(1, 0); break;
+    case 4: CALL(1, 1); break;
+    default: CALL(1, 2); break;
+    }
+#undef CALL
+    if (err != cudaSuccess) return -1;
+    return per_sm;
+}
+
+}  // namespace lbm

@@ -1,0 +1,56 @@
+// lbm_ensemble.h -- internal state of a batched ensemble of independent lattices.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr int kEnsTile = 32;        // tiles are 32 x 32 nodes
+constexpr int kEnsThreads = 256;    // 32 x 8 threads, four rows per thread
+
+// Per-instance data read by the kernels (device table).
+struct __align__(16) EnsInst {
+    float *pop[2];          // A/B population buffers (9 planes each)
+    long long pitch, plane;
+    long long phi_off;      // offset of this instance in the packed phi arrays
+    int nx, ny;
+    float A3, A35, A5;
+    float ux, uy, uxx, uxy, uyy;
+    float s1, s2, s4, s6, s7, s8, h1, h2, h4, h6;
+};
+
+__device__ __forceinline__ Params<float> ens_params(const EnsInst &I)
+{
+    Params<float> p;
+    p.nx = I.nx; p.ny = I.ny; p.pitch = I.pitch; p.plane = I.plane;
+    p.abb_x = 0; p.abb_y = 0;
+    p.s1 = I.s1; p.s2 = I.s2; p.s4 = I.s4; p.s6 = I.s6; p.s7 = I.s7; p.s8 = I.s8;
+    p.h1 = I.h1; p.h2 = I.h2; p.h4 = I.h4; p.h6 = I.h6;
+    p.A3 = I.A3; p.A35 = I.A35; p.A5 = I.A5;
+    p.ux = I.ux; p.uy = I.uy; p.uxx = I.uxx; p.uxy = I.uxy; p.uyy = I.uyy;
+    p.r0 = 0.f; p.r1 = 0.f; p.half_r0 = 0.f; p.inv_den = 1.f; p.inv_post = 1.f;
+    p.has_src = 0;
+    for (int i = 0; i < 4; ++i) p.phi_wall[i] = 0.f;
+    p.Afield = nullptr;
+    return p;
+}
+
+}  // namespace lbm
+
+struct lbm_ensemble_s {
+    int count = 0, family = 0, ntiles = 0, grid = 0, parity = 0;
+    lbm::EnsInst *d_inst = nullptr;
+    int4 *d_tiles = nullptr;
+    int *tile_begin = nullptr;      // host: first tile of each instance (count + 1)
+    long long total_nodes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_steps = 0, graph_parity = 0;
+};
+
+namespace lbm {
+cudaError_t ens_launch_step(const lbm_ensemble_s *e, int t_begin, int t_end, int blocks, cudaStream_t st);
+cudaError_t ens_launch_init(const lbm_ensemble_s *e, const void *phi, int in_prec, cudaStream_t st);
+cudaError_t ens_launch_get_phi(const lbm_ensemble_s *e, void *out, int out_prec, cudaStream_t st);
+int ens_occupancy_blocks(int family);
+}  // namespace lbm

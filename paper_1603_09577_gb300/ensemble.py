@@ -1,0 +1,80 @@
+"""A batched ensemble of independent lattices (see lbm.h): torch supplies the
+workspace and streams, liblbm runs every step."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as C
+from .solver import _prec_of, _ptr, _stream
+
+
+class Ensemble:
+    """instances: list of dicts with nx, ny, u (2), K (3) and optionally s (9
+    rates; default `s`); the coefficient family (conv, diff) is shared."""
+
+    def __init__(self, instances, conv=0, diff=1, s=(1.0, 1.2, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1), device=None):
+        self.lib = C.lib()
+        self.device = torch.device(device if device is not None else "cuda")
+        n = len(instances)
+        self.sizes = [(int(d["nx"]), int(d["ny"])) for d in instances]
+        self.nx = (ctypes.c_int * n)(*[a for a, _ in self.sizes])
+        self.ny = (ctypes.c_int * n)(*[b for _, b in self.sizes])
+        co = (C.Coeffs * n)()
+        for i, d in enumerate(instances):
+            co[i].conv, co[i].diff = int(conv), int(diff)
+            co[i].u[:] = [float(v) for v in d["u"]]
+            co[i].K[:] = [float(v) for v in d["K"]]
+            co[i].s[:] = [float(v) for v in d.get("s", s)]
+            co[i].r0 = co[i].r1 = 0.0
+        self.coeffs = co
+        size = ctypes.c_size_t()
+        C.check(self.lib.lbm_ensemble_workspace_size(n, self.nx, self.ny, ctypes.byref(size)))
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self.h = ctypes.c_void_p()
+        C.check(self.lib.lbm_ensemble_create(ctypes.byref(self.h), n, self.nx, self.ny, co, _ptr(self.workspace),
+                                             size.value))
+        nodes, tiles, grid = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        C.check(self.lib.lbm_ensemble_info(self.h, ctypes.byref(nodes), ctypes.byref(tiles), ctypes.byref(grid)))
+        self.nodes, self.tiles, self.grid = nodes.value, tiles.value, grid.value
+        self.offsets = [0]
+        for a, b in self.sizes:
+            self.offsets.append(self.offsets[-1] + a * b)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.lib.lbm_ensemble_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def pack(self, fields, dtype=torch.float64) -> torch.Tensor:
+        return torch.cat([torch.as_tensor(f, dtype=dtype).reshape(-1) for f in fields]).to(self.device)
+
+    def unpack(self, flat: torch.Tensor):
+        return [flat[self.offsets[i]:self.offsets[i + 1]].reshape(b, a) for i, (a, b) in enumerate(self.sizes)]
+
+    def set_phi(self, packed: torch.Tensor, stream=None):
+        assert packed.is_cuda and packed.numel() == self.nodes and packed.is_contiguous()
+        C.check(self.lib.lbm_ensemble_set_phi(self.h, _ptr(packed), _prec_of(packed), _stream(stream)))
+        return self
+
+    def step(self, n: int = 1, mode: int = 0, stream=None):
+        C.check(self.lib.lbm_ensemble_step(self.h, int(n), int(mode), _stream(stream)))
+        return self
+
+    def capture(self, n: int, stream=None):
+        C.check(self.lib.lbm_ensemble_capture(self.h, int(n), _stream(stream)))
+        return self
+
+    def replay(self, stream=None):
+        C.check(self.lib.lbm_ensemble_replay(self.h, _stream(stream)))
+        return self
+
+    def phi(self, dtype=torch.float64, stream=None) -> torch.Tensor:
+        out = torch.empty(self.nodes, dtype=dtype, device=self.device)
+        C.check(self.lib.lbm_ensemble_get_phi(self.h, _ptr(out), _prec_of(out), _stream(stream)))
+        return out

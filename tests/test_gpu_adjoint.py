@@ -23,7 +23,7 @@ def gpu_grads(phi0, Kf, tgt, u, steps, ckpt, prec):
     out = adjoint.run(p0, K, uu, steps, ckpt_every=ckpt, prec=prec, s_rates=W.s9())
     loss = 0.5 * ((out - torch.from_numpy(tgt).cuda()) ** 2).sum()
     loss.backward()
-    return float(loss), p0.grad.cpu().numpy(), K.grad.cpu().numpy(), uu.grad.cpu().numpy()
+    return float(loss.detach()), p0.grad.cpu().numpy(), K.grad.cpu().numpy(), uu.grad.cpu().numpy()
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-4)])

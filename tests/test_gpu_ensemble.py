@@ -1,0 +1,94 @@
+"""The batched ensemble (one persistent launch per step over all instances)
+against the FP64 oracle per instance, against one launch per instance and a
+replayed CUDA graph (bit for bit), and on the full 256-instance workload."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from paper_1603_09577_gb300.ensemble import Ensemble
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def small_instances():
+    base = W.ensemble(count=7, seed=17)
+    sizes = [(33, 40), (40, 33), (64, 64), (70, 96), (96, 70), (100, 100), (130, 65)]
+    out = []
+    for d, (nx, ny) in zip(base, sizes):
+        d = dict(d, nx=nx, ny=ny, xc=nx / 2, yc=ny / 3, sigma=max(4.0, nx / 8))
+        out.append(d)
+    return out
+
+
+def oracle_phi(d, phi0, steps, conv=0, diff=1):
+    sp = O.Spec(nx=d["nx"], ny=d["ny"], conv=conv, u=d["u"], diff=diff, K=d["K"], s=d["s"])
+    return O.run(sp, phi0, steps)
+
+
+@pytest.mark.parametrize("conv,diff", [(0, 1), (1, 2)])
+def test_ensemble_matches_oracle(conv, diff):
+    inst = small_instances()
+    phis = [W.ensemble_phi0(d) for d in inst]
+    e = Ensemble(inst, conv=conv, diff=diff)
+    e.set_phi(e.pack(phis))
+    e.step(150)
+    got = e.unpack(e.phi().cpu())
+    for d, p0, g in zip(inst, phis, got):
+        ref = oracle_phi(d, p0, 150, conv, diff)
+        assert rel(g.numpy(), ref) <= 1e-5, (d["nx"], d["ny"], rel(g.numpy(), ref))
+
+
+def test_ensemble_modes_agree_bitwise():
+    inst = small_instances()
+    packed = None
+    outs = []
+    for mode in ("persistent", "per_instance", "graph"):
+        e = Ensemble(inst)
+        if packed is None:
+            packed = e.pack([W.ensemble_phi0(d) for d in inst])
+        e.set_phi(packed)
+        if mode == "persistent":
+            e.step(40)
+        elif mode == "per_instance":
+            e.step(40, mode=1)
+        else:
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                e.capture(10)
+                for _ in range(4):
+                    e.replay()
+            torch.cuda.current_stream().wait_stream(s)
+        outs.append(e.phi().cpu())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_ensemble_full_workload():
+    """256 instances (sides 64..1024, 48.6 M nodes), 1000 steps through a
+    replayed graph: finite, mass conserved per instance, and the six smallest
+    instances within the FP32 bar of the oracle."""
+    inst = W.ensemble()
+    e = Ensemble(inst)
+    phis = [W.ensemble_phi0(d) for d in inst]
+    e.set_phi(e.pack(phis))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        e.capture(100)
+        for _ in range(10):
+            e.replay()
+    torch.cuda.current_stream().wait_stream(s)
+    out = e.unpack(e.phi().cpu())
+    assert all(torch.isfinite(o).all() for o in out)
+    for p0, o in zip(phis, out):
+        assert abs(float(o.sum()) - p0.sum()) <= 1e-5 * p0.sum()
+    order = np.argsort([d["nx"] * d["ny"] for d in inst])[:6]
+    for i in order:
+        ref = oracle_phi(inst[i], phis[i], 1000)
+        assert rel(out[i].numpy(), ref) <= 1e-5, (i, rel(out[i].numpy(), ref))
