@@ -49,8 +49,12 @@ def parse():
     ap.add_argument("--lbm-steps", type=int, default=None, help="time steps per bench step")
     ap.add_argument("--variant", type=int, default=0, help="0 auto, 1 one node per thread, 2 four nodes per thread")
     ap.add_argument("--block-rows", type=int, default=0)
+    ap.add_argument("--tune", action="store_true", help="launch configuration from the autotuner")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ens-count", type=int, default=256, help="instances of the ensemble workload")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "ensemble_256", "adjoint_512"],
+                    help="the default is the headline workload; the others print their own line")
     return ap.parse_args()
 
 
@@ -64,6 +68,7 @@ def config(args, lbm_steps):
                         f"R=-0.1 phi, 4096x4096, phi=0 anti-bounce-back walls, {lbm_steps} steps per job",
             "nx": p["nx"], "ny": p["ny"], "lbm_steps_per_bench_step": lbm_steps,
             "storage": args.prec, "steps_per_pass": args.spp, "kernel_variant": args.variant,
+            "block_rows": args.block_rows, "autotuned": bool(args.tune),
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
             "l2": "inputs larger than L2 (two population buffers of 604 MB each, FP32)"}
 
@@ -179,10 +184,144 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def timed(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_ensemble(args):
+    """256 independent lattices (sides 64..1024), 1000 steps per job: one
+    persistent launch per step replayed from a CUDA graph, against one launch
+    per instance per step."""
+    import torch
+
+    from paper_1603_09577_gb300.ensemble import Ensemble
+    inst = W.ensemble(count=args.ens_count)
+    e = Ensemble(inst)
+    packed = e.pack([W.ensemble_phi0(d) for d in inst], dtype=torch.float32)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    steps = args.lbm_steps or 1000
+    with torch.cuda.stream(side):
+        e.set_phi(packed)
+        e.capture(100)
+
+        def job_graph():
+            e.set_phi(packed)
+            for _ in range(steps // 100):
+                e.replay()
+
+        def job_launches():
+            e.set_phi(packed)
+            e.step(steps, mode=1)
+
+        def job_persistent():
+            e.set_phi(packed)
+            e.step(steps, mode=0)
+
+        for _ in range(args.warmup):
+            job_graph()
+        clk = clocks_sampler()
+        ms_graph = timed(job_graph, args.steps, side)
+        clocks = clocks_summary(clk)
+        ms_pers = timed(job_persistent, max(1, args.steps // 2), side)
+        ms_sep = timed(job_launches, max(1, args.steps // 2), side)
+    nodes = e.nodes
+    val = nodes * steps / (ms_graph / 1e3) / 1e6
+    peak, src = measured_peak()
+    achieved = 72.0 * nodes * steps / (ms_graph / 1e3) / 1e9
+    out = {"metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"ensemble_256: 256 D2Q9 MRT instances, sides 64..1024 ({nodes} nodes), "
+                                  f"D(phi)=D0(1+phi), {steps} steps per job", "instances": len(inst),
+                      "tiles": e.tiles, "persistent_grid_blocks": e.grid},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "kernel": "k_ens_step (persistent, graph-replayed)",
+                        "peak_source": src},
+           "persistent_no_graph_mlups": nodes * steps / (ms_pers / 1e3) / 1e6,
+           "one_launch_per_instance_mlups": nodes * steps / (ms_sep / 1e3) / 1e6,
+           "graph_speedup_vs_per_instance": ms_sep / ms_graph,
+           "gpu_launches": args.steps * (1 + steps)}
+    if clocks is not None:
+        out["clocks"] = clocks
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint(args):
+    """512^2 linear anisotropic CDE with per-node K(x), 500 steps, checkpoints
+    every 50: time of one reverse (adjoint) step against one forward step, and
+    of the whole backward pass against the forward pass."""
+    import ctypes
+
+    import torch
+
+    from paper_1603_09577_gb300 import Solver, adjoint
+    from paper_1603_09577_gb300 import _lib as C
+    p = W.params("adjoint_512")
+    Kf, phi0, tgt = W.adjoint_inputs(512, seed=4)
+    prec = args.prec if args.prec in ("f32", "f64") else "f32"
+    st = torch.cuda.current_stream()
+    s = Solver(512, 512, prec=prec, per_cell_K=True)
+    s.set_coeffs(conv=0, u=p["u"], diff=0, s=W.s9())
+    s.set_K_field(torch.from_numpy(Kf).cuda())
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    state = s.save()
+    n = 200
+    ms_fwd = timed(lambda: s.step(1), n, st)
+    size = ctypes.c_size_t()
+    C.check(s.lib.lbm_adjoint_workspace_size(s.h, ctypes.byref(size)))
+    ws = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+    g = torch.from_numpy(tgt).cuda()
+    C.check(s.lib.lbm_adjoint_begin(s.h, ctypes.c_void_p(ws.data_ptr()), size.value, ctypes.c_void_p(g.data_ptr()),
+                                    C.LBM_F64, ctypes.c_void_p(st.cuda_stream)))
+    ms_adj = timed(lambda: C.check(s.lib.lbm_adjoint_step(s.h, ctypes.c_void_p(state.data_ptr()),
+                                                          ctypes.c_void_p(st.cuda_stream))), n, st)
+    # whole passes through the autograd Function
+    p0 = torch.from_numpy(phi0).cuda().requires_grad_(True)
+    K = torch.from_numpy(Kf).cuda().requires_grad_(True)
+    u = torch.tensor(p["u"], dtype=torch.float64, device="cuda", requires_grad=True)
+    t = torch.from_numpy(tgt).cuda()
+    for _ in range(args.warmup):
+        out = adjoint.run(p0, K, u, p["steps"], p["ckpt_every"], prec, W.s9())
+        (0.5 * ((out - t) ** 2).sum()).backward()
+    torch.cuda.synchronize()
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record(st)
+    out = adjoint.run(p0, K, u, p["steps"], p["ckpt_every"], prec, W.s9())
+    loss = 0.5 * ((out - t) ** 2).sum()
+    b.record(st)
+    loss.backward()
+    c.record(st)
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = a.elapsed_time(b), b.elapsed_time(c)
+    cells = 512 * 512
+    res = {"metric": "adjoint_step_over_forward_step", "value": ms_adj / ms_fwd, "unit": "ratio",
+           "higher_is_better": False, "n_gpus": 1, "steps": n, "warmup": args.warmup, "dtype": prec,
+           "data": "synthetic",
+           "config": {"workload": "adjoint_512: linear anisotropic CDE, per-node K(x), u=(0.03,0), 512x512, "
+                                  "500 steps, checkpoints every 50, FP64 gradient accumulation"},
+           "forward_step_ms": ms_fwd, "adjoint_step_ms": ms_adj,
+           "forward_mlups": cells / (ms_fwd / 1e3) / 1e6, "adjoint_mlups": cells / (ms_adj / 1e3) / 1e6,
+           "forward_pass_ms": fwd_ms, "backward_pass_ms": bwd_ms,
+           "backward_over_forward_pass": bwd_ms / fwd_ms}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble_256":
+        return run_ensemble(args)
+    if args.workload == "adjoint_512":
+        return run_adjoint(args)
     import torch
     import torch.distributed as dist
 
@@ -199,6 +338,10 @@ def main():
 
     phi0_np = W.phi0_aniso(4096, seed=3).astype(np.float32)
     phi0 = torch.from_numpy(phi0_np).cuda()
+    if args.tune:
+        from paper_1603_09577_gb300 import tune
+        cfg = tune.tune(nx, ny, args.prec, bc=("abb", "abb"), conv=p["conv"], diff=p["diff"])
+        args.spp, args.variant, args.block_rows = cfg["steps_per_pass"], cfg["kernel_variant"], cfg["block_rows"]
     s = Solver(nx, ny, prec=args.prec, bc=("abb", "abb"), phi_wall=p["phi_wall"], steps_per_pass=args.spp,
                kernel_variant=args.variant, block_rows=args.block_rows)
     s.set_coeffs(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"], s=W.s9(), r0=p["r0"], r1=p["r1"])

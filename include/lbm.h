@@ -164,6 +164,13 @@ int lbm_adjoint_begin(lbm_handle h, void *dev_ws, size_t bytes, const void *dev_
    is the forward post-collision state F_n in lbm_save layout. */
 int lbm_adjoint_step(lbm_handle h, const void *dev_state_n, void *stream);
 
+/* A whole checkpoint segment in one call: from the forward state F_t0
+   (dev_ckpt, lbm_save layout) recompute F_{t0+1} .. F_{t0+nsteps-1} into
+   dev_states ((nsteps - 1) * lbm_state_bytes bytes, caller-owned scratch), then
+   run the nsteps reverse steps over them, last first. Equivalent to nsteps
+   lbm_adjoint_step calls with the recomputed states. */
+int lbm_adjoint_segment(lbm_handle h, const void *dev_ckpt, int nsteps, void *dev_states, size_t bytes, void *stream);
+
 /* Finish at the initial condition F_0 = feq(phi0) (Eq. 40): dev_phi0 (nx*ny of
    `prec`); outputs dL/dphi0 (nx*ny doubles), dL/dK (3 planes of nx*ny doubles:
    dKxx, dKxy, dKyy per node, Kxy counted once) and dL/du (2 doubles). */
@@ -172,7 +179,7 @@ int lbm_adjoint_end(lbm_handle h, const void *dev_phi0, int prec, double *dev_dp
 
 /* ---- batched ensemble of independent lattices ---------------------------------
    Many lattices of different sizes and coefficients advanced together with one
-   persistent launch per time step over a work list of 32 x 32 tiles taken from
+   persistent launch per time step over a work list of 32 x 8 tiles taken from
    every instance (each step is Eq. 34 per instance, FP32 storage, periodic
    walls). All instances share the coefficient family; u, K and the relaxation
    rates are per instance; no source term. Fields of all instances are

@@ -63,6 +63,7 @@ SIGNATURES = {
     "lbm_adjoint_begin": [_VP, _VP, _SZ, _VP, _I, _VP],
     "lbm_adjoint_step": [_VP, _VP, _VP],
     "lbm_adjoint_end": [_VP, _VP, _I, _VP, _VP, _VP, _VP],
+    "lbm_adjoint_segment": [_VP, _VP, _I, _VP, _SZ, _VP],
     "lbm_ensemble_workspace_size": [_I, _VP, _VP, ctypes.POINTER(_SZ)],
     "lbm_ensemble_create": [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, _SZ],
     "lbm_ensemble_destroy": [_VP],

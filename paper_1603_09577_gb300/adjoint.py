@@ -53,20 +53,13 @@ class LBMRun(torch.autograd.Function):
         C.check(lib.lbm_adjoint_begin(s.h, _ptr(ws), size.value, _ptr(g), C.LBM_F64, st))
         nseg = len(ctx.ckpts)
         nb = s.state_bytes()
-        keep = None
+        scratch = torch.empty(max(1, min(L, nsteps) - 1) * nb, dtype=torch.uint8, device=s.device)
         for seg in range(nseg - 1, -1, -1):
             t0 = seg * L
             t1 = min(t0 + L, nsteps)
-            # states F_t0 .. F_{t1-1} of this segment
-            if keep is None or keep.shape[0] < t1 - t0:
-                keep = torch.empty((t1 - t0, nb), dtype=torch.uint8, device=s.device)
-            s.load(ctx.ckpts[seg])
-            s.save(keep[0])
-            for j in range(1, t1 - t0):
-                s.step(1)
-                s.save(keep[j])
-            for j in range(t1 - t0 - 1, -1, -1):
-                C.check(lib.lbm_adjoint_step(s.h, _ptr(keep[j]), st))
+            # recompute the segment's states from its checkpoint and walk them back
+            C.check(lib.lbm_adjoint_segment(s.h, _ptr(ctx.ckpts[seg]), t1 - t0, _ptr(scratch),
+                                            scratch.numel(), st))
         ny, nx = ctx.phi0.shape
         dphi0 = torch.empty((ny, nx), dtype=torch.float64, device=s.device)
         dK = torch.empty((3, ny, nx), dtype=torch.float64, device=s.device)

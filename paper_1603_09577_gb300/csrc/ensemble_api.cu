@@ -28,7 +28,7 @@ int ens_layout(int count, const int *nx, const int *ny, EnsLayout *L)
     long long tiles = 0;
     for (int i = 0; i < count; ++i) {
         if (nx[i] < 2 || ny[i] < 2) return fail(LBM_EINVAL, "instance " + std::to_string(i) + ": nx and ny must be >= 2");
-        tiles += (long long)((nx[i] + kEnsTile - 1) / kEnsTile) * ((ny[i] + kEnsTile - 1) / kEnsTile);
+        tiles += (long long)((nx[i] + kEnsTile - 1) / kEnsTile) * ((ny[i] + kEnsRows - 1) / kEnsRows);
     }
     if (tiles > (1LL << 30)) return fail(LBM_EINVAL, "too many tiles");
     L->ntiles = (int)tiles;
@@ -128,7 +128,7 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
         e->tile_begin[i] = (int)tiles.size();
         inst[i].phi_off = phi_off;
         phi_off += (long long)nx[i] * ny[i];
-        for (int ty = 0; ty < ny[i]; ty += kEnsTile)
+        for (int ty = 0; ty < ny[i]; ty += kEnsRows)
             for (int tx = 0; tx < nx[i]; tx += kEnsTile) tiles.push_back(make_int4(i, tx, ty, 0));
     }
     e->tile_begin[count] = (int)tiles.size();

@@ -81,10 +81,11 @@ __device__ __forceinline__ void add_inverse(const C dm[9], C f[9])
     f[8] += base_d + X2 - Y2 - pxyn;
 }
 
-// fixed-order block sum of two values into partial[0..1] (accumulated)
-__device__ __forceinline__ void block_add2(double a, double b, double *partial)
+// fixed-order block sum of two values, added in FP64 to partial[0..1]
+template <class C>
+__device__ __forceinline__ void block_add2(C a, C b, double *partial)
 {
-    __shared__ double sh[kAdjBX * kAdjBY / 32][2];
+    __shared__ C sh[kAdjBX * kAdjBY / 32][2];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, off);
@@ -95,10 +96,10 @@ __device__ __forceinline__ void block_add2(double a, double b, double *partial)
     if (lane == 0) { sh[w][0] = a; sh[w][1] = b; }
     __syncthreads();
     if (t == 0) {
-        double sa = sh[0][0], sb = sh[0][1];
+        C sa = sh[0][0], sb = sh[0][1];
         for (int q = 1; q < (int)(blockDim.x * blockDim.y) / 32; ++q) { sa += sh[q][0]; sb += sh[q][1]; }
-        partial[0] += sa;
-        partial[1] += sb;
+        partial[0] += (double)sa;
+        partial[1] += (double)sb;
     }
 }
 
@@ -110,7 +111,7 @@ k_adjoint_step(const Params<C> p, const C *__restrict__ F, const C *__restrict__
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const bool in = x < p.nx && y < p.ny;
-    double dux = 0.0, duy = 0.0;
+    C dux = C(0), duy = C(0);
     if (in) {
         const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
         const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
@@ -172,18 +173,15 @@ k_adjoint_step(const Params<C> p, const C *__restrict__ F, const C *__restrict__
         lam_out[6 * P + rm + xp] = L[6];
         lam_out[7 * P + rp + xp] = L[7];
         lam_out[8 * P + rp + xm] = L[8];
-        // parameter gradients of this step (FP64)
-        const double phi = (double)m[0];
-        const double d3 = (double)m[3] - (double)p.ux * phi, d5 = (double)m[5] - (double)p.uy * phi;
-        const double m3 = (double)mu3, m5 = (double)mu5;
-        gA[own] -= m3 * d3;
-        gA[P + own] -= m3 * d5 + m5 * d3;
-        gA[2 * P + own] -= m5 * d5;
-        const double ux = p.ux, uy = p.uy;
-        dux = phi * (6.0 * ux * ((double)sg[1] - (double)sg[2]) + (double)sg[3] - (double)sg[4] +
-                     2.0 * ux * (double)sg[7] + uy * (double)sg[8]);
-        duy = phi * (6.0 * uy * ((double)sg[1] - (double)sg[2]) + (double)sg[5] - (double)sg[6] -
-                     2.0 * uy * (double)sg[7] + ux * (double)sg[8]);
+        // parameter gradients of this step: products in the compute type, the
+        // running sums over steps in FP64
+        const C phi = m[0];
+        const C d3 = m[3] - p.ux * phi, d5 = m[5] - p.uy * phi;
+        gA[own] -= (double)(mu3 * d3);
+        gA[P + own] -= (double)(mu3 * d5 + mu5 * d3);
+        gA[2 * P + own] -= (double)(mu5 * d5);
+        dux = phi * (C(6) * p.ux * (sg[1] - sg[2]) + sg[3] - sg[4] + C(2) * p.ux * sg[7] + p.uy * sg[8]);
+        duy = phi * (C(6) * p.uy * (sg[1] - sg[2]) + sg[5] - sg[6] - C(2) * p.uy * sg[7] + p.ux * sg[8]);
     }
     block_add2(dux, duy, partials + 2 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x));
 }

@@ -1,5 +1,5 @@
 // kernels_ensemble.cu -- many independent lattices advanced together: one
-// persistent launch per time step over a work list of 32 x 32 tiles drawn from
+// persistent launch per time step over a work list of 32 x 8 tiles drawn from
 // every instance (FP32 storage, periodic walls, one coefficient family shared,
 // per-instance u, K and relaxation rates). Blocks take tiles round-robin (t = blockIdx.x,
 // blockIdx.x + gridDim.x, ...): tiles have equal shape, so the static split is
@@ -12,17 +12,17 @@ template <int CONV, int DIFF>
 __device__ __forceinline__ void ens_tile(const EnsInst &I, int tx0, int ty0, int parity)
 {
     const Params<float> p = ens_params(I);
-    const float *__restrict__ src = I.pop[parity];
-    float *__restrict__ dst = I.pop[parity ^ 1];
+    // select with a conditional: a runtime index into the struct's array would
+    // put the struct in local memory
+    const float *__restrict__ src = parity ? I.pop[1] : I.pop[0];
+    float *__restrict__ dst = parity ? I.pop[0] : I.pop[1];
     const int x = tx0 + threadIdx.x;
-    if (x >= p.nx) return;
+    const int y = ty0 + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
     const int xm = x == 0 ? p.nx - 1 : x - 1;
     const int xp = x == p.nx - 1 ? 0 : x + 1;
     const long long P = p.plane;
-#pragma unroll 1
-    for (int r = threadIdx.y; r < kEnsTile; r += blockDim.y) {
-        const int y = ty0 + r;
-        if (y >= p.ny) break;
+    {
         const int ym = y == 0 ? p.ny - 1 : y - 1;
         const int yp = y == p.ny - 1 ? 0 : y + 1;
         const long long r0 = (long long)y * p.pitch, rm = (long long)ym * p.pitch, rp = (long long)yp * p.pitch;
@@ -69,9 +69,9 @@ k_ens_init(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int
         const Params<float> p = ens_params(I);
         const int x = tl.y + threadIdx.x;
         if (x >= I.nx) continue;
-        for (int r = threadIdx.y; r < kEnsTile; r += blockDim.y) {
-            const int y = tl.z + r;
-            if (y >= I.ny) break;
+        {
+            const int y = tl.z + threadIdx.y;
+            if (y >= I.ny) continue;
             const long long i = I.phi_off + (long long)y * I.nx + x;
             const float ph = in_prec == LBM_F64 ? (float)((const double *)phi)[i] : ((const float *)phi)[i];
             float f[9], phi_c;
@@ -79,7 +79,7 @@ k_ens_init(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int
             collide<float, CONV, DIFF>(p, f, p.A3, p.A35, p.A5, phi_c);
             const long long own = (long long)y * I.pitch + x;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) I.pop[parity][k * I.plane + own] = f[k];
+            for (int k = 0; k < 9; ++k) (parity ? I.pop[1] : I.pop[0])[k * I.plane + own] = f[k];
         }
     }
 }
@@ -93,11 +93,11 @@ k_ens_get_phi(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, 
         const EnsInst I = inst[tl.x];
         const int x = tl.y + threadIdx.x;
         if (x >= I.nx) continue;
-        for (int r = threadIdx.y; r < kEnsTile; r += blockDim.y) {
-            const int y = tl.z + r;
-            if (y >= I.ny) break;
+        {
+            const int y = tl.z + threadIdx.y;
+            if (y >= I.ny) continue;
             const long long own = (long long)y * I.pitch + x;
-            const float *f = I.pop[parity];
+            const float *f = parity ? I.pop[1] : I.pop[0];
             float s = f[own];
 #pragma unroll
             for (int k = 1; k < 9; ++k) s += f[k * I.plane + own];
@@ -121,7 +121,7 @@ k_ens_get_phi(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, 
 
 cudaError_t ens_launch_step(const lbm_ensemble_s *e, int t_begin, int t_end, int blocks, cudaStream_t st)
 {
-    dim3 block(kEnsTile, kEnsThreads / kEnsTile);
+    dim3 block(kEnsTile, kEnsRows);
 #define CALL(A, B) k_ens_step<A, B><<<blocks, block, 0, st>>>(e->d_inst, e->d_tiles, t_begin, t_end, e->parity)
     LBM_ENS_DISPATCH(e->family, CALL)
 #undef CALL
@@ -130,7 +130,7 @@ cudaError_t ens_launch_step(const lbm_ensemble_s *e, int t_begin, int t_end, int
 
 cudaError_t ens_launch_init(const lbm_ensemble_s *e, const void *phi, int in_prec, cudaStream_t st)
 {
-    dim3 block(kEnsTile, kEnsThreads / kEnsTile);
+    dim3 block(kEnsTile, kEnsRows);
 #define CALL(A, B) k_ens_init<A, B><<<e->grid, block, 0, st>>>(e->d_inst, e->d_tiles, e->ntiles, phi, in_prec, e->parity)
     LBM_ENS_DISPATCH(e->family, CALL)
 #undef CALL
@@ -139,7 +139,7 @@ cudaError_t ens_launch_init(const lbm_ensemble_s *e, const void *phi, int in_pre
 
 cudaError_t ens_launch_get_phi(const lbm_ensemble_s *e, void *out, int out_prec, cudaStream_t st)
 {
-    dim3 block(kEnsTile, kEnsThreads / kEnsTile);
+    dim3 block(kEnsTile, kEnsRows);
     k_ens_get_phi<<<e->grid, block, 0, st>>>(e->d_inst, e->d_tiles, e->ntiles, e->parity, out, out_prec);
     return cudaGetLastError();
 }

@@ -71,7 +71,8 @@ k_step(const Params<typename Store<PREC>::C> p, const typename Store<PREC>::T *_
 }
 
 template <int PREC, int CONV, int DIFF>
-static cudaError_t step_t(const lbm_solver *s, int src, cudaStream_t st)
+static cudaError_t step_t(const lbm_solver *s, const void *src, const float *src_h, void *dst, float *dst_h,
+                          cudaStream_t st)
 {
     using S = Store<PREC>;
     using T = typename S::T;
@@ -80,22 +81,36 @@ static cudaError_t step_t(const lbm_solver *s, int src, cudaStream_t st)
     const int by = s->d.block_rows > 0 ? s->d.block_rows : 8;
     dim3 block(32, by);
     dim3 grid((s->d.nx + 31) / 32, (s->d.ny + by - 1) / by);
-    k_step<PREC, CONV, DIFF><<<grid, block, 0, st>>>(p, (const T *)s->pop[src], s->phi[src], (T *)s->pop[src ^ 1],
-                                                      s->phi[src ^ 1]);
+    k_step<PREC, CONV, DIFF><<<grid, block, 0, st>>>(p, (const T *)src, src_h, (T *)dst, dst_h);
     return cudaGetLastError();
 }
 
 template <int PREC>
-static cudaError_t step_p(const lbm_solver *s, int src, cudaStream_t st)
+static cudaError_t step_p(const lbm_solver *s, const void *src, const float *src_h, void *dst, float *dst_h,
+                          cudaStream_t st)
 {
     const int key = s->c.conv * 3 + s->c.diff;
     switch (key) {
-    case 0: return step_t<PREC, 0, 0>(s, src, st);
-    case 1: return step_t<PREC, 0, 1>(s, src, st);
-    case 2: return step_t<PREC, 0, 2>(s, src, st);
-    case 3: return step_t<PREC, 1, 0>(s, src, st);
-    case 4: return step_t<PREC, 1, 1>(s, src, st);
-    case 5: return step_t<PREC, 1, 2>(s, src, st);
+    case 0: return step_t<PREC, 0, 0>(s, src, src_h, dst, dst_h, st);
+    case 1: return step_t<PREC, 0, 1>(s, src, src_h, dst, dst_h, st);
+    case 2: return step_t<PREC, 0, 2>(s, src, src_h, dst, dst_h, st);
+    case 3: return step_t<PREC, 1, 0>(s, src, src_h, dst, dst_h, st);
+    case 4: return step_t<PREC, 1, 1>(s, src, src_h, dst, dst_h, st);
+    case 5: return step_t<PREC, 1, 2>(s, src, src_h, dst, dst_h, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// one step between explicit state buffers (lbm_save layout; shift planes follow
+// the populations for LBM_BF16S)
+cudaError_t launch_step_ptr(const lbm_solver *s, const void *src, void *dst, cudaStream_t st)
+{
+    const float *src_h = s->L.phi_bytes ? (const float *)((const char *)src + s->L.pop_bytes) : nullptr;
+    float *dst_h = s->L.phi_bytes ? (float *)((char *)dst + s->L.pop_bytes) : nullptr;
+    switch (s->d.prec) {
+    case LBM_F64: return step_p<LBM_F64>(s, src, src_h, dst, dst_h, st);
+    case LBM_F32: return step_p<LBM_F32>(s, src, src_h, dst, dst_h, st);
+    case LBM_BF16S: return step_p<LBM_BF16S>(s, src, src_h, dst, dst_h, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -103,13 +118,11 @@ static cudaError_t step_p(const lbm_solver *s, int src, cudaStream_t st)
 cudaError_t launch_step(const lbm_solver *s, int src, cudaStream_t st)
 {
     switch (s->d.prec) {
-    case LBM_F64: return step_p<LBM_F64>(s, src, st);
-    case LBM_F32: return step_p<LBM_F32>(s, src, st);
-    case LBM_BF16S: return step_p<LBM_BF16S>(s, src, st);
+    case LBM_F64: return step_p<LBM_F64>(s, s->pop[src], s->phi[src], s->pop[src ^ 1], s->phi[src ^ 1], st);
+    case LBM_F32: return step_p<LBM_F32>(s, s->pop[src], s->phi[src], s->pop[src ^ 1], s->phi[src ^ 1], st);
+    case LBM_BF16S: return step_p<LBM_BF16S>(s, s->pop[src], s->phi[src], s->pop[src ^ 1], s->phi[src ^ 1], st);
     }
     return cudaErrorInvalidValue;
 }
-
-cudaError_t launch_step2(const lbm_solver *, int, cudaStream_t) { return cudaErrorNotSupported; }
 
 }  // namespace lbm

@@ -69,7 +69,8 @@ static int check_desc(const lbm_desc *d)
     for (int i = 0; i < 4; ++i)
         if (!isfinite(d->phi_wall[i])) return fail(LBM_EINVAL, "non-finite wall value");
     if (d->steps_per_pass != 1 && d->steps_per_pass != 2) return fail(LBM_EINVAL, "steps_per_pass must be 1 or 2");
-    if (d->steps_per_pass == 2) return fail(LBM_EUNSUPPORTED, "two steps per pass is not built yet");
+    if (d->steps_per_pass == 2 && d->prec == LBM_F64)
+        return fail(LBM_EUNSUPPORTED, "two steps per pass is built for LBM_F32 and LBM_BF16S");
     if (d->kernel_variant < 0 || d->kernel_variant > 2) return fail(LBM_EINVAL, "kernel_variant must be 0, 1 or 2");
     if (d->kernel_variant == 2 && !(d->prec != LBM_F64 && d->nx % 4 == 0))
         return fail(LBM_EUNSUPPORTED, "kernel_variant 2 needs LBM_F32 or LBM_BF16S and nx % 4 == 0");
@@ -400,6 +401,31 @@ int lbm_adjoint_step(lbm_handle h, const void *dev_state_n, void *stream)
                                                 h->adj_partials, st), "lbm_adjoint_step"))
         return rc;
     h->adj_cur ^= 1;
+    return LBM_OK;
+}
+
+int lbm_adjoint_segment(lbm_handle h, const void *dev_ckpt, int nsteps, void *dev_states, size_t bytes, void *stream)
+{
+    if (int rc = adjoint_supported(h)) return rc;
+    if (!h->adj_active) return fail(LBM_EINVAL, "lbm_adjoint_begin has not been called");
+    if (!dev_ckpt) return fail(LBM_EINVAL, "null checkpoint");
+    if (nsteps < 1) return fail(LBM_EINVAL, "segment length must be >= 1");
+    const size_t sb = h->L.pop_bytes + h->L.phi_bytes;
+    if (nsteps > 1 && (!dev_states || bytes < (size_t)(nsteps - 1) * sb))
+        return fail(LBM_EINVAL, "state scratch smaller than (nsteps - 1) * lbm_state_bytes");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto state = [&](int j) -> const void * { return j == 0 ? dev_ckpt : (const char *)dev_states + (size_t)(j - 1) * sb; };
+    // recompute F_{t0+1} .. F_{t0+nsteps-1} from the checkpoint
+    for (int j = 1; j < nsteps; ++j)
+        if (int rc = cuda_check(launch_step_ptr(h, state(j - 1), (void *)state(j), st), "lbm_adjoint_segment recompute"))
+            return rc;
+    // reverse steps over the segment, last state first
+    for (int j = nsteps - 1; j >= 0; --j) {
+        if (int rc = cuda_check(launch_adjoint_step(h, state(j), h->lam[h->adj_cur], h->lam[h->adj_cur ^ 1], h->gA,
+                                                    h->adj_partials, st), "lbm_adjoint_segment reverse step"))
+            return rc;
+        h->adj_cur ^= 1;
+    }
     return LBM_OK;
 }
 

@@ -5,8 +5,9 @@
 
 namespace lbm {
 
-constexpr int kEnsTile = 32;        // tiles are 32 x 32 nodes
-constexpr int kEnsThreads = 256;    // 32 x 8 threads, four rows per thread
+constexpr int kEnsTile = 32;        // tile width (nodes along x)
+constexpr int kEnsRows = 8;         // tile height: one node per thread
+constexpr int kEnsThreads = kEnsTile * kEnsRows;
 
 // Per-instance data read by the kernels (device table).
 struct __align__(16) EnsInst {

@@ -1,0 +1,96 @@
+"""Autotuner of the launch configuration of one lattice.
+
+For a problem (grid, storage precision, walls, coefficient family) it times the
+candidate configurations on the current device -- kernel variant (one node or
+four x-adjacent nodes per thread), rows per thread block, and one or two time
+steps per sweep through memory -- on a synthetic field, and keeps the fastest in
+a JSON cache keyed by device name and problem, so later runs reuse it.
+
+    cfg = tune(4096, 4096, "f32", bc=("abb", "abb"), conv=0, diff=2)
+    s = Solver(4096, 4096, prec="f32", bc=("abb", "abb"), **cfg)
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import torch
+
+from .solver import Solver
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("LBM_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "lbm_gb300", "tune.json"))
+
+
+def _key(nx, ny, prec, bc, conv, diff, per_cell_K):
+    dev = torch.cuda.get_device_name()
+    return f"{dev}|{nx}x{ny}|{prec}|{bc[0]},{bc[1]}|c{conv}d{diff}|K{int(per_cell_K)}"
+
+
+def candidates(nx: int, prec: str):
+    out = [dict(kernel_variant=1, block_rows=b, steps_per_pass=1) for b in (1, 2, 4, 8)]
+    if prec != "f64" and nx % 4 == 0:
+        out += [dict(kernel_variant=2, block_rows=b, steps_per_pass=1) for b in (1, 2, 4, 8)]
+    if prec != "f64":
+        out.append(dict(kernel_variant=0, block_rows=0, steps_per_pass=2))
+    return out
+
+
+def _time(cfg, nx, ny, prec, bc, conv, diff, per_cell_K, steps, reps):
+    s = Solver(nx, ny, prec=prec, bc=bc, per_cell_K=per_cell_K, **cfg)
+    s.set_coeffs(conv=conv, u=(0.02, 0.01), diff=diff, K=(0.02, 0.004, 0.015))
+    if per_cell_K:
+        K = torch.zeros((3, ny, nx), dtype=torch.float64, device="cuda")
+        K[0] = 0.02
+        K[2] = 0.015
+        s.set_K_field(K)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    phi0 = 0.5 + 0.1 * torch.rand((ny, nx), generator=g, device="cuda", dtype=torch.float64)
+    s.set_phi(phi0)
+    st = torch.cuda.current_stream()
+    s.step(steps)                                    # warm-up
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        s.step(steps)
+        b.record(st)
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b) / steps)
+    del s
+    return best
+
+
+def tune(nx: int, ny: int, prec: str = "f32", bc=("periodic", "periodic"), conv: int = 0, diff: int = 0,
+         per_cell_K: bool = False, steps: int = 20, reps: int = 3, use_cache: bool = True) -> dict:
+    """Fastest launch configuration (kwargs for Solver) for this problem."""
+    key = _key(nx, ny, prec, bc, conv, diff, per_cell_K)
+    path = cache_path()
+    with _lock:
+        cache = {}
+        if use_cache and os.path.exists(path):
+            try:
+                with open(path) as f:
+                    cache = json.load(f)
+            except (OSError, ValueError):
+                cache = {}
+        if use_cache and key in cache:
+            return dict(cache[key]["config"])
+        timings = []
+        for cfg in candidates(nx, prec):
+            ms = _time(cfg, nx, ny, prec, bc, conv, diff, per_cell_K, steps, reps)
+            timings.append((ms, cfg))
+        ms, best = min(timings, key=lambda t: t[0])
+        cache[key] = {"config": best, "ms_per_step": ms,
+                      "all": [{"config": c, "ms_per_step": t} for t, c in timings]}
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, path)
+        return dict(best)

@@ -56,6 +56,10 @@ def test_workspace_size_and_layout():
     assert rc == 0 and nb < n32
     rc, nk = ws_size(desc(per_cell_K=1))
     assert rc == 0 and nk > n32
+    rc, _ = ws_size(desc(steps_per_pass=2))
+    assert rc == 0
+    rc, _ = ws_size(desc(steps_per_pass=2, prec=C.LBM_F64))
+    assert rc == C.LBM_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(prec=7), dict(bc_x=3), dict(steps_per_pass=3),

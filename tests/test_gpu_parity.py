@@ -78,6 +78,46 @@ def test_parity_families_and_walls(prec, variant, case):
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
+TB = [(c, prec, n) for c in CASES for prec in ("f32", "bf16s") for n in (60, 61)]
+
+
+@pytest.mark.parametrize("case,prec,steps", TB, ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}-{p}-{n}" for c, p, n in TB])
+def test_two_steps_per_pass(case, prec, steps):
+    """Temporal blocking (two steps per sweep; an odd count ends with one step)."""
+    nx, ny, bc, conv, diff, u, K, r0, r1 = case
+    rng = np.random.default_rng(nx * 131 + ny)
+    phi0 = W.jacobi_smooth(rng.uniform(0.05, 0.95, (ny, nx)), 2)
+    walls = (0.3, 0.7, 0.1, 0.5) if bc != (0, 0) else (0, 0, 0, 0)
+    coef = dict(conv=conv, u=u, diff=diff, K=K, r0=r0, r1=r1)
+    ref = run_oracle(nx, ny, phi0, steps, bc, walls, **coef)
+    got, _ = run_gpu(prec, nx, ny, phi0, steps, bc, walls, spp=2, **coef)
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
+def test_two_steps_per_pass_per_cell_tensor():
+    nx, ny = 70, 45
+    Kf, phi0, _ = W.adjoint_inputs(nx, seed=8, ny=ny)
+    coef = dict(conv=0, u=(0.03, 0.01), diff=0, K=(0.0, 0.0, 0.0))
+    ref = run_oracle(nx, ny, phi0, 40, Kfield=Kf, **coef)
+    got, _ = run_gpu("f32", nx, ny, phi0, 40, Kfield=Kf, spp=2, **coef)
+    assert rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16s"])
+def test_aniso_dirichlet_two_steps_per_pass(prec):
+    """The 4096^2 Dirichlet workload with temporal blocking: all elements after
+    12 steps, and all 2000 steps on 512^2."""
+    coef, p = aniso_coef()
+    phi0 = W.phi0_aniso(4096, seed=3)
+    ref = run_oracle(4096, 4096, phi0, 12, p["bc"], p["phi_wall"], **coef)
+    got, _ = run_gpu(prec, 4096, 4096, phi0, 12, p["bc"], p["phi_wall"], spp=2, **coef)
+    assert rel(got, ref) <= TOL[prec]
+    phi0 = W.phi0_aniso(512, seed=3)
+    ref = run_oracle(512, 512, phi0, p["steps"], p["bc"], p["phi_wall"], **coef)
+    got, _ = run_gpu(prec, 512, 512, phi0, p["steps"], p["bc"], p["phi_wall"], spp=2, **coef)
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
 @pytest.mark.parametrize("variant", [1, 2])
 def test_block_shapes(variant):
     nx, ny = 196, 45
