@@ -35,7 +35,7 @@ import workloads as W  # noqa: E402
 WORKLOAD = "aniso_dirichlet_4096"
 BYTES_PER_UPDATE = {"f32": 72, "bf16s": 44, "f64": 144}
 KERNEL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
-              for f in ("kernels_step.cu", "kernels_step_vec.cu", "lbm_device.cuh")]
+              for f in ("kernels_step.cu", "kernels_step_vec.cu", "kernels_step2.cu", "lbm_device.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--lbm-steps", type=int, default=None, help="time steps per bench step")
     ap.add_argument("--variant", type=int, default=0, help="0 auto, 1 one node per thread, 2 four nodes per thread")
     ap.add_argument("--block-rows", type=int, default=0)
-    ap.add_argument("--tune", action="store_true", help="launch configuration from the autotuner")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="use --variant/--block-rows/--spp as given instead of the autotuner's choice")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ens-count", type=int, default=256, help="instances of the ensemble workload")
@@ -68,7 +69,7 @@ def config(args, lbm_steps):
                         f"R=-0.1 phi, 4096x4096, phi=0 anti-bounce-back walls, {lbm_steps} steps per job",
             "nx": p["nx"], "ny": p["ny"], "lbm_steps_per_bench_step": lbm_steps,
             "storage": args.prec, "steps_per_pass": args.spp, "kernel_variant": args.variant,
-            "block_rows": args.block_rows, "autotuned": bool(args.tune),
+            "block_rows": args.block_rows, "autotuned": bool(getattr(args, "autotuned", False)),
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
             "l2": "inputs larger than L2 (two population buffers of 604 MB each, FP32)"}
 
@@ -338,10 +339,11 @@ def main():
 
     phi0_np = W.phi0_aniso(4096, seed=3).astype(np.float32)
     phi0 = torch.from_numpy(phi0_np).cuda()
-    if args.tune:
+    if args.tune and args.variant == 0 and args.block_rows == 0 and args.spp == 1:
         from paper_1603_09577_gb300 import tune
         cfg = tune.tune(nx, ny, args.prec, bc=("abb", "abb"), conv=p["conv"], diff=p["diff"])
         args.spp, args.variant, args.block_rows = cfg["steps_per_pass"], cfg["kernel_variant"], cfg["block_rows"]
+        args.autotuned = True
     s = Solver(nx, ny, prec=args.prec, bc=("abb", "abb"), phi_wall=p["phi_wall"], steps_per_pass=args.spp,
                kernel_variant=args.variant, block_rows=args.block_rows)
     s.set_coeffs(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"], s=W.s9(), r0=p["r0"], r1=p["r1"])
@@ -417,14 +419,18 @@ def main():
         achieved = alg_bytes / (launch_ms / 1e3) / 1e9
         peak, src = measured_peak()
         sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRC)).hexdigest()
+        kernel = ("k_step2 (two fused pull-stream + collide steps per sweep)" if args.spp == 2 else
+                  "k_step_v4 (fused pull-stream + collide, four nodes per thread)" if args.variant == 2 or
+                  (args.variant == 0 and args.prec == "bf16s") else "k_step (fused pull-stream + collide)")
         out = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.prec, "data": "synthetic", "config": config(args, lbm_steps),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic_per_launch(sha),
-                         "kernel": "k_step_v4 (fused pull-stream + collide, four nodes per thread)"
-                         if args.variant != 1 and args.prec != "f64" else "k_step (fused pull-stream + collide)",
+                         "kernel": kernel,
+                         "one_step_roof_mlups": peak * 1e3 / BYTES_PER_UPDATE[args.prec],
+                         "value_over_one_step_roof": value / world / (peak * 1e3 / BYTES_PER_UPDATE[args.prec]),
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_ms,
                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src},
             "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": int(host_in.numel() * 4),
