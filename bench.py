@@ -63,6 +63,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, cells: int, lbm_steps: int, ms_per_step: float) -> float:
+    """Units all ranks processed (each rank runs the full workload: replicas) per second."""
+    return world * cells * lbm_steps / (ms_per_step / 1e3) / 1e6
+
+
 def config(args, lbm_steps):
     p = W.params(WORKLOAD)
     return {"workload": f"{WORKLOAD}: D2Q9 MRT, D(phi)=(1+phi^2)K, K=[[0.02,0.008],[0.008,0.01]], "
@@ -381,14 +397,12 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     step_kernels_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
     mass = float(red[0].item())
+    total_ms = max_over_ranks(total_ms, device="cuda")
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
 
     ms_per_step = total_ms / args.steps
-    value = world * cells * lbm_steps / (ms_per_step / 1e3) / 1e6
+    value = whole_job_mlups(world, cells, lbm_steps, ms_per_step)
 
     # end to end through the C ABI with host buffers (pinned), copies included
     host_in = torch.from_numpy(phi0_np).pin_memory()
@@ -403,12 +417,8 @@ def main():
         s.set_phi_host(host_in)
         s.step(lbm_steps)
         s.phi_host(host_out)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = world * cells * lbm_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
+    e2e_val = whole_job_mlups(world, cells, lbm_steps, e2e_s * 1e3)
 
     if rank == 0:
         launches_per_job = lbm_steps // args.spp + lbm_steps % args.spp

@@ -68,9 +68,13 @@ typedef struct {
     int per_cell_K;         /* 1: K comes from lbm_set_K_field                    */
     int kernel_variant;     /* 0: automatic; 1: one node per thread; 2: four
                                x-adjacent nodes per thread with vector loads
-                               (LBM_F32 / LBM_BF16S, nx % 4 == 0)                 */
+                               (LBM_F32 / LBM_BF16S, nx % 4 == 0); 3: with
+                               steps_per_pass 2, the register column march (each
+                               warp walks a 30-column strip) instead of the
+                               shared-memory tile kernel                          */
     int block_rows;         /* rows of 32-thread warps per thread block: 0 (= 8),
-                               1, 2, 4 or 8                                       */
+                               1, 2, 4 or 8; for kernel_variant 3 the rows each
+                               warp marches are 16 * block_rows (0: 64)           */
 } lbm_desc;
 
 /* Coefficient families of Eq. 1 (Sec. 2.1), source and relaxation rates. */

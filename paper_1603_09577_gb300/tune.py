@@ -2,8 +2,9 @@
 
 For a problem (grid, storage precision, walls, coefficient family) it times the
 candidate configurations on the current device -- kernel variant (one node or
-four x-adjacent nodes per thread), rows per thread block, and one or two time
-steps per sweep through memory -- on a synthetic field, and keeps the fastest in
+four x-adjacent nodes per thread), rows per thread block, one or two time steps
+per sweep through memory (shared-memory tiles or the register column march with
+16 to 128 rows per warp) -- on a synthetic field, and keeps the fastest in
 a JSON cache keyed by device name and problem, so later runs reuse it.
 
     cfg = tune(4096, 4096, "f32", bc=("abb", "abb"), conv=0, diff=2)
@@ -38,6 +39,7 @@ def candidates(nx: int, prec: str):
         out += [dict(kernel_variant=2, block_rows=b, steps_per_pass=1) for b in (1, 2, 4, 8)]
     if prec != "f64":
         out.append(dict(kernel_variant=0, block_rows=0, steps_per_pass=2))
+        out += [dict(kernel_variant=3, block_rows=b, steps_per_pass=2) for b in (1, 2, 4, 8)]
     return out
 
 

@@ -78,20 +78,34 @@ def test_parity_families_and_walls(prec, variant, case):
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
-TB = [(c, prec, n) for c in CASES for prec in ("f32", "bf16s") for n in (60, 61)]
+TB = [(c, prec, n, v) for c in CASES for prec in ("f32", "bf16s") for n in (60, 61) for v in (0, 3)]
 
 
-@pytest.mark.parametrize("case,prec,steps", TB, ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}-{p}-{n}" for c, p, n in TB])
-def test_two_steps_per_pass(case, prec, steps):
-    """Temporal blocking (two steps per sweep; an odd count ends with one step)."""
+@pytest.mark.parametrize("case,prec,steps,variant", TB,
+                         ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}-{p}-{n}-v{v}" for c, p, n, v in TB])
+def test_two_steps_per_pass(case, prec, steps, variant):
+    """Temporal blocking (two steps per sweep; an odd count ends with one step):
+    the shared-memory tile kernel (variant 0) and the register column march (3)."""
     nx, ny, bc, conv, diff, u, K, r0, r1 = case
     rng = np.random.default_rng(nx * 131 + ny)
     phi0 = W.jacobi_smooth(rng.uniform(0.05, 0.95, (ny, nx)), 2)
     walls = (0.3, 0.7, 0.1, 0.5) if bc != (0, 0) else (0, 0, 0, 0)
     coef = dict(conv=conv, u=u, diff=diff, K=K, r0=r0, r1=r1)
     ref = run_oracle(nx, ny, phi0, steps, bc, walls, **coef)
-    got, _ = run_gpu(prec, nx, ny, phi0, steps, bc, walls, spp=2, **coef)
+    got, _ = run_gpu(prec, nx, ny, phi0, steps, bc, walls, spp=2, variant=variant, **coef)
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
+@pytest.mark.parametrize("block_rows", [1, 2, 8])
+def test_column_march_segment_heights(block_rows):
+    nx, ny = 100, 75
+    phi0 = W.phi0_aniso(nx, seed=12, ny=ny)
+    coef = dict(conv=1, u=(0.06, -0.03), diff=2, K=(0.02, 0.008, 0.01), r1=-0.05)
+    for bc in ((1, 1), (0, 0), (0, 1)):
+        walls = (0.2, 0.3, 0.4, 0.5) if bc != (0, 0) else (0, 0, 0, 0)
+        ref = run_oracle(nx, ny, phi0, 24, bc, walls, **coef)
+        got, _ = run_gpu("f32", nx, ny, phi0, 24, bc, walls, spp=2, variant=3, block_rows=block_rows, **coef)
+        assert rel(got, ref) <= 1e-5, (bc, rel(got, ref))
 
 
 def test_two_steps_per_pass_per_cell_tensor():
@@ -99,22 +113,23 @@ def test_two_steps_per_pass_per_cell_tensor():
     Kf, phi0, _ = W.adjoint_inputs(nx, seed=8, ny=ny)
     coef = dict(conv=0, u=(0.03, 0.01), diff=0, K=(0.0, 0.0, 0.0))
     ref = run_oracle(nx, ny, phi0, 40, Kfield=Kf, **coef)
-    got, _ = run_gpu("f32", nx, ny, phi0, 40, Kfield=Kf, spp=2, **coef)
-    assert rel(got, ref) <= 1e-5
+    for v in (0, 3):
+        got, _ = run_gpu("f32", nx, ny, phi0, 40, Kfield=Kf, spp=2, variant=v, **coef)
+        assert rel(got, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("prec", ["f32", "bf16s"])
-def test_aniso_dirichlet_two_steps_per_pass(prec):
+@pytest.mark.parametrize("prec,variant", [("f32", 0), ("bf16s", 0), ("f32", 3), ("bf16s", 3)])
+def test_aniso_dirichlet_two_steps_per_pass(prec, variant):
     """The 4096^2 Dirichlet workload with temporal blocking: all elements after
     12 steps, and all 2000 steps on 512^2."""
     coef, p = aniso_coef()
     phi0 = W.phi0_aniso(4096, seed=3)
     ref = run_oracle(4096, 4096, phi0, 12, p["bc"], p["phi_wall"], **coef)
-    got, _ = run_gpu(prec, 4096, 4096, phi0, 12, p["bc"], p["phi_wall"], spp=2, **coef)
+    got, _ = run_gpu(prec, 4096, 4096, phi0, 12, p["bc"], p["phi_wall"], spp=2, variant=variant, **coef)
     assert rel(got, ref) <= TOL[prec]
     phi0 = W.phi0_aniso(512, seed=3)
     ref = run_oracle(512, 512, phi0, p["steps"], p["bc"], p["phi_wall"], **coef)
-    got, _ = run_gpu(prec, 512, 512, phi0, p["steps"], p["bc"], p["phi_wall"], spp=2, **coef)
+    got, _ = run_gpu(prec, 512, 512, phi0, p["steps"], p["bc"], p["phi_wall"], spp=2, variant=variant, **coef)
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
@@ -212,7 +227,7 @@ def test_burgers_short(prec):
     assert rel(got, ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["f32", "bf16s"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16s"])
 def test_burgers_full_steps_reduced_grid(prec):
     """All 5000 steps of the Burgers workload on 256^2 (same scaling, K = 0.005 n)."""
     p = W.params("burgers_1024")
@@ -222,6 +237,22 @@ def test_burgers_full_steps_reduced_grid(prec):
     ref = run_oracle(n, n, phi0, p["steps"], **coef)
     got, _ = run_gpu(prec, n, n, phi0, p["steps"], **coef)
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
+def test_burgers_full_size_properties():
+    """Full 1024^2 x 5000 steps: bounded by the initial amplitude, mass conserved,
+    FP32 and BF16S within their bars of the FP64 CUDA path (pinned to the oracle
+    at 1e-12 on the same workload at 256^2 and for 50 steps at 1024^2), also with
+    two steps per sweep."""
+    p = W.params("burgers_1024")
+    phi0 = W.phi0_burgers()
+    coef = dict(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"])
+    f64, s64 = run_gpu("f64", 1024, 1024, phi0, p["steps"], **coef)
+    assert np.isfinite(f64).all() and np.abs(f64).max() <= 0.5 + 1e-3
+    assert abs(f64.sum() - phi0.sum()) <= 1e-9 * np.abs(phi0).sum()
+    for prec, spp in (("f32", 1), ("f32", 2), ("bf16s", 1), ("bf16s", 2)):
+        got, _ = run_gpu(prec, 1024, 1024, phi0, p["steps"], spp=spp, **coef)
+        assert rel(got, f64) <= TOL[prec], (prec, spp, rel(got, f64))
 
 
 def test_reductions_match_numpy():
