@@ -74,7 +74,9 @@ typedef struct {
                                shared-memory tile kernel                          */
     int block_rows;         /* rows of 32-thread warps per thread block: 0 (= 8),
                                1, 2, 4 or 8; for kernel_variant 3 the rows each
-                               warp marches are 16 * block_rows (0: 64)           */
+                               warp marches are 16 * block_rows (0: 64); for the
+                               two-step tile kernel 4 selects 30 x 30 tiles,
+                               other values 30 x 62                               */
 } lbm_desc;
 
 /* Coefficient families of Eq. 1 (Sec. 2.1), source and relaxation rates. */

@@ -16,12 +16,17 @@
 
 namespace lbm {
 
-// Output tile 30 x 62 nodes; the recomputed region (tile plus one-node halo)
-// is then exactly 32 x 64: one warp per region row, every lane busy in step A.
-constexpr int kTX = 30, kTY = 62;
-constexpr int kRX = kTX + 2, kRY = kTY + 2;      // 32 x 64
+// Output tile 30 x TY nodes; the recomputed region (tile plus one-node halo)
+// is then exactly 32 x (TY + 2): one warp per region row, every lane busy in
+// step A. TY = 62 (73.7 KB of shared memory, 3 blocks per SM) or TY = 30
+// (36.9 KB, registers capped so that 4 blocks fit).
+constexpr int kTX = 30;
+constexpr int kRX = kTX + 2;                     // 32
 constexpr int kT2Threads = 256;                  // 32 x 8
-constexpr int kRP = kRX * kRY;                   // shared-memory plane (floats)
+template <int TY> struct Tile2 {
+    static constexpr int kTY = TY, kRY = TY + 2, kRP = kRX * kRY;
+    static constexpr int kMinBlocks = TY > 32 ? 3 : 4;
+};
 
 // Pull the nine populations of node (x, y) from global memory; INTERIOR: the
 // node and its neighbours are inside the domain (no wrap, no wall).
@@ -69,12 +74,46 @@ __device__ __forceinline__ void pull_global(const Params<float> &p, const typena
     }
 }
 
-template <int PREC, int CONV, int DIFF, bool INTERIOR>
+// the coefficients of a Params<float> broadcast to both halves of the packed type
+__device__ __forceinline__ Params<F2> widen(const Params<float> &p)
+{
+    Params<F2> w;
+    w.nx = p.nx; w.ny = p.ny; w.pitch = p.pitch; w.plane = p.plane;
+    w.abb_x = p.abb_x; w.abb_y = p.abb_y;
+    w.s1 = p.s1; w.s2 = p.s2; w.s4 = p.s4; w.s6 = p.s6; w.s7 = p.s7; w.s8 = p.s8;
+    w.h1 = p.h1; w.h2 = p.h2; w.h4 = p.h4; w.h6 = p.h6;
+    w.A3 = p.A3; w.A35 = p.A35; w.A5 = p.A5;
+    w.ux = p.ux; w.uy = p.uy; w.uxx = p.uxx; w.uxy = p.uxy; w.uyy = p.uyy;
+    w.r0 = p.r0; w.r1 = p.r1; w.half_r0 = p.half_r0; w.inv_den = p.inv_den; w.inv_post = p.inv_post;
+    w.has_src = p.has_src;
+    w.Afield = nullptr;
+    return w;
+}
+
+// collide two nodes with one packed instruction stream
+template <int CONV, int DIFF>
+__device__ __forceinline__ void collide_pair(const Params<F2> &pw, float f[2][9], const float A3[2], const float A35[2],
+                                             const float A5[2], float phi[2])
+{
+    F2 g[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = F2(f[0][k], f[1][k]);
+    F2 ph;
+    collide<F2, CONV, DIFF>(pw, g, F2(A3[0], A3[1]), F2(A35[0], A35[1]), F2(A5[0], A5[1]), ph);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { f[0][k] = g[k].v.x; f[1][k] = g[k].v.y; }
+    phi[0] = ph.v.x;
+    phi[1] = ph.v.y;
+}
+
+template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY>
 __device__ __forceinline__ void two_steps(const Params<float> &p, const typename Store<PREC>::T *__restrict__ src,
                                           const float *__restrict__ src_h, typename Store<PREC>::T *__restrict__ dst,
                                           float *__restrict__ dst_h, float *sm, int tx0, int ty0)
 {
     using S = Store<PREC>;
+    constexpr int kTY = Tile2<TY>::kTY, kRY = Tile2<TY>::kRY, kRP = Tile2<TY>::kRP;
+    const Params<F2> pw = widen(p);
     const int lane = threadIdx.x, warp = threadIdx.y;
     const long long P = p.plane;
 
@@ -109,17 +148,19 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
             ys[h] = y;
             pull_global<PREC, CONV, DIFF, INTERIOR>(p, src, src_h, x, y, f[h]);
         }
+        float A3[2] = {p.A3, p.A3}, A35[2] = {p.A35, p.A35}, A5[2] = {p.A5, p.A5}, phi[2];
+        if (p.Afield) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned own = (unsigned)ys[h] * (unsigned)p.pitch + xs[h];
+                A3[h] = __ldg(p.Afield + own);
+                A35[h] = __ldg(p.Afield + P + own);
+                A5[h] = __ldg(p.Afield + 2 * P + own);
+            }
+        }
+        collide_pair<CONV, DIFF>(pw, f, A3, A35, A5, phi);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            float A3 = p.A3, A35 = p.A35, A5 = p.A5;
-            if (p.Afield) {
-                const unsigned own = (unsigned)ys[h] * (unsigned)p.pitch + xs[h];
-                A3 = __ldg(p.Afield + own);
-                A35 = __ldg(p.Afield + P + own);
-                A5 = __ldg(p.Afield + 2 * P + own);
-            }
-            float phi;
-            collide<float, CONV, DIFF>(p, f[h], A3, A35, A5, phi);
             if (INTERIOR || ok[h]) {
                 const int c = (hy0 + h * kWarps) * kRX + lane;
 #pragma unroll
@@ -129,77 +170,95 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
     }
     __syncthreads();
 
-    // ---- step B: output rows r = warp, warp + 8, ...; lanes 0..29 ----------------
+    // ---- step B: output rows in pairs (r, r + 8); lanes 0..29 --------------------
     const int x = tx0 + lane;
     if (lane >= kTX || x >= p.nx) return;
 #pragma unroll 1
-    for (int r = warp; r < kTY; r += kT2Threads / 32) {
-        const int y = ty0 + r;
-        if (!INTERIOR && y >= p.ny) return;
-        const int c = (r + 1) * kRX + lane + 1;
-        float f[9];
+    for (int r0 = warp; r0 < kTY; r0 += 2 * kWarps) {
+        float f[2][9], A3[2], A35[2], A5[2], phi[2];
+        bool ok[2];
+        unsigned own[2];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) f[k] = sm[k * kRP + c - cy(k) * kRX - cx(k)];
-        if (!INTERIOR) {
-            const bool wall = (p.abb_x && (x == 0 || x == p.nx - 1)) || (p.abb_y && (y == 0 || y == p.ny - 1));
-            if (wall) {
+        for (int h = 0; h < 2; ++h) {
+            const int r = r0 + h * kWarps;
+            const int y = ty0 + r;
+            ok[h] = r < kTY && (INTERIOR || y < p.ny);
+            const int rr = ok[h] ? r : r0;                       // a valid row; result unused
+            const int c = (rr + 1) * kRX + lane + 1;
 #pragma unroll
-                for (int k = 1; k < 9; ++k) {
-                    const int xs = x - cx(k), ys = y - cy(k);
-                    const bool ox = p.abb_x && (xs < 0 || xs >= p.nx);
-                    const bool oy = p.abb_y && (ys < 0 || ys >= p.ny);
-                    if (ox || oy) {
-                        const float wx = xs < 0 ? p.phi_wall[0] : p.phi_wall[1];
-                        const float wy = ys < 0 ? p.phi_wall[2] : p.phi_wall[3];
-                        const float phiw = (ox && oy) ? 0.5f * (wx + wy) : (ox ? wx : wy);
-                        f[k] = wall_term<float, CONV, DIFF>(p, k, phiw) - sm[opp(k) * kRP + c];
+            for (int k = 0; k < 9; ++k) f[h][k] = sm[k * kRP + c - cy(k) * kRX - cx(k)];
+            const int yy = ok[h] ? y : ty0 + r0;
+            if (!INTERIOR) {
+                const bool wall = (p.abb_x && (x == 0 || x == p.nx - 1)) || (p.abb_y && (yy == 0 || yy == p.ny - 1));
+                if (wall) {
+#pragma unroll
+                    for (int k = 1; k < 9; ++k) {
+                        const int xs = x - cx(k), ys = yy - cy(k);
+                        const bool ox = p.abb_x && (xs < 0 || xs >= p.nx);
+                        const bool oy = p.abb_y && (ys < 0 || ys >= p.ny);
+                        if (ox || oy) {
+                            const float wx = xs < 0 ? p.phi_wall[0] : p.phi_wall[1];
+                            const float wy = ys < 0 ? p.phi_wall[2] : p.phi_wall[3];
+                            const float phiw = (ox && oy) ? 0.5f * (wx + wy) : (ox ? wx : wy);
+                            f[h][k] = wall_term<float, CONV, DIFF>(p, k, phiw) - sm[opp(k) * kRP + c];
+                        }
                     }
                 }
             }
+            own[h] = (unsigned)yy * (unsigned)p.pitch + x;
+            A3[h] = p.A3; A35[h] = p.A35; A5[h] = p.A5;
+            if (p.Afield) {
+                A3[h] = __ldg(p.Afield + own[h]);
+                A35[h] = __ldg(p.Afield + P + own[h]);
+                A5[h] = __ldg(p.Afield + 2 * P + own[h]);
+            }
         }
-        const unsigned own = (unsigned)y * (unsigned)p.pitch + x;
-        float A3 = p.A3, A35 = p.A35, A5 = p.A5;
-        if (p.Afield) {
-            A3 = __ldg(p.Afield + own);
-            A35 = __ldg(p.Afield + P + own);
-            A5 = __ldg(p.Afield + 2 * P + own);
-        }
-        float phi;
-        collide<float, CONV, DIFF>(p, f, A3, A35, A5, phi);
-        S::store_cell(dst, dst_h, P, own, f, phi);
+        collide_pair<CONV, DIFF>(pw, f, A3, A35, A5, phi);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (ok[h]) S::store_cell(dst, dst_h, P, own[h], f[h], phi[h]);
     }
 }
 
-template <int PREC, int CONV, int DIFF>
-__global__ void __launch_bounds__(kT2Threads, 3)
+template <int PREC, int CONV, int DIFF, int TY>
+__global__ void __launch_bounds__(kT2Threads, Tile2<TY>::kMinBlocks)
 k_step2(const Params<float> p, const typename Store<PREC>::T *__restrict__ src, const float *__restrict__ src_h,
         typename Store<PREC>::T *__restrict__ dst, float *__restrict__ dst_h)
 {
     extern __shared__ float sm[];       // 9 planes of kRY x kRX
+    constexpr int kTY = Tile2<TY>::kTY;
     const int tx0 = blockIdx.x * kTX, ty0 = blockIdx.y * kTY;
     // interior block: the region and every node it pulls from lie inside the
     // domain, so no wrap and no wall can occur
     const bool interior = tx0 >= 2 && tx0 + kTX + 1 <= p.nx - 1 && ty0 >= 2 && ty0 + kTY + 1 <= p.ny - 1;
-    if (interior) two_steps<PREC, CONV, DIFF, true>(p, src, src_h, dst, dst_h, sm, tx0, ty0);
-    else two_steps<PREC, CONV, DIFF, false>(p, src, src_h, dst, dst_h, sm, tx0, ty0);
+    if (interior) two_steps<PREC, CONV, DIFF, true, TY>(p, src, src_h, dst, dst_h, sm, tx0, ty0);
+    else two_steps<PREC, CONV, DIFF, false, TY>(p, src, src_h, dst, dst_h, sm, tx0, ty0);
 }
 
-constexpr size_t kStep2Smem = 9 * kRP * sizeof(float);
-
-template <int PREC, int CONV, int DIFF>
-static cudaError_t step2_t(const lbm_solver *s, int src, cudaStream_t st)
+template <int PREC, int CONV, int DIFF, int TY>
+static cudaError_t step2_ty(const lbm_solver *s, int src, cudaStream_t st)
 {
     using T = typename Store<PREC>::T;
+    constexpr size_t smem = 9 * Tile2<TY>::kRP * sizeof(float);
     // opt in to more than 48 KB of dynamic shared memory (per device, so every call)
-    cudaError_t e = cudaFuncSetAttribute(k_step2<PREC, CONV, DIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kStep2Smem);
+    cudaError_t e = cudaFuncSetAttribute(k_step2<PREC, CONV, DIFF, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     const Params<float> p = make_params<float>(s);
     dim3 block(32, kT2Threads / 32);
-    dim3 grid((s->d.nx + kTX - 1) / kTX, (s->d.ny + kTY - 1) / kTY);
-    k_step2<PREC, CONV, DIFF><<<grid, block, kStep2Smem, st>>>(p, (const T *)s->pop[src], s->phi[src],
-                                                               (T *)s->pop[src ^ 1], s->phi[src ^ 1]);
+    dim3 grid((s->d.nx + kTX - 1) / kTX, (s->d.ny + TY - 1) / TY);
+    k_step2<PREC, CONV, DIFF, TY><<<grid, block, smem, st>>>(p, (const T *)s->pop[src], s->phi[src],
+                                                             (T *)s->pop[src ^ 1], s->phi[src ^ 1]);
     return cudaGetLastError();
+}
+
+// tile height from the descriptor: block_rows 4 selects 30 x 30 tiles, anything
+// else 30 x 62
+template <int PREC, int CONV, int DIFF>
+static cudaError_t step2_t(const lbm_solver *s, int src, cudaStream_t st)
+{
+    if (s->d.block_rows == 4) return step2_ty<PREC, CONV, DIFF, 30>(s, src, st);
+    return step2_ty<PREC, CONV, DIFF, 62>(s, src, st);
 }
 
 template <int PREC>

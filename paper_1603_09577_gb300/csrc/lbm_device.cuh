@@ -19,6 +19,27 @@ __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : (k <= 4 ? (k 
 template <class C>
 __host__ __device__ constexpr C wgt(int k) { return k == 0 ? C(4) / C(9) : (k <= 4 ? C(1) / C(9) : C(1) / C(36)); }
 
+// ---- two nodes per instruction: Blackwell's packed FP32x2 arithmetic ---------
+// F2 carries the same quantity of two lattice nodes; its operators issue one
+// packed add / multiply / fused multiply-add for both (sm_100 and later).
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit F2(float2 a) : v(a) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { a = a + b; return a; }
+__device__ __forceinline__ F2 &operator-=(F2 &a, F2 b) { a = a - b; return a; }
+
+// a * b + c: fused for the packed type, left to contraction for scalars
+template <class C> __device__ __forceinline__ C mad(C a, C b, C c) { return a * b + c; }
+template <> __device__ __forceinline__ F2 mad<F2>(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
 // ---- kernel parameters (passed by value) -----------------------------------
 // Relaxation rates, flux and source coefficients in the compute type C.
 template <class C>
@@ -107,6 +128,7 @@ struct Coef {
     __device__ __forceinline__ Coef(const Params<C> &p, C phi)
     {
         C Cxx, Cxy, Cyy;
+        const C third = C(1.0 / 3.0);
         if (CONV == 0) {
             Bx = p.ux * phi; By = p.uy * phi;
             Bpx = p.ux; Bpy = p.uy;
@@ -115,14 +137,14 @@ struct Coef {
             const C phi2 = phi * phi;
             Bx = C(0.5) * p.ux * phi2; By = C(0.5) * p.uy * phi2;
             Bpx = p.ux * phi; Bpy = p.uy * phi;
-            const C p3 = phi2 * phi * (C(1) / C(3));
+            const C p3 = phi2 * phi * third;
             Cxx = p.uxx * p3; Cxy = p.uxy * p3; Cyy = p.uyy * p3;
         }
         C g;
         if (DIFF == 0) g = phi;
-        else if (DIFF == 1) g = phi + C(0.5) * phi * phi;
-        else g = phi + phi * phi * phi * (C(1) / C(3));
-        const C cg = g * (C(1) / C(3));      // d c_s^2 g with d = 1
+        else if (DIFF == 1) g = mad(C(0.5) * phi, phi, phi);
+        else g = mad(phi * phi * third, phi, phi);
+        const C cg = g * third;              // d c_s^2 g with d = 1
         Cbxx = Cxx + cg; Cbyy = Cyy + cg; Cbxy = Cxy;
     }
 };
@@ -150,17 +172,19 @@ __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35,
     // moments m = M0 f (Eq. 15): rho, e, eps, jx, qx, jy, qy, pxx, pxy
     const C ax = f[1] + f[3], ay = f[2] + f[4];
     const C axis = ax + ay;
-    const C dg = (f[5] + f[7]) + (f[6] + f[8]);
+    const C s57 = f[5] + f[7], s68 = f[6] + f[8];
+    const C dg = s57 + s68;
     const C rho = f[0] + axis + dg;
-    const C e = C(2) * dg - axis - C(4) * f[0];
-    const C eps = C(4) * f[0] - C(2) * axis + dg;
+    const C e = mad(C(2), dg, mad(C(-4), f[0], -axis));
+    const C eps = mad(C(4), f[0], mad(C(-2), axis, dg));
     const C dx1 = f[1] - f[3], dy1 = f[2] - f[4];
-    const C dxd = (f[5] - f[7]) + (f[8] - f[6]);
-    const C dyd = (f[5] - f[7]) + (f[6] - f[8]);
-    const C jx = dx1 + dxd, qx = dxd - C(2) * dx1;
-    const C jy = dy1 + dyd, qy = dyd - C(2) * dy1;
+    const C d57 = f[5] - f[7];
+    const C dxd = d57 + (f[8] - f[6]);
+    const C dyd = d57 + (f[6] - f[8]);
+    const C jx = dx1 + dxd, qx = mad(C(-2), dx1, dxd);
+    const C jy = dy1 + dyd, qy = mad(C(-2), dy1, dyd);
     const C pxx = ax - ay;
-    const C pxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const C pxy = s57 - s68;
 
     // Eq. 35 for R = r0 + r1 phi
     const C phi = (rho + p.half_r0) * p.inv_den;
@@ -169,8 +193,8 @@ __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35,
 
     // equilibrium moments (Eq. 16 with c = 1)
     const C C2 = q.Cbxx + q.Cbyy;
-    const C e_eq = C(3) * C2 - C(4) * phi;
-    const C eps_eq = C(3) * phi - C(3) * C2;
+    const C e_eq = mad(C(3), C2, C(-4) * phi);
+    const C eps_eq = C(3) * (phi - C2);
     const C pxx_eq = q.Cbxx - q.Cbyy;
 
     // relaxation (Eq. 17) plus (I - S/2) M0 R (Eq. 34), M0 R = (R, -2R, R,
@@ -185,41 +209,44 @@ __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35,
     const C dpxx = -p.s7 * (pxx - pxx_eq);
     const C dpxy = -p.s8 * (pxy - q.Cbxy);
     const C d3 = jx - q.Bx, d5 = jy - q.By;
-    C djx = -(A3 * d3 + A35 * d5);
-    C djy = -(A35 * d3 + A5 * d5);
+    C djx = -mad(A3, d3, A35 * d5);
+    C djy = -mad(A35, d3, A5 * d5);
     C drho = C(0);
     if (p.has_src) {
-        const C R = p.r0 + p.r1 * phi;
+        const C R = mad(p.r1, phi, p.r0);
         const C sx = q.Bpx * R, sy = q.Bpy * R;
         drho = R;                                // rho* = phi + R/2 = rho + R for every s0
-        de -= C(2) * p.h1 * R;
-        deps += p.h2 * R;
-        dqx -= p.h4 * sx;
-        dqy -= p.h6 * sy;
-        djx += sx - C(0.5) * (A3 * sx + A35 * sy);
-        djy += sy - C(0.5) * (A35 * sx + A5 * sy);
+        de = mad(C(-2) * p.h1, R, de);
+        deps = mad(p.h2, R, deps);
+        dqx = mad(-p.h4, sx, dqx);
+        dqy = mad(-p.h6, sy, dqy);
+        djx += sx - C(0.5) * mad(A3, sx, A35 * sy);
+        djy += sy - C(0.5) * mad(A35, sx, A5 * sy);
     }
 
     // f* = f + M0^-1 dm, M0^-1 = M0^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-    const C r = drho * (C(1) / C(9));
-    const C ee = de * (C(1) / C(36));
-    const C pp = deps * (C(1) / C(36));
-    const C jxn = djx * (C(1) / C(6)), qxn = dqx * (C(1) / C(12));
-    const C jyn = djy * (C(1) / C(6)), qyn = dqy * (C(1) / C(12));
+    const C r = drho * C(1.0 / 9.0);
+    const C ee = de * C(1.0 / 36.0);
+    const C pp = deps * C(1.0 / 36.0);
+    const C jxn = djx * C(1.0 / 6.0), qxn = dqx * C(1.0 / 12.0);
+    const C jyn = djy * C(1.0 / 6.0), qyn = dqy * C(1.0 / 12.0);
     const C pxxn = dpxx * C(0.25), pxyn = dpxy * C(0.25);
-    f[0] += r - C(4) * ee + C(4) * pp;
-    const C base_a = r - ee - C(2) * pp;
-    const C X1 = jxn - C(2) * qxn, Y1 = jyn - C(2) * qyn;
-    f[1] += base_a + X1 + pxxn;
-    f[3] += base_a - X1 + pxxn;
-    f[2] += base_a + Y1 - pxxn;
-    f[4] += base_a - Y1 - pxxn;
-    const C base_d = r + C(2) * ee + pp;
+    f[0] += mad(C(4), pp - ee, r);
+    const C base_a = mad(C(-2), pp, r - ee);
+    const C X1 = mad(C(-2), qxn, jxn), Y1 = mad(C(-2), qyn, jyn);
+    const C ba_p = base_a + pxxn, ba_m = base_a - pxxn;
+    f[1] += ba_p + X1;
+    f[3] += ba_p - X1;
+    f[2] += ba_m + Y1;
+    f[4] += ba_m - Y1;
+    const C base_d = mad(C(2), ee, r + pp);
     const C X2 = jxn + qxn, Y2 = jyn + qyn;
-    f[5] += base_d + X2 + Y2 + pxyn;
-    f[6] += base_d - X2 + Y2 - pxyn;
-    f[7] += base_d - X2 - Y2 + pxyn;
-    f[8] += base_d + X2 - Y2 - pxyn;
+    const C bd_p = base_d + pxyn, bd_m = base_d - pxyn;
+    const C XpY = X2 + Y2, XmY = X2 - Y2;
+    f[5] += bd_p + XpY;
+    f[6] += bd_m - XmY;
+    f[7] += bd_p - XpY;
+    f[8] += bd_m + XmY;
 }
 
 // Equilibrium populations of Eq. 3 (used only at initialisation).

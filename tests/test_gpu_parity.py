@@ -96,6 +96,20 @@ def test_two_steps_per_pass(case, prec, steps, variant):
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16s"])
+def test_two_step_tile_heights(prec):
+    """The 30 x 30 and 30 x 62 tiles of the shared-memory two-step kernel."""
+    nx, ny = 97, 130
+    phi0 = W.phi0_aniso(nx, seed=13, ny=ny)
+    coef = dict(conv=1, u=(0.05, 0.04), diff=1, K=(0.03, -0.006, 0.02), r1=-0.05)
+    for bc in ((1, 1), (0, 0), (1, 0)):
+        walls = (0.2, 0.3, 0.4, 0.5) if bc != (0, 0) else (0, 0, 0, 0)
+        ref = run_oracle(nx, ny, phi0, 30, bc, walls, **coef)
+        for br in (4, 0):
+            got, _ = run_gpu(prec, nx, ny, phi0, 30, bc, walls, spp=2, variant=0, block_rows=br, **coef)
+            assert rel(got, ref) <= TOL[prec], (bc, br, rel(got, ref))
+
+
 @pytest.mark.parametrize("block_rows", [1, 2, 8])
 def test_column_march_segment_heights(block_rows):
     nx, ny = 100, 75
