@@ -106,7 +106,7 @@ __device__ __forceinline__ void collide_pair(const Params<F2> &pw, float f[2][9]
     phi[1] = ph.v.y;
 }
 
-template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY>
+template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY, bool KF>
 __device__ __forceinline__ void two_steps(const Params<float> &p, const typename Store<PREC>::T *__restrict__ src,
                                           const float *__restrict__ src_h, typename Store<PREC>::T *__restrict__ dst,
                                           float *__restrict__ dst_h, float *sm, int tx0, int ty0)
@@ -149,7 +149,7 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
             pull_global<PREC, CONV, DIFF, INTERIOR>(p, src, src_h, x, y, f[h]);
         }
         float A3[2] = {p.A3, p.A3}, A35[2] = {p.A35, p.A35}, A5[2] = {p.A5, p.A5}, phi[2];
-        if (p.Afield) {
+        if (KF) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const unsigned own = (unsigned)ys[h] * (unsigned)p.pitch + xs[h];
@@ -207,7 +207,7 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
             }
             own[h] = (unsigned)yy * (unsigned)p.pitch + x;
             A3[h] = p.A3; A35[h] = p.A35; A5[h] = p.A5;
-            if (p.Afield) {
+            if (KF) {
                 A3[h] = __ldg(p.Afield + own[h]);
                 A35[h] = __ldg(p.Afield + P + own[h]);
                 A5[h] = __ldg(p.Afield + 2 * P + own[h]);
@@ -220,7 +220,7 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
     }
 }
 
-template <int PREC, int CONV, int DIFF, int TY>
+template <int PREC, int CONV, int DIFF, int TY, bool KF>
 __global__ void __launch_bounds__(kT2Threads, Tile2<TY>::kMinBlocks)
 k_step2(const Params<float> p, const typename Store<PREC>::T *__restrict__ src, const float *__restrict__ src_h,
         typename Store<PREC>::T *__restrict__ dst, float *__restrict__ dst_h)
@@ -231,24 +231,24 @@ k_step2(const Params<float> p, const typename Store<PREC>::T *__restrict__ src, 
     // interior block: the region and every node it pulls from lie inside the
     // domain, so no wrap and no wall can occur
     const bool interior = tx0 >= 2 && tx0 + kTX + 1 <= p.nx - 1 && ty0 >= 2 && ty0 + kTY + 1 <= p.ny - 1;
-    if (interior) two_steps<PREC, CONV, DIFF, true, TY>(p, src, src_h, dst, dst_h, sm, tx0, ty0);
-    else two_steps<PREC, CONV, DIFF, false, TY>(p, src, src_h, dst, dst_h, sm, tx0, ty0);
+    if (interior) two_steps<PREC, CONV, DIFF, true, TY, KF>(p, src, src_h, dst, dst_h, sm, tx0, ty0);
+    else two_steps<PREC, CONV, DIFF, false, TY, KF>(p, src, src_h, dst, dst_h, sm, tx0, ty0);
 }
 
-template <int PREC, int CONV, int DIFF, int TY>
+template <int PREC, int CONV, int DIFF, int TY, bool KF>
 static cudaError_t step2_ty(const lbm_solver *s, int src, cudaStream_t st)
 {
     using T = typename Store<PREC>::T;
     constexpr size_t smem = 9 * Tile2<TY>::kRP * sizeof(float);
     // opt in to more than 48 KB of dynamic shared memory (per device, so every call)
-    cudaError_t e = cudaFuncSetAttribute(k_step2<PREC, CONV, DIFF, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_step2<PREC, CONV, DIFF, TY, KF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const Params<float> p = make_params<float>(s);
     dim3 block(32, kT2Threads / 32);
     dim3 grid((s->d.nx + kTX - 1) / kTX, (s->d.ny + TY - 1) / TY);
-    k_step2<PREC, CONV, DIFF, TY><<<grid, block, smem, st>>>(p, (const T *)s->pop[src], s->phi[src],
-                                                             (T *)s->pop[src ^ 1], s->phi[src ^ 1]);
+    k_step2<PREC, CONV, DIFF, TY, KF><<<grid, block, smem, st>>>(p, (const T *)s->pop[src], s->phi[src],
+                                                                 (T *)s->pop[src ^ 1], s->phi[src ^ 1]);
     return cudaGetLastError();
 }
 
@@ -257,8 +257,14 @@ static cudaError_t step2_ty(const lbm_solver *s, int src, cudaStream_t st)
 template <int PREC, int CONV, int DIFF>
 static cudaError_t step2_t(const lbm_solver *s, int src, cudaStream_t st)
 {
-    if (s->d.block_rows == 4) return step2_ty<PREC, CONV, DIFF, 30>(s, src, st);
-    return step2_ty<PREC, CONV, DIFF, 62>(s, src, st);
+    // per-node tensor field or not: a compile-time choice, so the constant-K
+    // kernel carries no field loads or their registers
+    if (s->d.per_cell_K) {
+        if (s->d.block_rows == 4) return step2_ty<PREC, CONV, DIFF, 30, true>(s, src, st);
+        return step2_ty<PREC, CONV, DIFF, 62, true>(s, src, st);
+    }
+    if (s->d.block_rows == 4) return step2_ty<PREC, CONV, DIFF, 30, false>(s, src, st);
+    return step2_ty<PREC, CONV, DIFF, 62, false>(s, src, st);
 }
 
 template <int PREC>
