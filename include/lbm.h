@@ -120,7 +120,11 @@ int lbm_set_K_field(lbm_handle h, const double *dev_K, void *stream);
 int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream);
 
 /* Advance nsteps time steps (fused pull-stream + collide of Eq. 34 with the
-   boundaries of lbm_desc). Asynchronous; no host synchronisation. */
+   boundaries of lbm_desc). Asynchronous; no host synchronisation. The kernels
+   alternate between the two population buffers; a stream capture of an even
+   number of launches (nsteps even, or with steps_per_pass 2 a multiple of 4)
+   therefore replays consistently. The first call on a device configures kernel
+   attributes: make it before any stream capture. */
 int lbm_step(lbm_handle h, int nsteps, void *stream);
 
 /* phi(t_n) of the current state into dev_out (nx*ny values of `prec`). */
@@ -138,6 +142,11 @@ int lbm_get_phi_host(lbm_handle h, void *host_out, int prec, void *stream);
    [4] sum ref^2, [5] max |phi|, [6] number of non-finite phi, [7] sum phi^2.
    Entries 1-4 are 0 when dev_ref is NULL. GRE (Eq. 39) = out[1] / out[2]. */
 int lbm_reduce(lbm_handle h, const double *dev_ref, double *dev_out, void *stream);
+
+/* Failure detection: counts the nodes whose phi(t_n) is not finite (a blown-up
+   run, a NaN in the input). Synchronises `stream`. Returns LBM_ENONFINITE (and
+   the count in *nonfinite, which may be NULL) if there is any, else LBM_OK. */
+int lbm_check_finite(lbm_handle h, long long *nonfinite, void *stream);
 
 /* Checkpoint / resume: the state is lbm_state_bytes bytes (populations and, for
    LBM_BF16S, the phi plane). dev_dst / dev_src: device buffers of that size. */

@@ -59,6 +59,7 @@ SIGNATURES = {
     "lbm_save": [_VP, _VP, _VP],
     "lbm_load": [_VP, _VP, _VP],
     "lbm_reduce_field_noalloc": [_VP, _VP, ctypes.c_longlong, _VP, _VP],
+    "lbm_check_finite": [_VP, ctypes.POINTER(ctypes.c_longlong), _VP],
     "lbm_adjoint_workspace_size": [_VP, ctypes.POINTER(_SZ)],
     "lbm_adjoint_begin": [_VP, _VP, _SZ, _VP, _I, _VP],
     "lbm_adjoint_step": [_VP, _VP, _VP],

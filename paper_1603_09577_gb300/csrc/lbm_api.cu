@@ -54,6 +54,8 @@ int make_layout(const lbm_desc *d, Layout *L)
     off += up256((size_t)kReduceBlocks * 8 * sizeof(double));
     L->off_flag = off;
     off += 256;
+    L->off_check = off;
+    off += 256;
     L->total = off;
     return LBM_OK;
 }
@@ -185,6 +187,7 @@ int lbm_create(lbm_handle *h, const lbm_desc *desc, void *dev_workspace, size_t 
     s->staging = s->ws + L.off_staging;
     s->partials = (double *)(s->ws + L.off_partials);
     s->flag = (int *)(s->ws + L.off_flag);
+    s->check = (double *)(s->ws + L.off_check);
     *h = s;
     return LBM_OK;
 }
@@ -309,6 +312,22 @@ int lbm_reduce(lbm_handle h, const double *dev_ref, double *dev_out, void *strea
     if (!h->phi_set) return fail(LBM_EINVAL, "lbm_set_phi has not been called");
     if (!dev_out) return fail(LBM_EINVAL, "null output");
     return cuda_check(launch_reduce(h, dev_ref, dev_out, (cudaStream_t)stream), "lbm_reduce");
+}
+
+int lbm_check_finite(lbm_handle h, long long *nonfinite, void *stream)
+{
+    if (int rc = check_ready(h)) return rc;
+    if (!h->phi_set) return fail(LBM_EINVAL, "lbm_set_phi has not been called");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(launch_reduce(h, nullptr, h->check, st), "lbm_check_finite")) return rc;
+    double out[8];
+    if (int rc = cuda_check(cudaMemcpyAsync(out, h->check, sizeof(out), cudaMemcpyDeviceToHost, st), "lbm_check_finite copy"))
+        return rc;
+    if (int rc = cuda_check(cudaStreamSynchronize(st), "lbm_check_finite sync")) return rc;
+    const long long bad = (long long)out[6];
+    if (nonfinite) *nonfinite = bad;
+    if (bad) return fail(LBM_ENONFINITE, std::to_string(bad) + " nodes have a non-finite phi at step " + std::to_string(h->t));
+    return LBM_OK;
 }
 
 int lbm_state_bytes(lbm_handle h, size_t *bytes)

@@ -127,6 +127,11 @@ class Solver:
         v = self.reduce_async(ref).cpu().tolist()
         return dict(zip(REDUCE_KEYS, v))
 
+    def check_finite(self, stream=None) -> None:
+        """Raise LBMError (LBM_ENONFINITE) if any node's phi is not finite."""
+        n = ctypes.c_longlong()
+        C.check(self.lib.lbm_check_finite(self.h, ctypes.byref(n), _stream(stream)))
+
     # -- checkpoints -----------------------------------------------------------
     def state_bytes(self) -> int:
         n = ctypes.c_size_t()

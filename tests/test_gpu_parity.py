@@ -334,3 +334,45 @@ def test_nonfinite_detected():
     phi0[3, 7] = np.nan
     _, s = run_gpu("f32", nx, ny, phi0, 3, conv=0, u=(0.0, 0.0), diff=0, K=(0.01, 0.0, 0.01))
     assert s.reduce()["nonfinite"] > 0
+    with pytest.raises(LBMError) as e:
+        s.check_finite()
+    assert e.value.code == 3
+    _, ok = run_gpu("f32", nx, ny, np.full((ny, nx), 0.5), 3, conv=0, u=(0.0, 0.0), diff=0, K=(0.01, 0.0, 0.01))
+    ok.check_finite()
+
+
+def test_unstable_rates_are_detected():
+    """A run made unstable on purpose (the 128^2 workload's free rates at D0 = 0.0012,
+    |u| = 0.087, the instability the ensemble's rates avoid) is reported as
+    non-finite instead of returning garbage silently."""
+    n = 64
+    phi0 = W.gaussian_hill(n, n, 20, 30, 12.0, 0.8)
+    s = Solver(n, n, prec="f32")
+    s.set_coeffs(conv=0, u=(0.0794, 0.0356), diff=1, K=(0.0012, 0.0, 0.0012), s=W.s9())
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    s.step(3000)
+    with pytest.raises(LBMError) as e:
+        s.check_finite()
+    assert e.value.code == 3
+
+
+@pytest.mark.parametrize("prec,spp", [("f32", 1), ("f32", 2), ("bf16s", 2)])
+def test_step_replays_from_a_cuda_graph(prec, spp):
+    nx, ny = 90, 64
+    phi0 = torch.from_numpy(W.phi0_aniso(nx, seed=14, ny=ny)).cuda()
+    coef = dict(conv=0, u=(0.03, 0.02), diff=2, K=(0.02, 0.008, 0.01), r1=-0.05)
+    s = Solver(nx, ny, prec=prec, bc=("abb", "abb"), steps_per_pass=spp)
+    s.set_coeffs(s=W.s9(), **coef)
+    s.set_phi(phi0)
+    s.step(4)                               # first use on this device, outside capture
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        s.step(20)
+    s.set_phi(phi0)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    replayed = s.phi().cpu()
+    s.set_phi(phi0)
+    s.step(60)
+    assert torch.equal(replayed, s.phi().cpu())
