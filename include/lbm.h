@@ -148,6 +148,15 @@ int lbm_reduce(lbm_handle h, const double *dev_ref, double *dev_out, void *strea
    the count in *nonfinite, which may be NULL) if there is any, else LBM_OK. */
 int lbm_check_finite(lbm_handle h, long long *nonfinite, void *stream);
 
+/* Checked builds (liblbm_checked.so, compiled with LBM_CHECKED): every node
+   coordinate the kernels derive is tested before it indexes memory; one out of
+   range sets a bit (1: x, 2: y, 4: shared-memory region, 8: linear index) of a
+   device word and is replaced by 0. lbm_debug_flags reads the word (cleared by
+   lbm_set_phi), synchronising `stream`; lbm_build_checked returns 1 in a checked
+   build, 0 otherwise. In normal builds the word stays 0. */
+int lbm_debug_flags(lbm_handle h, int *flags, void *stream);
+int lbm_build_checked(void);
+
 /* Checkpoint / resume: the state is lbm_state_bytes bytes (populations and, for
    LBM_BF16S, the phi plane). dev_dst / dev_src: device buffers of that size. */
 int lbm_state_bytes(lbm_handle h, size_t *bytes);
@@ -222,6 +231,8 @@ int lbm_ensemble_capture(lbm_ensemble e, int nsteps, void *stream);
 int lbm_ensemble_replay(lbm_ensemble e, void *stream);
 /* phi(t_n) of every instance into the packed array dev_out. */
 int lbm_ensemble_get_phi(lbm_ensemble e, void *dev_out, int prec, void *stream);
+/* Index-fault word of checked builds (see lbm_debug_flags); synchronises. */
+int lbm_ensemble_debug_flags(lbm_ensemble e, int *flags, void *stream);
 
 /* The reductions of lbm_reduce over a caller-given field, for callers that
    cannot allocate device memory (the paper has no counterpart: this serves

@@ -10,7 +10,8 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblbm.so")
+# LBM_LIBRARY=checked selects the bounds-checked build (see lbm_debug_flags)
+LIB_PATH = os.path.join(HERE, "liblbm_checked.so" if os.environ.get("LBM_LIBRARY") == "checked" else "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EUNSUPPORTED = range(6)
 LBM_F64, LBM_F32, LBM_BF16S = 0, 1, 2
@@ -60,6 +61,8 @@ SIGNATURES = {
     "lbm_load": [_VP, _VP, _VP],
     "lbm_reduce_field_noalloc": [_VP, _VP, ctypes.c_longlong, _VP, _VP],
     "lbm_check_finite": [_VP, ctypes.POINTER(ctypes.c_longlong), _VP],
+    "lbm_debug_flags": [_VP, ctypes.POINTER(_I), _VP],
+    "lbm_build_checked": [],
     "lbm_adjoint_workspace_size": [_VP, ctypes.POINTER(_SZ)],
     "lbm_adjoint_begin": [_VP, _VP, _SZ, _VP, _I, _VP],
     "lbm_adjoint_step": [_VP, _VP, _VP],
@@ -74,6 +77,7 @@ SIGNATURES = {
     "lbm_ensemble_capture": [_VP, _I, _VP],
     "lbm_ensemble_replay": [_VP, _VP],
     "lbm_ensemble_get_phi": [_VP, _VP, _I, _VP],
+    "lbm_ensemble_debug_flags": [_VP, ctypes.POINTER(_I), _VP],
 }
 
 

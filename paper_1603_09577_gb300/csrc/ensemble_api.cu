@@ -15,7 +15,7 @@ namespace {
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct EnsLayout {
-    size_t off_inst = 0, off_tiles = 0, total = 0;
+    size_t off_inst = 0, off_tiles = 0, off_err = 0, total = 0;
     int ntiles = 0;
     std::vector<size_t> off_pop;    // per instance: buffer A offset (B follows)
     std::vector<long long> pitch;
@@ -37,6 +37,8 @@ int ens_layout(int count, const int *nx, const int *ny, EnsLayout *L)
     off += up256(sizeof(EnsInst) * (size_t)count);
     L->off_tiles = off;
     off += up256(sizeof(int4) * (size_t)tiles);
+    L->off_err = off;
+    off += 256;
     L->off_pop.resize(count);
     L->pitch.resize(count);
     for (int i = 0; i < count; ++i) {
@@ -114,6 +116,7 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
         I.s6 = (float)c.s[6]; I.s7 = (float)c.s[7]; I.s8 = (float)c.s[8];
         I.h1 = (float)(1.0 - 0.5 * c.s[1]); I.h2 = (float)(1.0 - 0.5 * c.s[2]);
         I.h4 = (float)(1.0 - 0.5 * c.s[4]); I.h6 = (float)(1.0 - 0.5 * c.s[6]);
+        I.err = (int *)(ws + L.off_err);
     }
     lbm_ensemble_s *e = new (std::nothrow) lbm_ensemble_s();
     if (!e) return fail(LBM_EINVAL, "out of host memory");
@@ -135,8 +138,10 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     e->total_nodes = phi_off;
     e->d_inst = (EnsInst *)(ws + L.off_inst);
     e->d_tiles = (int4 *)(ws + L.off_tiles);
+    e->err = (int *)(ws + L.off_err);
     int rc = cuda_check(cudaMemcpy(e->d_inst, inst.data(), sizeof(EnsInst) * count, cudaMemcpyHostToDevice),
                         "lbm_ensemble_create instance table");
+    if (!rc) rc = cuda_check(cudaMemset(e->err, 0, sizeof(int)), "lbm_ensemble_create error word");
     if (!rc) rc = cuda_check(cudaMemcpy(e->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice),
                              "lbm_ensemble_create tile table");
     int dev = 0, sms = 0;
@@ -233,6 +238,15 @@ int lbm_ensemble_replay(lbm_ensemble e, void *stream)
     if (!e || !e->exec) return fail(LBM_EINVAL, "no captured graph");
     if (e->parity != e->graph_parity) return fail(LBM_EINVAL, "state parity differs from the captured graph's");
     return cuda_check(cudaGraphLaunch(e->exec, (cudaStream_t)stream), "cudaGraphLaunch");
+}
+
+int lbm_ensemble_debug_flags(lbm_ensemble e, int *flags, void *stream)
+{
+    if (!e || !flags) return fail(LBM_EINVAL, "null ensemble or flags pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(cudaMemcpyAsync(flags, e->err, sizeof(int), cudaMemcpyDeviceToHost, st), "lbm_ensemble_debug_flags"))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(st), "lbm_ensemble_debug_flags sync");
 }
 
 int lbm_ensemble_get_phi(lbm_ensemble e, void *dev_out, int prec, void *stream)

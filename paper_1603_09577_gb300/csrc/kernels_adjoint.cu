@@ -113,8 +113,12 @@ k_adjoint_step(const Params<C> p, const C *__restrict__ F, const C *__restrict__
     const bool in = x < p.nx && y < p.ny;
     C dux = C(0), duy = C(0);
     if (in) {
-        const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+        int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+        int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+        LBM_CHK(xm, p.nx, p.err, kErrX);
+        LBM_CHK(xp, p.nx, p.err, kErrX);
+        LBM_CHK(ym, p.ny, p.err, kErrY);
+        LBM_CHK(yp, p.ny, p.err, kErrY);
         const long long r0 = (long long)y * p.pitch, rm = (long long)ym * p.pitch, rp = (long long)yp * p.pitch;
         const long long own = r0 + x, P = p.plane;
         C G[9], L[9];

@@ -21,10 +21,14 @@ k_step(const Params<typename Store<PREC>::C> p, const typename Store<PREC>::T *_
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
 
-    const int xm = x == 0 ? p.nx - 1 : x - 1;
-    const int xp = x == p.nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? p.ny - 1 : y - 1;
-    const int yp = y == p.ny - 1 ? 0 : y + 1;
+    int xm = x == 0 ? p.nx - 1 : x - 1;
+    int xp = x == p.nx - 1 ? 0 : x + 1;
+    int ym = y == 0 ? p.ny - 1 : y - 1;
+    int yp = y == p.ny - 1 ? 0 : y + 1;
+    LBM_CHK(xm, p.nx, p.err, kErrX);
+    LBM_CHK(xp, p.nx, p.err, kErrX);
+    LBM_CHK(ym, p.ny, p.err, kErrY);
+    LBM_CHK(yp, p.ny, p.err, kErrY);
     const long long r0 = (long long)y * p.pitch, rm = (long long)ym * p.pitch, rp = (long long)yp * p.pitch;
     const long long own = r0 + x;
     const long long P = p.plane;

@@ -43,6 +43,12 @@ __device__ __forceinline__ void pull_global(const Params<float> &p, const typena
         ym = y == 0 ? p.ny - 1 : ym;
         yp = y == p.ny - 1 ? 0 : yp;
     }
+    LBM_CHK(x, p.nx, p.err, kErrX);
+    LBM_CHK(y, p.ny, p.err, kErrY);
+    LBM_CHK(xm, p.nx, p.err, kErrX);
+    LBM_CHK(xp, p.nx, p.err, kErrX);
+    LBM_CHK(ym, p.ny, p.err, kErrY);
+    LBM_CHK(yp, p.ny, p.err, kErrY);
     const unsigned pit = (unsigned)p.pitch;
     const unsigned r0 = (unsigned)y * pit, rm = (unsigned)ym * pit, rp = (unsigned)yp * pit;
     f[0] = S::ld(src, r0 + x, src_h, wgt<float>(0));
@@ -184,7 +190,9 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
             const int y = ty0 + r;
             ok[h] = r < kTY && (INTERIOR || y < p.ny);
             const int rr = ok[h] ? r : r0;                       // a valid row; result unused
-            const int c = (rr + 1) * kRX + lane + 1;
+            int c0 = rr * kRX + lane;                             // c - kRX - 1: the region's corner
+            LBM_CHK(c0, kRP - 2 * kRX - 1, p.err, kErrShared);
+            const int c = c0 + kRX + 1;
 #pragma unroll
             for (int k = 0; k < 9; ++k) f[h][k] = sm[k * kRP + c - cy(k) * kRX - cx(k)];
             const int yy = ok[h] ? y : ty0 + r0;
@@ -205,7 +213,10 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
                     }
                 }
             }
-            own[h] = (unsigned)yy * (unsigned)p.pitch + x;
+            int xx = x, yc = yy;
+            LBM_CHK(xx, p.nx, p.err, kErrX);
+            LBM_CHK(yc, p.ny, p.err, kErrY);
+            own[h] = (unsigned)yc * (unsigned)p.pitch + xx;
             A3[h] = p.A3; A35[h] = p.A35; A5[h] = p.A5;
             if (KF) {
                 A3[h] = __ldg(p.Afield + own[h]);

@@ -42,6 +42,12 @@ __device__ __forceinline__ void pull_row(const Params<float> &p, const typename 
         ym = ya == 0 ? p.ny - 1 : ym;
         yp = ya == p.ny - 1 ? 0 : yp;
     }
+    LBM_CHK(xc, p.nx, p.err, kErrX);
+    LBM_CHK(xl, p.nx, p.err, kErrX);
+    LBM_CHK(xr, p.nx, p.err, kErrX);
+    LBM_CHK(ya, p.ny, p.err, kErrY);
+    LBM_CHK(ym, p.ny, p.err, kErrY);
+    LBM_CHK(yp, p.ny, p.err, kErrY);
     const long long r0 = (long long)ya * p.pitch, rm = (long long)ym * p.pitch, rp = (long long)yp * p.pitch;
     // own-column values
     float v[9];
@@ -186,7 +192,10 @@ __device__ __forceinline__ void march(const Params<float> &p, const typename Sto
             f[8] = __shfl_up_sync(kFullM, G[8], 1);
             if (out_lane) {
                 if (!INTERIOR) walls<CONV, DIFF>(p, xo, yb, f, [&](int o) { return P1[o]; });
-                const long long own = (long long)yb * p.pitch + xo;
+                int xs = xo, ys = yb;
+                LBM_CHK(xs, p.nx, p.err, kErrX);
+                LBM_CHK(ys, p.ny, p.err, kErrY);
+                const long long own = (long long)ys * p.pitch + xs;
                 float A3 = p.A3, A35 = p.A35, A5 = p.A5;
                 if (p.Afield) {
                     A3 = __ldg(p.Afield + own);

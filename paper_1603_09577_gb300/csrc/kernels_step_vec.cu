@@ -139,8 +139,13 @@ k_step_v4(const Params<float> p, const typename VecIO<PREC>::T *__restrict__ src
     L.xl = L.x0 == 0 ? p.nx - 1 : L.x0 - 1;
     L.xr = L.x0 + 4 >= p.nx ? 0 : L.x0 + 4;
 
-    const int ym = y == 0 ? p.ny - 1 : y - 1;
-    const int yp = y == p.ny - 1 ? 0 : y + 1;
+    int ym = y == 0 ? p.ny - 1 : y - 1;
+    int yp = y == p.ny - 1 ? 0 : y + 1;
+    LBM_CHK(L.x0, p.nx - 3, p.err, kErrX);
+    LBM_CHK(L.xl, p.nx, p.err, kErrX);
+    LBM_CHK(L.xr, p.nx, p.err, kErrX);
+    LBM_CHK(ym, p.ny, p.err, kErrY);
+    LBM_CHK(yp, p.ny, p.err, kErrY);
     const long long r0 = (long long)y * p.pitch, rm = (long long)ym * p.pitch, rp = (long long)yp * p.pitch;
     const long long P = p.plane;
 

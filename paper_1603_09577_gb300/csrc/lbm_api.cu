@@ -56,6 +56,8 @@ int make_layout(const lbm_desc *d, Layout *L)
     off += 256;
     L->off_check = off;
     off += 256;
+    L->off_err = off;
+    off += 256;
     L->total = off;
     return LBM_OK;
 }
@@ -125,6 +127,7 @@ Params<C> make_params(const lbm_solver *s)
     p.has_src = (c.r0 != 0.0 || c.r1 != 0.0);
     for (int i = 0; i < 4; ++i) p.phi_wall[i] = (C)s->d.phi_wall[i];
     p.Afield = s->d.per_cell_K ? (const C *)s->afield : nullptr;
+    p.err = s->err;
     return p;
 }
 
@@ -188,6 +191,7 @@ int lbm_create(lbm_handle *h, const lbm_desc *desc, void *dev_workspace, size_t 
     s->partials = (double *)(s->ws + L.off_partials);
     s->flag = (int *)(s->ws + L.off_flag);
     s->check = (double *)(s->ws + L.off_check);
+    s->err = (int *)(s->ws + L.off_err);
     *h = s;
     return LBM_OK;
 }
@@ -243,6 +247,7 @@ int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream)
     if (int rc = check_ready(h)) return rc;
     if (!dev_phi) return fail(LBM_EINVAL, "null phi");
     if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "phi must be LBM_F64 or LBM_F32");
+    if (int rc = cuda_check(cudaMemsetAsync(h->err, 0, sizeof(int), (cudaStream_t)stream), "lbm_set_phi")) return rc;
     if (int rc = cuda_check(launch_init(h, dev_phi, prec, (cudaStream_t)stream), "lbm_set_phi")) return rc;
     h->phi_set = 1;
     h->t = 0;
@@ -328,6 +333,25 @@ int lbm_check_finite(lbm_handle h, long long *nonfinite, void *stream)
     if (nonfinite) *nonfinite = bad;
     if (bad) return fail(LBM_ENONFINITE, std::to_string(bad) + " nodes have a non-finite phi at step " + std::to_string(h->t));
     return LBM_OK;
+}
+
+int lbm_debug_flags(lbm_handle h, int *flags, void *stream)
+{
+    if (check_handle(h)) return LBM_EINVAL;
+    if (!flags) return fail(LBM_EINVAL, "null flags pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(cudaMemcpyAsync(flags, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "lbm_debug_flags"))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(st), "lbm_debug_flags sync");
+}
+
+int lbm_build_checked(void)
+{
+#ifdef LBM_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int lbm_state_bytes(lbm_handle h, size_t *bytes)

@@ -56,7 +56,29 @@ struct Params {
     int has_src;
     C phi_wall[4];          // west, east, south, north
     const C *Afield;        // per-cell blocks: 3 planes (A3, A35, A5) or null
+    int *err;               // checked builds: device word that records index faults
 };
+
+// ---- checked builds ------------------------------------------------------------
+// Compiled with -DLBM_CHECKED, every node coordinate a kernel derives is tested
+// against the grid before it is used to index memory; a coordinate out of range
+// sets a bit of a device error word and is replaced by 0, so the access stays in
+// bounds and no lane leaves a warp-wide shuffle. Without the macro the checks
+// compile to nothing.
+#ifdef LBM_CHECKED
+__device__ __forceinline__ int lbm_chk(int v, int n, int *err, int code)
+{
+    if (v < 0 || v >= n) {
+        if (err) atomicOr(err, code);
+        return 0;
+    }
+    return v;
+}
+#define LBM_CHK(v, n, err, code) ((v) = lbm::lbm_chk((v), (n), (err), (code)))
+#else
+#define LBM_CHK(v, n, err, code) ((void)0)
+#endif
+constexpr int kErrX = 1, kErrY = 2, kErrShared = 4, kErrIndex = 8;
 
 // ---- storage traits ---------------------------------------------------------
 // Populations are structure-of-arrays: plane k at base + k * plane, element

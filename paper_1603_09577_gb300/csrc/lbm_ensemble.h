@@ -18,6 +18,7 @@ struct __align__(16) EnsInst {
     float A3, A35, A5;
     float ux, uy, uxx, uxy, uyy;
     float s1, s2, s4, s6, s7, s8, h1, h2, h4, h6;
+    int *err;               // checked builds: shared index-fault word
 };
 
 __device__ __forceinline__ Params<float> ens_params(const EnsInst &I)
@@ -33,6 +34,7 @@ __device__ __forceinline__ Params<float> ens_params(const EnsInst &I)
     p.has_src = 0;
     for (int i = 0; i < 4; ++i) p.phi_wall[i] = 0.f;
     p.Afield = nullptr;
+    p.err = I.err;
     return p;
 }
 
@@ -47,6 +49,7 @@ struct lbm_ensemble_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_steps = 0, graph_parity = 0;
+    int *err = nullptr;             // index-fault word of checked builds
 };
 
 namespace lbm {

@@ -20,7 +20,7 @@ struct Layout {
     long long pitch = 0, plane = 0;
     size_t esize = 0, csize = 0;
     size_t off_pop[2] = {0, 0}, off_phi[2] = {0, 0};
-    size_t off_afield = 0, off_staging = 0, off_partials = 0, off_flag = 0, off_check = 0;
+    size_t off_afield = 0, off_staging = 0, off_partials = 0, off_flag = 0, off_check = 0, off_err = 0;
     size_t pop_bytes = 0, phi_bytes = 0, total = 0;
 };
 
@@ -42,6 +42,7 @@ struct lbm_solver {
     double *partials = nullptr;
     int *flag = nullptr;
     double *check = nullptr;        // 8 doubles: reduction output of lbm_check_finite
+    int *err = nullptr;             // index-fault word of checked builds
     int cur = 0;
     long long t = 0;
     // adjoint (caller-provided second workspace)
