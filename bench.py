@@ -35,7 +35,8 @@ import workloads as W  # noqa: E402
 WORKLOAD = "aniso_dirichlet_4096"
 BYTES_PER_UPDATE = {"f32": 72, "bf16s": 44, "f64": 144}
 KERNEL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
-              for f in ("kernels_step.cu", "kernels_step_vec.cu", "kernels_step2.cu", "lbm_device.cuh")]
+              for f in ("kernels_step.cu", "kernels_step_vec.cu", "kernels_step2.cuh", "kernels_step2_f32.cu",
+                        "kernels_step2_bf16.cu", "lbm_device.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 

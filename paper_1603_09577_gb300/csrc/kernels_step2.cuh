@@ -1,4 +1,4 @@
-// kernels_step2.cu -- two fused stream-collide time steps (Eq. 34) per sweep
+// kernels_step2.cuh -- two fused stream-collide time steps (Eq. 34) per sweep
 // through HBM (temporal blocking), FP32 and BF16-shifted storage.
 //
 // A block owns a 30 x 62 output tile. Step A recomputes the state after the
@@ -12,6 +12,8 @@
 // Blocks whose region lies inside the domain skip all wrap and wall logic.
 // Walls: periodic wrap or anti-bounce-back exactly as in the one-step kernel;
 // halo nodes outside an anti-bounce-back wall do not exist and are skipped.
+#pragma once
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -195,7 +197,9 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
             const int c = c0 + kRX + 1;
 #pragma unroll
             for (int k = 0; k < 9; ++k) f[h][k] = sm[k * kRP + c - cy(k) * kRX - cx(k)];
-            const int yy = ok[h] ? y : ty0 + r0;
+            // an inactive row (beyond the tile or the grid) borrows the tile's first
+            // row, which always exists, so every index below stays in bounds
+            const int yy = ok[h] ? y : ty0;
             if (!INTERIOR) {
                 const bool wall = (p.abb_x && (x == 0 || x == p.nx - 1)) || (p.abb_y && (yy == 0 || yy == p.ny - 1));
                 if (wall) {
@@ -287,27 +291,6 @@ static cudaError_t step2_t(const lbm_solver *s, int src, cudaStream_t st)
     }
     if (s->d.block_rows == 4) return step2_ty<PREC, CONV, DIFF, 30, false>(s, src, st);
     return step2_ty<PREC, CONV, DIFF, 62, false>(s, src, st);
-}
-
-template <int PREC>
-static cudaError_t step2_p(const lbm_solver *s, int src, cudaStream_t st)
-{
-    switch (s->c.conv * 3 + s->c.diff) {
-    case 0: return step2_t<PREC, 0, 0>(s, src, st);
-    case 1: return step2_t<PREC, 0, 1>(s, src, st);
-    case 2: return step2_t<PREC, 0, 2>(s, src, st);
-    case 3: return step2_t<PREC, 1, 0>(s, src, st);
-    case 4: return step2_t<PREC, 1, 1>(s, src, st);
-    case 5: return step2_t<PREC, 1, 2>(s, src, st);
-    }
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_step2(const lbm_solver *s, int src, cudaStream_t st)
-{
-    if (s->d.prec == LBM_F32) return step2_p<LBM_F32>(s, src, st);
-    if (s->d.prec == LBM_BF16S) return step2_p<LBM_BF16S>(s, src, st);
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace lbm
