@@ -221,12 +221,17 @@ int lbm_ensemble_destroy(lbm_ensemble e);
 int lbm_ensemble_info(lbm_ensemble e, long long *nodes, int *tiles, int *grid);
 /* Initial condition of every instance (Eq. 40) from the packed phi array. */
 int lbm_ensemble_set_phi(lbm_ensemble e, const void *dev_phi, int prec, void *stream);
-/* nsteps time steps; mode 0: one persistent launch per step over all tiles;
-   mode 1: one launch per instance per step (same arithmetic, for comparison). */
+/* Persistent launches advance 1 (default) or 2 time steps each; with 2, every
+   launch runs the two-step shared-memory tile routine on 30 x 30 tiles of all
+   instances (two steps per sweep through HBM). Set before capturing a graph. */
+int lbm_ensemble_configure(lbm_ensemble e, int steps_per_pass);
+/* nsteps time steps; mode 0: persistent launches over all tiles (two steps per
+   launch when configured, an odd remainder with one); mode 1: one launch per
+   instance per step (one-step arithmetic, for comparison). */
 int lbm_ensemble_step(lbm_ensemble e, int nsteps, int mode, void *stream);
-/* Capture nsteps (even, >= 2) persistent steps on a non-default stream into a
-   CUDA graph held by the ensemble; lbm_ensemble_replay launches it (advancing
-   the state by nsteps). */
+/* Capture nsteps persistent steps (a positive multiple of 2 * steps per
+   launch) on a non-default stream into a CUDA graph held by the ensemble;
+   lbm_ensemble_replay launches it (advancing the state by nsteps). */
 int lbm_ensemble_capture(lbm_ensemble e, int nsteps, void *stream);
 int lbm_ensemble_replay(lbm_ensemble e, void *stream);
 /* phi(t_n) of every instance into the packed array dev_out. */

@@ -15,8 +15,8 @@ namespace {
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct EnsLayout {
-    size_t off_inst = 0, off_tiles = 0, off_err = 0, total = 0;
-    int ntiles = 0;
+    size_t off_inst = 0, off_tiles = 0, off_tiles2 = 0, off_err = 0, total = 0;
+    int ntiles = 0, ntiles2 = 0;
     std::vector<size_t> off_pop;    // per instance: buffer A offset (B follows)
     std::vector<long long> pitch;
 };
@@ -25,18 +25,22 @@ int ens_layout(int count, const int *nx, const int *ny, EnsLayout *L)
 {
     if (count < 1) return fail(LBM_EINVAL, "ensemble count must be >= 1");
     if (!nx || !ny) return fail(LBM_EINVAL, "null size arrays");
-    long long tiles = 0;
+    long long tiles = 0, tiles2 = 0;
     for (int i = 0; i < count; ++i) {
         if (nx[i] < 2 || ny[i] < 2) return fail(LBM_EINVAL, "instance " + std::to_string(i) + ": nx and ny must be >= 2");
         tiles += (long long)((nx[i] + kEnsTile - 1) / kEnsTile) * ((ny[i] + kEnsRows - 1) / kEnsRows);
+        tiles2 += (long long)((nx[i] + kEns2Tile - 1) / kEns2Tile) * ((ny[i] + kEns2Tile - 1) / kEns2Tile);
     }
     if (tiles > (1LL << 30)) return fail(LBM_EINVAL, "too many tiles");
     L->ntiles = (int)tiles;
+    L->ntiles2 = (int)tiles2;
     size_t off = 0;
     L->off_inst = off;
     off += up256(sizeof(EnsInst) * (size_t)count);
     L->off_tiles = off;
     off += up256(sizeof(int4) * (size_t)tiles);
+    L->off_tiles2 = off;
+    off += up256(sizeof(int4) * (size_t)tiles2);
     L->off_err = off;
     off += 256;
     L->off_pop.resize(count);
@@ -136,11 +140,20 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     }
     e->tile_begin[count] = (int)tiles.size();
     e->total_nodes = phi_off;
+    std::vector<int4> tiles2;
+    tiles2.reserve(L.ntiles2);
+    for (int i = 0; i < count; ++i)
+        for (int ty = 0; ty < ny[i]; ty += kEns2Tile)
+            for (int tx = 0; tx < nx[i]; tx += kEns2Tile) tiles2.push_back(make_int4(i, tx, ty, 0));
+    e->ntiles2 = (int)tiles2.size();
+    e->d_tiles2 = (int4 *)(ws + L.off_tiles2);
     e->d_inst = (EnsInst *)(ws + L.off_inst);
     e->d_tiles = (int4 *)(ws + L.off_tiles);
     e->err = (int *)(ws + L.off_err);
     int rc = cuda_check(cudaMemcpy(e->d_inst, inst.data(), sizeof(EnsInst) * count, cudaMemcpyHostToDevice),
                         "lbm_ensemble_create instance table");
+    if (!rc) rc = cuda_check(cudaMemcpy(e->d_tiles2, tiles2.data(), sizeof(int4) * tiles2.size(), cudaMemcpyHostToDevice),
+                             "lbm_ensemble_create two-step tile table");
     if (!rc) rc = cuda_check(cudaMemset(e->err, 0, sizeof(int)), "lbm_ensemble_create error word");
     if (!rc) rc = cuda_check(cudaMemcpy(e->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice),
                              "lbm_ensemble_create tile table");
@@ -149,12 +162,15 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     const int per_sm = rc ? 0 : ens_occupancy_blocks(e->family);
     if (!rc && per_sm <= 0) rc = fail(LBM_ECUDA, "occupancy query failed");
+    const int per_sm2 = rc ? 0 : ens2_occupancy_blocks(e->family);
+    if (!rc && per_sm2 <= 0) rc = fail(LBM_ECUDA, "occupancy query failed (two-step kernel)");
     if (rc) {
         delete[] e->tile_begin;
         delete e;
         return rc;
     }
     e->grid = sms * per_sm;
+    e->grid2 = sms * per_sm2;
     *out = e;
     return LBM_OK;
 }
@@ -191,7 +207,13 @@ int lbm_ensemble_step(lbm_ensemble e, int nsteps, int mode, void *stream)
     if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
     if (mode != 0 && mode != 1) return fail(LBM_EINVAL, "mode must be 0 (persistent) or 1 (one launch per instance)");
     cudaStream_t st = (cudaStream_t)stream;
-    for (int n = 0; n < nsteps; ++n) {
+    int n = 0;
+    if (mode == 0 && e->spp == 2)
+        for (; n + 2 <= nsteps; n += 2) {
+            if (int rc = cuda_check(ens_launch_step2(e, st), "lbm_ensemble_step (two steps per pass)")) return rc;
+            e->parity ^= 1;
+        }
+    for (; n < nsteps; ++n) {
         if (mode == 0) {
             if (int rc = cuda_check(ens_launch_step(e, 0, e->ntiles, e->grid, st), "lbm_ensemble_step")) return rc;
         } else {
@@ -205,11 +227,21 @@ int lbm_ensemble_step(lbm_ensemble e, int nsteps, int mode, void *stream)
     return LBM_OK;
 }
 
+int lbm_ensemble_configure(lbm_ensemble e, int steps_per_pass)
+{
+    if (!e) return fail(LBM_EINVAL, "null ensemble");
+    if (steps_per_pass != 1 && steps_per_pass != 2) return fail(LBM_EINVAL, "steps_per_pass must be 1 or 2");
+    if (e->exec) return fail(LBM_EINVAL, "configure before capturing a graph");
+    e->spp = steps_per_pass;
+    return LBM_OK;
+}
+
 int lbm_ensemble_capture(lbm_ensemble e, int nsteps, void *stream)
 {
     if (!e) return fail(LBM_EINVAL, "null ensemble");
     if (!stream) return fail(LBM_EINVAL, "capture needs a non-default stream");
-    if (nsteps < 2 || nsteps % 2) return fail(LBM_EINVAL, "captured step count must be even and >= 2");
+    if (nsteps < 2 || nsteps % (2 * e->spp))
+        return fail(LBM_EINVAL, "captured step count must be a positive multiple of 2 * steps per pass");
     cudaStream_t st = (cudaStream_t)stream;
     if (e->exec) { cudaGraphExecDestroy(e->exec); e->exec = nullptr; }
     if (e->graph) { cudaGraphDestroy(e->graph); e->graph = nullptr; }
@@ -217,8 +249,9 @@ int lbm_ensemble_capture(lbm_ensemble e, int nsteps, void *stream)
     if (int rc = cuda_check(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture"))
         return rc;
     int rc = LBM_OK;
-    for (int n = 0; n < nsteps && !rc; ++n) {
-        rc = cuda_check(ens_launch_step(e, 0, e->ntiles, e->grid, st), "captured step");
+    for (int n = 0; n < nsteps && !rc; n += e->spp) {
+        rc = cuda_check(e->spp == 2 ? ens_launch_step2(e, st) : ens_launch_step(e, 0, e->ntiles, e->grid, st),
+                        "captured step");
         e->parity ^= 1;
     }
     cudaGraph_t g = nullptr;

@@ -180,7 +180,9 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
 
     // ---- step B: output rows in pairs (r, r + 8); lanes 0..29 --------------------
     const int x = tx0 + lane;
-    if (lane >= kTX || x >= p.nx) return;
+    // idle lanes skip step B but do not return: a persistent caller reuses the
+    // block for further tiles after a barrier
+    if (lane < kTX && x < p.nx) {
 #pragma unroll 1
     for (int r0 = warp; r0 < kTY; r0 += 2 * kWarps) {
         float f[2][9], A3[2], A35[2], A5[2], phi[2];
@@ -232,6 +234,7 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             if (ok[h]) S::store_cell(dst, dst_h, P, own[h], f[h], phi[h]);
+    }
     }
 }
 

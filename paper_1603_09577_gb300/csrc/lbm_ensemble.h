@@ -42,6 +42,9 @@ __device__ __forceinline__ Params<float> ens_params(const EnsInst &I)
 
 struct lbm_ensemble_s {
     int count = 0, family = 0, ntiles = 0, grid = 0, parity = 0;
+    int spp = 1;                    // time steps per persistent launch (1 or 2)
+    int ntiles2 = 0, grid2 = 0;     // 30 x 30 tiles of the two-step kernel
+    int4 *d_tiles2 = nullptr;
     lbm::EnsInst *d_inst = nullptr;
     int4 *d_tiles = nullptr;
     int *tile_begin = nullptr;      // host: first tile of each instance (count + 1)
@@ -54,6 +57,9 @@ struct lbm_ensemble_s {
 
 namespace lbm {
 cudaError_t ens_launch_step(const lbm_ensemble_s *e, int t_begin, int t_end, int blocks, cudaStream_t st);
+cudaError_t ens_launch_step2(const lbm_ensemble_s *e, cudaStream_t st);
+int ens2_occupancy_blocks(int family);
+constexpr int kEns2Tile = 30;       // two-step tiles: 30 x 30 outputs
 cudaError_t ens_launch_init(const lbm_ensemble_s *e, const void *phi, int in_prec, cudaStream_t st);
 cudaError_t ens_launch_get_phi(const lbm_ensemble_s *e, void *out, int out_prec, cudaStream_t st);
 int ens_occupancy_blocks(int family);
