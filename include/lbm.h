@@ -71,7 +71,9 @@ typedef struct {
                                (LBM_F32 / LBM_BF16S, nx % 4 == 0); 3: with
                                steps_per_pass 2, the register column march (each
                                warp walks a 30-column strip) instead of the
-                               shared-memory tile kernel                          */
+                               shared-memory tile kernel; 4: with steps_per_pass
+                               2 and LBM_F32, the tile kernel with each interior
+                               tile's input staged by a TMA tensor copy           */
     int block_rows;         /* rows of 32-thread warps per thread block: 0 (= 8),
                                1, 2, 4 or 8; for kernel_variant 3 the rows each
                                warp marches are 16 * block_rows (0: 64); for the

@@ -114,70 +114,18 @@ __device__ __forceinline__ void collide_pair(const Params<F2> &pw, float f[2][9]
     phi[1] = ph.v.y;
 }
 
+// Step B of the two-step tile: output rows in pairs from the shared-memory
+// region sm (the state after the first step), stored to global memory.
 template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY, bool KF>
-__device__ __forceinline__ void two_steps(const Params<float> &p, const typename Store<PREC>::T *__restrict__ src,
-                                          const float *__restrict__ src_h, typename Store<PREC>::T *__restrict__ dst,
-                                          float *__restrict__ dst_h, float *sm, int tx0, int ty0)
+__device__ __forceinline__ void step2_B(const Params<float> &p, const Params<F2> &pw,
+                                        typename Store<PREC>::T *__restrict__ dst, float *__restrict__ dst_h,
+                                        const float *sm, int tx0, int ty0)
 {
     using S = Store<PREC>;
-    constexpr int kTY = Tile2<TY>::kTY, kRY = Tile2<TY>::kRY, kRP = Tile2<TY>::kRP;
-    const Params<F2> pw = widen(p);
+    constexpr int kTY = Tile2<TY>::kTY, kRP = Tile2<TY>::kRP;
+    constexpr int kWarps = kT2Threads / 32;
     const int lane = threadIdx.x, warp = threadIdx.y;
     const long long P = p.plane;
-
-    // ---- step A: region rows hy = warp + 8 j; lane = hx. Two rows per pass keep
-    // twice the global loads in flight. -------------------------------------------
-    constexpr int kWarps = kT2Threads / 32;
-    static_assert(kRY % (2 * kWarps) == 0, "region rows must split into row pairs");
-#pragma unroll 1
-    for (int hy0 = warp; hy0 < kRY; hy0 += 2 * kWarps) {
-        float f[2][9];
-        bool ok[2];
-        int xs[2], ys[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int x = tx0 - 1 + lane, y = ty0 - 1 + hy0 + h * kWarps;
-            bool valid = true;
-            if (!INTERIOR) {
-                // a halo node outside the domain wraps (periodic) or does not exist (wall)
-                if (x < 0 || x >= p.nx) {
-                    if (p.abb_x) valid = false;
-                    else x = x < 0 ? x + p.nx : x - p.nx;
-                }
-                if (y < 0 || y >= p.ny) {
-                    if (p.abb_y) valid = false;
-                    else y = y < 0 ? y + p.ny : y - p.ny;
-                }
-                if (x < 0 || x >= p.nx || y < 0 || y >= p.ny) valid = false;
-                if (!valid) { x = 0; y = 0; }          // any in-domain node; result unused
-            }
-            ok[h] = valid;
-            xs[h] = x;
-            ys[h] = y;
-            pull_global<PREC, CONV, DIFF, INTERIOR>(p, src, src_h, x, y, f[h]);
-        }
-        float A3[2] = {p.A3, p.A3}, A35[2] = {p.A35, p.A35}, A5[2] = {p.A5, p.A5}, phi[2];
-        if (KF) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const unsigned own = (unsigned)ys[h] * (unsigned)p.pitch + xs[h];
-                A3[h] = __ldg(p.Afield + own);
-                A35[h] = __ldg(p.Afield + P + own);
-                A5[h] = __ldg(p.Afield + 2 * P + own);
-            }
-        }
-        collide_pair<CONV, DIFF>(pw, f, A3, A35, A5, phi);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (INTERIOR || ok[h]) {
-                const int c = (hy0 + h * kWarps) * kRX + lane;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) sm[k * kRP + c] = f[h][k];
-            }
-        }
-    }
-    __syncthreads();
-
     // ---- step B: output rows in pairs (r, r + 8); lanes 0..29 --------------------
     const int x = tx0 + lane;
     // idle lanes skip step B but do not return: a persistent caller reuses the
@@ -236,6 +184,72 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
             if (ok[h]) S::store_cell(dst, dst_h, P, own[h], f[h], phi[h]);
     }
     }
+}
+
+template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY, bool KF>
+__device__ __forceinline__ void two_steps(const Params<float> &p, const typename Store<PREC>::T *__restrict__ src,
+                                          const float *__restrict__ src_h, typename Store<PREC>::T *__restrict__ dst,
+                                          float *__restrict__ dst_h, float *sm, int tx0, int ty0)
+{
+    using S = Store<PREC>;
+    constexpr int kRY = Tile2<TY>::kRY, kRP = Tile2<TY>::kRP;
+    const Params<F2> pw = widen(p);
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const long long P = p.plane;
+
+    // ---- step A: region rows hy = warp + 8 j; lane = hx. Two rows per pass keep
+    // twice the global loads in flight. -------------------------------------------
+    constexpr int kWarps = kT2Threads / 32;
+    static_assert(kRY % (2 * kWarps) == 0, "region rows must split into row pairs");
+#pragma unroll 1
+    for (int hy0 = warp; hy0 < kRY; hy0 += 2 * kWarps) {
+        float f[2][9];
+        bool ok[2];
+        int xs[2], ys[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int x = tx0 - 1 + lane, y = ty0 - 1 + hy0 + h * kWarps;
+            bool valid = true;
+            if (!INTERIOR) {
+                // a halo node outside the domain wraps (periodic) or does not exist (wall)
+                if (x < 0 || x >= p.nx) {
+                    if (p.abb_x) valid = false;
+                    else x = x < 0 ? x + p.nx : x - p.nx;
+                }
+                if (y < 0 || y >= p.ny) {
+                    if (p.abb_y) valid = false;
+                    else y = y < 0 ? y + p.ny : y - p.ny;
+                }
+                if (x < 0 || x >= p.nx || y < 0 || y >= p.ny) valid = false;
+                if (!valid) { x = 0; y = 0; }          // any in-domain node; result unused
+            }
+            ok[h] = valid;
+            xs[h] = x;
+            ys[h] = y;
+            pull_global<PREC, CONV, DIFF, INTERIOR>(p, src, src_h, x, y, f[h]);
+        }
+        float A3[2] = {p.A3, p.A3}, A35[2] = {p.A35, p.A35}, A5[2] = {p.A5, p.A5}, phi[2];
+        if (KF) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned own = (unsigned)ys[h] * (unsigned)p.pitch + xs[h];
+                A3[h] = __ldg(p.Afield + own);
+                A35[h] = __ldg(p.Afield + P + own);
+                A5[h] = __ldg(p.Afield + 2 * P + own);
+            }
+        }
+        collide_pair<CONV, DIFF>(pw, f, A3, A35, A5, phi);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (INTERIOR || ok[h]) {
+                const int c = (hy0 + h * kWarps) * kRX + lane;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) sm[k * kRP + c] = f[h][k];
+            }
+        }
+    }
+    __syncthreads();
+    step2_B<PREC, CONV, DIFF, INTERIOR, TY, KF>(p, pw, dst, dst_h, sm, tx0, ty0);
 }
 
 template <int PREC, int CONV, int DIFF, int TY, bool KF>

@@ -67,6 +67,7 @@ cudaError_t launch_init(const lbm_solver *s, const void *phi, int in_prec, cudaS
 cudaError_t launch_step(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2m(const lbm_solver *s, int src, cudaStream_t st);
+cudaError_t launch_step2_tma(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step_ptr(const lbm_solver *s, const void *src, void *dst, cudaStream_t st);
 bool step_v4_supported(const lbm_solver *s);
 bool step_v4_preferred(const lbm_solver *s);

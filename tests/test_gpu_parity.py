@@ -78,14 +78,16 @@ def test_parity_families_and_walls(prec, variant, case):
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
-TB = [(c, prec, n, v) for c in CASES for prec in ("f32", "bf16s") for n in (60, 61) for v in (0, 3)]
+TB = [(c, prec, n, v) for c in CASES for prec in ("f32", "bf16s") for n in (60, 61) for v in (0, 3, 4)
+      if not (v == 4 and prec != "f32")]
 
 
 @pytest.mark.parametrize("case,prec,steps,variant", TB,
                          ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}-{p}-{n}-v{v}" for c, p, n, v in TB])
 def test_two_steps_per_pass(case, prec, steps, variant):
     """Temporal blocking (two steps per sweep; an odd count ends with one step):
-    the shared-memory tile kernel (variant 0) and the register column march (3)."""
+    the shared-memory tile kernel (variant 0), the register column march (3) and
+    the tile kernel with TMA-staged input (4)."""
     nx, ny, bc, conv, diff, u, K, r0, r1 = case
     rng = np.random.default_rng(nx * 131 + ny)
     phi0 = W.jacobi_smooth(rng.uniform(0.05, 0.95, (ny, nx)), 2)
@@ -123,16 +125,16 @@ def test_column_march_segment_heights(block_rows):
 
 
 def test_two_steps_per_pass_per_cell_tensor():
-    nx, ny = 70, 45
+    nx, ny = 170, 145
     Kf, phi0, _ = W.adjoint_inputs(nx, seed=8, ny=ny)
     coef = dict(conv=0, u=(0.03, 0.01), diff=0, K=(0.0, 0.0, 0.0))
     ref = run_oracle(nx, ny, phi0, 40, Kfield=Kf, **coef)
-    for v in (0, 3):
+    for v in (0, 3, 4):
         got, _ = run_gpu("f32", nx, ny, phi0, 40, Kfield=Kf, spp=2, variant=v, **coef)
         assert rel(got, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("prec,variant", [("f32", 0), ("bf16s", 0), ("f32", 3), ("bf16s", 3)])
+@pytest.mark.parametrize("prec,variant", [("f32", 0), ("bf16s", 0), ("f32", 3), ("bf16s", 3), ("f32", 4)])
 def test_aniso_dirichlet_two_steps_per_pass(prec, variant):
     """The 4096^2 Dirichlet workload with temporal blocking: all elements after
     12 steps, and all 2000 steps on 512^2."""
