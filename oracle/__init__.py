@@ -53,6 +53,8 @@ class Problem(ctypes.Structure):
         ("r0", ctypes.c_double), ("r1", ctypes.c_double),
         ("src", ctypes.c_int), ("src_par", ctypes.c_double * 8),
         ("collision", ctypes.c_int),
+        ("scheme", ctypes.c_int), ("power", ctypes.c_int),
+        ("src_family", ctypes.c_int), ("b", ctypes.c_double),
     ]
 
 
@@ -74,6 +76,10 @@ def lib():
             L.oracle_phi_from_post.argtypes = [P, dp, ctypes.c_int, dp]
             L.oracle_run.argtypes = [P, dp, ctypes.c_int, dp, dp]
             L.oracle_adjoint.argtypes = [P, dp, dp, ctypes.c_int, dp, dp, dp, dp]
+            L.oracle_init_x.argtypes = [P, dp, dp, dp]
+            L.oracle_step_x.argtypes = [P, dp, dp, dp, dp, dp]
+            L.oracle_run_x.argtypes = [P, dp, ctypes.c_int, dp, dp]
+            L.oracle_collide_cell_x.argtypes = [P, dp, dp, ctypes.c_double, dp, dp]
             _lib = L
     return _lib
 
@@ -109,6 +115,10 @@ class Spec:
     src: int = 0
     src_par: tuple = ()
     collision: int = 0            # 0 moment form, 1 P-form, 2 BGK loop
+    scheme: int = 0               # 0 Scheme B, 1 Scheme A (general path only)
+    power: int = 1                # delta of conv 2 and of the Fisher source
+    src_family: int = 0           # 0 R = r0 + r1 phi, 1 R = b phi (1 - phi^delta)
+    b: float = 0.0
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> Problem:
@@ -132,6 +142,7 @@ class Spec:
         sp = list(self.src_par) + [0.0] * (8 - len(self.src_par))
         p.src_par[:] = sp
         p.collision = self.collision
+        p.scheme, p.power, p.src_family, p.b = self.scheme, self.power, self.src_family, float(self.b)
         return p
 
 
@@ -228,3 +239,63 @@ def adjoint(spec: Spec, phi0, target, nsteps: int):
     if rc:
         raise ValueError(f"oracle_adjoint failed with status {rc}")
     return float(loss[0]), dphi0, dK, du
+
+
+# ---- general path: Scheme A, Fisher source, extrapolation boundary (bc 2) ----
+
+def _null():
+    return ctypes.POINTER(ctypes.c_double)()
+
+
+def collide_cell_x(spec: Spec, f, phi_prev: float = 0.0, K=None):
+    k = _f64(spec.K if K is None else K)
+    fi = _f64(f)
+    out = np.zeros(9)
+    phi = ctypes.c_double()
+    if lib().oracle_collide_cell_x(ctypes.byref(spec.c()), _ptr(k), _ptr(fi), float(phi_prev), _ptr(out),
+                                   ctypes.byref(phi)):
+        raise ValueError("invalid collision request")
+    return out, phi.value
+
+
+def init_x(spec: Spec, phi0):
+    """State (F, Phi) after Eq. 40 and the first collision."""
+    p = spec.c()
+    ph = _f64(phi0)
+    F = np.zeros((9, spec.ny, spec.nx))
+    Phi = np.zeros((spec.ny, spec.nx))
+    if lib().oracle_init_x(ctypes.byref(p), _ptr(ph), _ptr(F), _ptr(Phi)):
+        raise ValueError("oracle_init_x rejected the problem")
+    return F, Phi
+
+
+def step_x(spec: Spec, F, Phi, bvals=None):
+    """One step; bvals: 2 (nx + ny) Dirichlet values (west, east, south, north)."""
+    p = spec.c()
+    Fi, Pi = _f64(F), _f64(Phi)
+    Fo, Po = np.zeros_like(Fi), np.zeros_like(Pi)
+    bv = _f64(bvals) if bvals is not None else None
+    if bv is not None:
+        assert bv.size == 2 * (spec.nx + spec.ny)
+    if lib().oracle_step_x(ctypes.byref(p), _ptr(Fi), _ptr(Pi), _ptr(bv) if bv is not None else _null(),
+                           _ptr(Fo), _ptr(Po)):
+        raise ValueError("oracle_step_x rejected the problem")
+    return Fo, Po
+
+
+def run_x(spec: Spec, phi0, nsteps: int, bvals=None) -> np.ndarray:
+    """phi(t_N) from phi0; bvals: (nsteps, 2 (nx + ny)) Dirichlet records, record
+    n for the step that produces t_{n+1}."""
+    p = spec.c()
+    ph = _f64(phi0)
+    assert ph.shape == (spec.ny, spec.nx)
+    out = np.zeros_like(ph)
+    bv = None
+    if bvals is not None:
+        bv = _f64(bvals)
+        assert bv.shape == (nsteps, 2 * (spec.nx + spec.ny)), bv.shape
+    rc = lib().oracle_run_x(ctypes.byref(p), _ptr(ph), int(nsteps), _ptr(bv) if bv is not None else _null(),
+                            _ptr(out))
+    if rc:
+        raise ValueError(f"oracle_run_x failed with status {rc}")
+    return out

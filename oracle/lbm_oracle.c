@@ -21,6 +21,16 @@
  *   initialisation ............... Eq. 40
  *   walls ........................ anti-bounce-back, half-way wall (Sec. 3.6)
  *   explicit sources ............. Eq. 43 (Sec. 3.1), Eq. 66 (Sec. 3.5)
+ *   power-law flux ............... Eq. 49-50 (conv 2), C from Eq. 7
+ *   Fisher source ................ Eq. 46, R = b phi (1 - phi^delta)
+ *   Scheme A ..................... Remark II: gamma = 0, theta = 1 (Eq. 28), so
+ *                                  Btilde = (I - A/2) B' and the source term of
+ *                                  Eq. 2 is dt R_k + dt^2/2 d_t R_k with the
+ *                                  backward difference of Remark II
+ *   extrapolation boundary ....... non-equilibrium extrapolation (cited in Sec. 3,
+ *                                  Guo, Zheng & Shi 2002): a boundary node takes
+ *                                  feq(phi_b) plus the non-equilibrium part of
+ *                                  its inward neighbour, then collides
  */
 #include "lbm_oracle.h"
 
@@ -82,6 +92,13 @@ int oracle_num_threads(void)
 /* ---- coefficient functions of Eq. 1 ------------------------------------ */
 
 /* B(phi), B'(phi) and C(phi) with C' = B' B'^T (Eq. 7). C is (xx, xy, yy). */
+static double ipow(double v, int n)
+{
+    double r = 1.0;
+    for (int i = 0; i < n; ++i) r *= v;
+    return r;
+}
+
 static void flux(const oracle_problem *p, double phi, double B[2], double Bp[2], double C[3])
 {
     const double ax = p->u[0], ay = p->u[1];
@@ -89,6 +106,16 @@ static void flux(const oracle_problem *p, double phi, double B[2], double Bp[2],
         B[0] = ax * phi;            B[1] = ay * phi;
         Bp[0] = ax;                 Bp[1] = ay;
         C[0] = ax * ax * phi;       C[1] = ax * ay * phi;      C[2] = ay * ay * phi;
+    } else if (p->conv == 2) {
+        /* Eq. 49: B = a phi^(delta+1) / (delta+1); B' = a phi^delta;
+           Eq. 7 / Eq. 50: C = a a^T phi^(2 delta+1) / (2 delta+1) */
+        const int dl = p->power;
+        const double pb = ipow(phi, dl + 1) / (dl + 1);
+        const double pd = ipow(phi, dl);
+        const double pc = ipow(phi, 2 * dl + 1) / (2 * dl + 1);
+        B[0] = ax * pb;             B[1] = ay * pb;
+        Bp[0] = ax * pd;            Bp[1] = ay * pd;
+        C[0] = ax * ax * pc;        C[1] = ax * ay * pc;       C[2] = ay * ay * pc;
     } else {
         B[0] = ax * phi * phi / 2;  B[1] = ay * phi * phi / 2;
         Bp[0] = ax * phi;           Bp[1] = ay * phi;
@@ -443,6 +470,177 @@ int oracle_run(const oracle_problem *p, const double *phi0, int nsteps, double *
     }
     if (!rc && F_out) memcpy(F_out, a, n * sizeof(double));
     free(a); free(b);
+    return rc;
+}
+
+/* ---- general path: Scheme A, Fisher source, extrapolation boundary -------- */
+
+/* Source value R(phi) of the general path. */
+static double source_value(const oracle_problem *p, double phi)
+{
+    if (p->src_family == 1) return p->b * phi * (1.0 - ipow(phi, p->power)); /* Eq. 46 */
+    return p->r0 + p->r1 * phi;
+}
+
+/* Discrete source populations (Eq. 9) with the scheme's Btilde (Eq. 28):
+   Scheme B (gamma = 1) Btilde = B'; Scheme A (gamma = 0) Btilde = (I - A/2) B'. */
+static void source_pop_x(const oracle_problem *p, const double A[4], double phi, double R, double Rk[Q])
+{
+    double B[2], Bp[2], C[3], Bt[2];
+    flux(p, phi, B, Bp, C);
+    if (p->scheme == 1) {
+        Bt[0] = Bp[0] - 0.5 * (A[0] * Bp[0] + A[1] * Bp[1]);
+        Bt[1] = Bp[1] - 0.5 * (A[2] * Bp[0] + A[3] * Bp[1]);
+    } else {
+        Bt[0] = Bp[0];
+        Bt[1] = Bp[1];
+    }
+    for (int k = 0; k < Q; ++k) Rk[k] = WK[k] * (1.0 + (CX[k] * Bt[0] + CY[k] * Bt[1]) / CS2) * R;
+}
+
+int oracle_collide_cell_x(const oracle_problem *p, const double K[3], const double f[9], double phi_prev,
+                          double fout[9], double *phi_out)
+{
+    double S[Q][Q], A[4];
+    if (relax_matrix(p, K, S) || oracle_relax_block(K, A)) return 1;
+    double feq[Q], Rk[Q], phi = 0.0;
+    if (p->scheme == 1) {
+        /* Scheme A: phi = sum_k phi_k (Eq. 10a); Eq. 2 with theta = 1, gamma = 0:
+           phi*_k = phi_k - (M^-1 S M)(phi - phi_eq) + dt R_k(t) + dt^2/2 d_t R_k,
+           d_t R_k = [R_k(t) - R_k(t - dt)] / dt (Remark II). */
+        for (int k = 0; k < Q; ++k) phi += f[k];
+        double Rk0[Q], m[Q], meq[Q], ms[Q], relaxed[Q];
+        oracle_feq(p, phi, feq);
+        source_pop_x(p, A, phi, source_value(p, phi), Rk);
+        source_pop_x(p, A, phi_prev, source_value(p, phi_prev), Rk0);
+        matvec_M0(f, m);
+        matvec_M0(feq, meq);
+        for (int i = 0; i < Q; ++i) {
+            double r = 0.0;
+            for (int j = 0; j < Q; ++j) r += S[i][j] * (m[j] - meq[j]);
+            ms[i] = m[i] - r;
+        }
+        matvec_M0inv(ms, relaxed);
+        for (int k = 0; k < Q; ++k) fout[k] = relaxed[k] + Rk[k] + 0.5 * (Rk[k] - Rk0[k]);
+    } else {
+        /* Scheme B (Eq. 34-35), affine source only */
+        if (p->src_family != 0) return 1;
+        phi = phi_from_pre(p, f, 0.0);
+        oracle_feq(p, phi, feq);
+        source_pop_x(p, A, phi, source_value(p, phi), Rk);
+        collide_moment(S, f, feq, Rk, fout);
+    }
+    if (phi_out) *phi_out = phi;
+    return 0;
+}
+
+static int check_problem_x(const oracle_problem *p)
+{
+    if (p->nx < 1 || p->ny < 1 || p->src != 0 || p->collision != 0) return 1;
+    if (p->scheme != 0 && p->scheme != 1) return 1;
+    if (p->src_family == 1 && p->scheme != 1) return 1;
+    if ((p->conv == 2 || p->src_family == 1) && p->power < 1) return 1;
+    if (p->bc_x < 0 || p->bc_x > 2 || p->bc_y < 0 || p->bc_y > 2) return 1;
+    /* extrapolation needs an inward neighbour inside the domain, and the other
+       axis periodic or extrapolated (no anti-bounce-back link at that node) */
+    if (p->bc_x == 2 && (p->nx < 3 || p->bc_y == 1)) return 1;
+    if (p->bc_y == 2 && (p->ny < 3 || p->bc_x == 1)) return 1;
+    return 0;
+}
+
+/* feq minus the Scheme B shift (Eq. 33): the equilibrium of the stored variable. */
+static void feq_stored(const oracle_problem *p, double phi, double out[Q])
+{
+    oracle_feq(p, phi, out);
+    if (p->scheme == 0) {
+        double Rk[Q], A[4] = {0, 0, 0, 0};
+        source_pop_x(p, A, phi, source_value(p, phi), Rk);
+        for (int k = 0; k < Q; ++k) out[k] -= 0.5 * Rk[k];
+    }
+}
+
+int oracle_init_x(const oracle_problem *p, const double *phi0, double *F, double *Phi)
+{
+    if (check_problem_x(p)) return 1;
+    int bad = 0;
+#pragma omp parallel for reduction(| : bad)
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            double phi = phi0[(size_t)y * p->nx + x];
+            double f[Q], out[Q], K[3];
+            /* Eq. 40 (Scheme A: phi_k = feq; Scheme B: its shifted form, Eq. 33);
+               Scheme A takes d_t R_k = 0 at t = 0 (phi_prev = phi0) */
+            feq_stored(p, phi, f);
+            cell_K(p, x, y, K);
+            bad |= oracle_collide_cell_x(p, K, f, phi, out, NULL);
+            for (int k = 0; k < Q; ++k) F[IDX(p, k, x, y)] = out[k];
+            Phi[(size_t)y * p->nx + x] = phi;
+        }
+    return bad;
+}
+
+/* Dirichlet value of an extrapolated boundary node (corners: west/east first). */
+static double boundary_value(const oracle_problem *p, const double *bv, int x, int y)
+{
+    if (p->bc_x == 2 && x == 0) return bv[y];
+    if (p->bc_x == 2 && x == p->nx - 1) return bv[p->ny + y];
+    if (p->bc_y == 2 && y == 0) return bv[2 * p->ny + x];
+    return bv[2 * p->ny + p->nx + x];
+}
+
+int oracle_step_x(const oracle_problem *p, const double *F_in, const double *Phi_in, const double *bvals,
+                  double *F_out, double *Phi_out)
+{
+    if (check_problem_x(p)) return 1;
+    if ((p->bc_x == 2 || p->bc_y == 2) && !bvals) return 1;
+    int bad = 0;
+#pragma omp parallel for reduction(| : bad)
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            double f[Q], out[Q], K[3], phi;
+            const int ex = p->bc_x == 2 && (x == 0 || x == p->nx - 1);
+            const int ey = p->bc_y == 2 && (y == 0 || y == p->ny - 1);
+            if (ex || ey) {
+                /* non-equilibrium extrapolation: pull the inward neighbour xf,
+                   f(xb) = feq(phi_b) + [f(xf) - feq(phi(xf))] in the stored variable */
+                const int xf = ex ? (x == 0 ? 1 : p->nx - 2) : x;
+                const int yf = ey ? (y == 0 ? 1 : p->ny - 2) : y;
+                double ff[Q], eb[Q], ef[Q], phif = 0.0;
+                for (int k = 0; k < Q; ++k) ff[k] = pull(p, F_in, k, xf, yf);
+                if (p->scheme == 1) {
+                    for (int k = 0; k < Q; ++k) phif += ff[k];
+                } else {
+                    phif = phi_from_pre(p, ff, 0.0);
+                }
+                feq_stored(p, boundary_value(p, bvals, x, y), eb);
+                feq_stored(p, phif, ef);
+                for (int k = 0; k < Q; ++k) f[k] = eb[k] + (ff[k] - ef[k]);
+            } else {
+                for (int k = 0; k < Q; ++k) f[k] = pull(p, F_in, k, x, y);
+            }
+            cell_K(p, x, y, K);
+            const double prev = Phi_in ? Phi_in[(size_t)y * p->nx + x] : 0.0;
+            bad |= oracle_collide_cell_x(p, K, f, prev, out, &phi);
+            for (int k = 0; k < Q; ++k) F_out[IDX(p, k, x, y)] = out[k];
+            Phi_out[(size_t)y * p->nx + x] = phi;
+        }
+    return bad;
+}
+
+int oracle_run_x(const oracle_problem *p, const double *phi0, int nsteps, const double *bvals_all, double *phi_out)
+{
+    const size_t cells = (size_t)p->nx * p->ny, n = (size_t)Q * cells, rec = 2 * ((size_t)p->nx + p->ny);
+    double *a = malloc(n * sizeof(double)), *b = malloc(n * sizeof(double));
+    double *pa = malloc(cells * sizeof(double)), *pb = malloc(cells * sizeof(double));
+    if (!a || !b || !pa || !pb) { free(a); free(b); free(pa); free(pb); return 2; }
+    int rc = oracle_init_x(p, phi0, a, pa);
+    for (int s = 0; s < nsteps && !rc; ++s) {
+        rc = oracle_step_x(p, a, pa, bvals_all ? bvals_all + (size_t)s * rec : NULL, b, pb);
+        double *t = a; a = b; b = t;
+        t = pa; pa = pb; pb = t;
+    }
+    if (!rc) memcpy(phi_out, pa, cells * sizeof(double));
+    free(a); free(b); free(pa); free(pb);
     return rc;
 }
 

@@ -37,6 +37,17 @@ typedef struct {
     int src;                /* explicit source: 0 none, 1 Eq. 43, 2 Eq. 66        */
     double src_par[8];      /* x0, y0, dx, dt, kappa, ux, uy (physical units)     */
     int collision;          /* 0: moment form, 1: P-form, 2: single-rate BGK loop */
+    /* Scheme A, the power-law flux, the Fisher source and the non-equilibrium
+       extrapolation boundary (bc_x / bc_y = 2); used by the *_x functions.    */
+    int scheme;             /* 0: Scheme B (Eq. 33-35); 1: Scheme A (gamma = 0,
+                               Remark II: Btilde = (I - A/2) B', dt R_k by a
+                               backward difference)                               */
+    int power;              /* delta >= 1 of conv 2, B = a phi^(delta+1)/(delta+1),
+                               C = a a phi^(2 delta+1)/(2 delta+1) (Eq. 49-50),
+                               and of the Fisher source                           */
+    int src_family;         /* 0: R = r0 + r1 phi; 1: R = b phi (1 - phi^delta)
+                               (Eq. 46; Scheme A only)                            */
+    double b;               /* Fisher source coefficient                          */
 } oracle_problem;
 
 /* Status: 0 ok, nonzero invalid argument. */
@@ -63,6 +74,24 @@ int oracle_step(const oracle_problem *p, const double *F_in, double *F_out, int 
 int oracle_phi_from_post(const oracle_problem *p, const double *F, int n, double *phi);
 /* Whole run: init from phi0, nsteps steps, phi(t_N) out, optional final state. */
 int oracle_run(const oracle_problem *p, const double *phi0, int nsteps, double *phi_out, double *F_out);
+
+/* General stepping: Scheme A or B, periodic, anti-bounce-back (1) or
+   non-equilibrium extrapolation (2) boundaries, every flux and source family.
+   The state is the post-collision populations F plus the plane Phi = phi(t_n)
+   (Scheme A needs phi(t_n) for the backward difference of R_k).
+   bvals: the Dirichlet values phi_b of the time level being computed, laid
+   out west[ny], east[ny], south[nx], north[nx]; a node on two edges (a corner)
+   takes the west/east value. NULL when no axis uses extrapolation. */
+int oracle_init_x(const oracle_problem *p, const double *phi0, double *F, double *Phi);
+int oracle_step_x(const oracle_problem *p, const double *F_in, const double *Phi_in, const double *bvals,
+                  double *F_out, double *Phi_out);
+/* nsteps steps from phi0; bvals_all: nsteps records of 2 (nx + ny) values
+   (record n for the step that produces t_{n+1}) or NULL. */
+int oracle_run_x(const oracle_problem *p, const double *phi0, int nsteps, const double *bvals_all, double *phi_out);
+/* One collision of one cell for the general path (phi_prev: phi(t_{n-1}) of the
+   cell, used by Scheme A only). */
+int oracle_collide_cell_x(const oracle_problem *p, const double K[3], const double f[9], double phi_prev,
+                          double fout[9], double *phi_out);
 
 /* Discrete adjoint of a run for the linear family (conv 0, diff 0, no source),
    loss = 1/2 sum (phi_N - target)^2. dK: 3 planes (dKxx, dKxy, dKyy) per cell. */

@@ -1,0 +1,205 @@
+"""Pins of the oracle's general path: Scheme A (Remark II, gamma = 0), the
+power-law flux (Eq. 49-50), the Fisher source (Eq. 46) and the
+non-equilibrium extrapolation boundary.
+
+Each part is checked against something other than the code itself: the
+moment conditions of Eq. 9-10 with Btilde of Eq. 28, the exact Adams-Bashforth
+recursion and the closed-form logistic solution that a spatially uniform field
+must follow, the exact linear steady state of the extrapolation boundary, the
+travelling-wave solution of Eq. 47 with second-order convergence, and the
+special cases that reduce to the Scheme B oracle pinned elsewhere.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
+def gre(a, e):
+    """Eq. 39."""
+    return float(np.abs(a - e).sum() / np.abs(e).sum())
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def bf_spec(bf, delta, scheme=1):
+    return O.Spec(nx=bf["nx"], ny=bf["ny"], bc_x=2, bc_y=2, conv=2, u=bf["u"], diff=0,
+                  K=(bf["K"], 0.0, bf["K"]), s=W.s9(), scheme=scheme, power=delta, src_family=1, b=bf["b"])
+
+
+@pytest.mark.parametrize("conv,delta", [(0, 1), (1, 1), (2, 1), (2, 2), (2, 3)])
+def test_scheme_a_source_moments(conv, delta):
+    """With f = feq(phi) the relaxation vanishes and the collision adds
+    3/2 R_k(phi) - 1/2 R_k(phi_prev) (Remark II); its moments must be those
+    Eq. 9-10 fix: sum R_k = R, sum c_k R_k = Btilde R with Btilde = (I - A/2) B'
+    (Eq. 28, gamma = 0), sum c_k c_k R_k = c_s^2 R I."""
+    K = (0.04, 0.012, 0.02)
+    sp = O.Spec(nx=4, ny=4, conv=conv, u=(0.07, -0.04), diff=1, K=K, s=W.s9(), scheme=1, power=delta,
+                src_family=1, b=0.3)
+    A = O.relax_block(K)
+    phi, prev = 0.63, 0.41
+    f = O.feq(sp, phi)
+    out, ph = O.collide_cell_x(sp, f, phi_prev=prev)
+    assert abs(ph - phi) < 1e-15
+    d = out - f
+
+    def Bp(v):
+        if conv == 0:
+            return np.array([0.07, -0.04])
+        return np.array([0.07, -0.04]) * v ** (1 if conv == 1 else delta)
+
+    R = lambda v: 0.3 * v * (1 - v ** delta)
+    Bt = lambda v: (np.eye(2) - 0.5 * A) @ Bp(v)
+    assert abs(d.sum() - (1.5 * R(phi) - 0.5 * R(prev))) < 1e-14
+    first = np.array([(CX * d).sum(), (CY * d).sum()])
+    want = 1.5 * Bt(phi) * R(phi) - 0.5 * Bt(prev) * R(prev)
+    assert np.abs(first - want).max() < 1e-14
+    second = np.array([[(CX * CX * d).sum(), (CX * CY * d).sum()], [(CY * CX * d).sum(), (CY * CY * d).sum()]])
+    assert np.abs(second - (1.5 * R(phi) - 0.5 * R(prev)) / 3.0 * np.eye(2)).max() < 1e-14
+
+
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1), (0, 1)])
+@pytest.mark.parametrize("conv,diff", [(0, 0), (1, 2), (0, 1)])
+def test_scheme_a_without_source_is_scheme_b(bc, conv, diff):
+    """With R = 0 the two schemes are the same scheme (Eq. 33 shifts nothing):
+    Scheme A must reproduce the Scheme B oracle, and the general path's
+    Scheme B must reproduce it bit for bit."""
+    nx, ny = 23, 17
+    rng = np.random.default_rng(7)
+    phi0 = W.jacobi_smooth(rng.uniform(0.1, 0.9, (ny, nx)), 2)
+    common = dict(nx=nx, ny=ny, bc_x=bc[0], bc_y=bc[1], phi_wall=(0.2, 0.6, 0.1, 0.4), conv=conv,
+                  u=(0.06, -0.03), diff=diff, K=(0.03, 0.01, 0.02), s=W.s9())
+    ref = O.run(O.Spec(**common), phi0, 40)
+    a = O.run_x(O.Spec(**common, scheme=1), phi0, 40)
+    b = O.run_x(O.Spec(**common, scheme=0), phi0, 40)
+    assert rel(a, ref) < 1e-13
+    assert np.array_equal(b, ref)
+
+
+def test_power_flux_delta_one_is_burgers_family():
+    """Eq. 49-50 with delta = 1 is the Burgers flux B = a phi^2/2, C = a a phi^3/3."""
+    nx, ny = 20, 14
+    phi0 = W.phi0_aniso(nx, seed=11, ny=ny)
+    common = dict(nx=nx, ny=ny, u=(0.08, 0.05), diff=2, K=(0.02, 0.004, 0.015), s=W.s9(), r1=-0.01)
+    ref = O.run(O.Spec(conv=1, **common), phi0, 30)
+    got = O.run_x(O.Spec(conv=2, power=1, **common), phi0, 30)
+    assert rel(got, ref) < 1e-13
+
+
+@pytest.mark.parametrize("delta", [1, 2])
+def test_uniform_field_follows_adams_bashforth(delta):
+    """A uniform field on a periodic grid has no gradients, so phi follows the
+    zeroth moment of the Scheme A update: phi_{n+1} = phi_n + 3/2 R(phi_n)
+    - 1/2 R(phi_{n-1}) (second-order Adams-Bashforth, with d_t R = 0 at t = 0).
+    It must match that recursion to rounding and converge to the exact solution
+    of the ODE phi' = b phi (1 - phi^delta) at second order in dt."""
+    phi0, b, T = 0.2, 1.0, 2.0
+    exact = (1 + (1 / phi0 ** delta - 1) * math.exp(-delta * b * T)) ** (-1 / delta)
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        n = int(round(T / dt))
+        sp = O.Spec(nx=4, ny=3, conv=2, u=(0.05, 0.03), diff=1, K=(0.02, 0.005, 0.01), s=W.s9(), scheme=1,
+                    power=delta, src_family=1, b=b * dt)
+        phi = O.run_x(sp, np.full((3, 4), phi0), n)
+        assert np.ptp(phi) < 1e-15
+        R = lambda p: b * dt * p * (1 - p ** delta)
+        prev, cur = phi0, phi0
+        for _ in range(n):
+            prev, cur = cur, cur + 1.5 * R(cur) - 0.5 * R(prev)
+        assert abs(phi[0, 0] - cur) < 1e-13
+        errs.append(abs(phi[0, 0] - exact))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.9 < o < 2.1 for o in orders), orders
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_extrapolation_boundary_keeps_linear_field(scheme):
+    """For pure anisotropic diffusion a linear field is an exact steady state of
+    the lattice scheme; with extrapolated Dirichlet data from that field on all
+    four sides the oracle must converge to it exactly, from a perturbed start."""
+    nx, ny = 17, 13
+    xs, ys = np.arange(nx), np.arange(ny)
+    X, Y = np.meshgrid(xs, ys)
+    lin = lambda x, y: 0.3 + 0.02 * x - 0.015 * y
+    bv = np.concatenate([lin(0, ys), lin(nx - 1, ys), lin(xs, 0), lin(xs, ny - 1)])
+    sp = O.Spec(nx=nx, ny=ny, bc_x=2, bc_y=2, conv=0, u=(0.0, 0.0), K=(0.3, 0.1, 0.2), s=W.s9(), scheme=scheme)
+    phi0 = lin(X, Y) + 0.1 * np.sin(X * math.pi / (nx - 1)) * np.sin(Y * math.pi / (ny - 1))
+    n = 4000
+    phi = O.run_x(sp, phi0, n, np.tile(bv, (n, 1)))
+    assert np.abs(phi - lin(X, Y)).max() < 1e-12
+
+
+@pytest.mark.parametrize("scheme,bc", [(1, (2, 2)), (0, (2, 2)), (1, (2, 0)), (0, (0, 2))])
+def test_extrapolated_nodes_hold_dirichlet_values(scheme, bc):
+    """The extrapolation sets a boundary node's populations to feq(phi_b) plus a
+    non-equilibrium part whose zeroth moment vanishes, so phi there is phi_b."""
+    nx, ny = 15, 12
+    rng = np.random.default_rng(3)
+    phi0 = W.jacobi_smooth(rng.uniform(0.2, 0.8, (ny, nx)), 2)
+    sp = O.Spec(nx=nx, ny=ny, bc_x=bc[0], bc_y=bc[1], conv=1, u=(0.05, 0.04), diff=1, K=(0.04, 0.01, 0.03),
+                s=W.s9(), scheme=scheme, r1=-0.02 if scheme == 0 else 0.0,
+                src_family=1 if scheme == 1 else 0, b=0.01, power=1)
+    F, Phi = O.init_x(sp, phi0)
+    bv = rng.uniform(0.3, 0.7, 2 * (nx + ny))
+    F, Phi = O.step_x(sp, F, Phi, bv)
+    if bc[0] == 2:
+        assert np.abs(Phi[:, 0] - bv[:ny]).max() < 1e-14
+        assert np.abs(Phi[:, -1] - bv[ny:2 * ny]).max() < 1e-14
+    if bc[1] == 2:
+        lo = 1 if bc[0] == 2 else 0                       # corners take the x-edge values
+        hi = nx - 1 if bc[0] == 2 else nx
+        assert np.abs(Phi[0, lo:hi] - bv[2 * ny + lo:2 * ny + hi]).max() < 1e-14
+        assert np.abs(Phi[-1, lo:hi] - bv[2 * ny + nx + lo:2 * ny + nx + hi]).max() < 1e-14
+
+
+def test_burgers_fisher_exact_solution_residual():
+    """Eq. 47 solves Eq. 46 only with omega = (a^2 + 2 b kappa (delta+1)^2) /
+    (a (delta+1)); the residual of the printed Eq. 48 omega is O(1e-2)."""
+    a, b, k = 4.0, 1.0, 0.12
+    h = 1e-4
+    pts = [(0.3, 0.1, 0.2), (-0.4, 0.7, 0.6), (1.1, -0.8, 0.9)]
+    for delta in (1, 2):
+        f = lambda x, y, t: W.burgers_fisher_exact(x, y, t, a, b, k, delta)
+        worst = 0.0
+        for x, y, t in pts:
+            p = f(x, y, t)
+            pt = (f(x, y, t + h) - f(x, y, t - h)) / (2 * h)
+            px = (f(x + h, y, t) - f(x - h, y, t)) / (2 * h)
+            lap = (f(x + h, y, t) + f(x - h, y, t) + f(x, y + h, t) + f(x, y - h, t) - 4 * p) / h ** 2
+            res = pt + a * p ** delta * px - k * lap - b * p * (1 - p ** delta)
+            worst = max(worst, abs(res))
+        assert worst < 1e-5, worst
+
+
+def test_burgers_fisher_second_order():
+    """Scheme A with the extrapolation boundary on the travelling wave of
+    Eq. 47 (a = 4, b = 1, kappa = 0.12, delta = 1, [-1, 2]^2): GRE (Eq. 39)
+    at T = 0.25 falls at second order under diffusive refinement (kappa in
+    lattice units fixed, dt ~ dx^2), as the paper reports for this problem."""
+    errs = []
+    for N in (60, 120, 240):
+        bf = W.burgers_fisher(N, 0.25, c=40.0 * N / 60)
+        phi = O.run_x(bf_spec(bf, 1), bf["phi0"], bf["steps"], bf["bvals"])
+        errs.append(gre(phi, bf["exact"]))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 1e-4, errs
+    assert all(1.8 < o < 2.2 for o in orders), (errs, orders)
+
+
+def test_general_path_rejects_invalid_problems():
+    base = dict(nx=8, ny=8, conv=2, u=(0.05, 0.0), K=(0.05, 0.0, 0.05), s=W.s9(), power=1)
+    phi0 = np.full((8, 8), 0.5)
+    with pytest.raises(ValueError):      # the Fisher source needs Scheme A (Eq. 35 is not closed-form)
+        O.init_x(O.Spec(**base, scheme=0, src_family=1, b=0.1), phi0)
+    with pytest.raises(ValueError):      # extrapolation next to an anti-bounce-back axis
+        O.init_x(O.Spec(**base, scheme=1, bc_x=2, bc_y=1), phi0)
+    with pytest.raises(ValueError):      # delta must be >= 1
+        O.init_x(O.Spec(**{**base, "power": 0}, scheme=1), phi0)

@@ -17,6 +17,10 @@ Workloads (sizes, parameters and seeds):
                        u = (0.03, 0), 500 steps, smooth seeded fields (seed 4)
   ensemble_256         256 nonlinear CDE instances, sides log-uniform in [64, 1024],
                        |u| <= 0.1, D(phi) = D0 (1 + phi), D0 in [0.001, 0.05] (seed 5)
+  burgers_fisher_*     2-D Burgers-Fisher equation (Eq. 46-51) on [-1, 2]^2 with the
+                       travelling-wave solution of Eq. 47-48 as initial and Dirichlet
+                       data, a = 4, b = 1, delta = 1, kappa = 0.12 (Pe = La/kappa = 100,
+                       L = 3), Scheme A with the extrapolation boundary
 
 The Burgers workload reads the diffusivity D = 0.005 on the unit square with
 dx = dt = 1/1024, i.e. K = 0.005 * 1024 = 5.12 in lattice units, while the
@@ -157,3 +161,44 @@ def ensemble(count: int = 256, seed: int = 5, side_min: int = 64, side_max: int 
 
 def ensemble_phi0(inst: dict):
     return gaussian_hill(inst["nx"], inst["ny"], inst["xc"], inst["yc"], inst["sigma"], inst["amp"])
+
+
+# ---- Burgers-Fisher travelling wave (Eq. 46-51) ---------------------------------
+
+def burgers_fisher_exact(x, y, t, a=4.0, b=1.0, kappa=0.12, delta=1):
+    """Eq. 47 with A of Eq. 48 and the wave speed omega = (a^2 + 2 b kappa
+    (delta + 1)^2) / (a (delta + 1)). As printed, Eq. 48 has (delta + 1) in place
+    of (delta + 1)^2 in omega; only the squared form makes Eq. 47 an exact
+    solution of Eq. 46 (substitution: the travelling-wave reduction with
+    xi = x + y has diffusivity 2 kappa)."""
+    A = -a * delta / (4.0 * kappa * (delta + 1))
+    w = (a * a + 2.0 * b * kappa * (delta + 1) ** 2) / (a * (delta + 1))
+    return (0.5 + 0.5 * np.tanh(A * (x + y - w * t))) ** (1.0 / delta)
+
+
+def burgers_fisher(N: int, T: float, c: float = 40.0, a: float = 4.0, b: float = 1.0, kappa: float = 0.12,
+                   delta: int = 1, x0: float = -1.0, L: float = 3.0) -> dict:
+    """The Burgers-Fisher problem on [x0, x0 + L]^2 with N intervals per side
+    (N + 1 nodes), lattice speed c = dx/dt, run to time T.
+
+    Lattice units (dx = dt = 1 on the lattice): the flux direction becomes
+    a dt / dx, the source rate b dt and the diffusivity kappa dt / dx^2 (reading
+    of the paper, which leaves dt unstated). Returns the lattice parameters, the
+    initial field, the Dirichlet records of every step (west, east, south,
+    north; record n holds t_{n+1}) and the exact field at the final time."""
+    dx = L / N
+    dt = dx / c
+    steps = int(round(T / dt))
+    xs = x0 + dx * np.arange(N + 1)
+    X, Y = np.meshgrid(xs, xs)               # (ny, nx): row y, column x
+    ex = lambda xx, yy, t: burgers_fisher_exact(xx, yy, t, a, b, kappa, delta)
+    n = N + 1
+    bv = np.empty((steps, 4 * n))
+    for s in range(steps):
+        t = (s + 1) * dt
+        bv[s, 0:n] = ex(xs[0], xs, t)              # west: x = x0, all y
+        bv[s, n:2 * n] = ex(xs[-1], xs, t)         # east
+        bv[s, 2 * n:3 * n] = ex(xs, xs[0], t)      # south: y = x0, all x
+        bv[s, 3 * n:4 * n] = ex(xs, xs[-1], t)     # north
+    return dict(nx=n, ny=n, dx=dx, dt=dt, steps=steps, u=(a * dt / dx, 0.0), K=kappa * dt / dx ** 2,
+                b=b * dt, power=delta, phi0=ex(X, Y, 0.0), bvals=bv, exact=ex(X, Y, steps * dt))
