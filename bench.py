@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ens-count", type=int, default=256, help="instances of the ensemble workload")
     ap.add_argument("--ens-spp", type=int, default=2, help="time steps per persistent ensemble launch (1 or 2)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "ensemble_256", "adjoint_512"],
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "ensemble_256", "adjoint_512", "burgers_fisher_4096"],
                     help="the default is the headline workload; the others print their own line")
     return ap.parse_args()
 
@@ -347,6 +348,110 @@ def run_adjoint(args):
     print(json.dumps(res), flush=True)
 
 
+def run_burgers_fisher(args):
+    """Scheme A with the extrapolation boundary on the Burgers-Fisher travelling
+    wave (Eq. 46-51: a = 4, b = 1, kappa = 0.12, delta = 1, [-1, 2]^2, c = 40)
+    at 4096^2 nodes, 2000 steps per job: set_phi, the steps with per-step
+    Dirichlet records, and the error reduction against Eq. 47."""
+    import torch
+
+    from paper_1603_09577_gb300 import Solver
+    prec = args.prec if args.prec in ("f32", "f64") else "f32"
+    n = 4096
+    lbm_steps = args.lbm_steps or 2000
+    bf = W.burgers_fisher(n - 1, 0.0)
+    T = lbm_steps * bf["dt"]
+    bf = W.burgers_fisher(n - 1, T)
+    assert bf["steps"] == lbm_steps
+    tdt = torch.float64 if prec == "f64" else torch.float32
+    phi0 = torch.from_numpy(bf["phi0"]).to(tdt).cuda()
+    exact = torch.from_numpy(bf["exact"]).cuda()
+    bv = torch.from_numpy(bf["bvals"]).cuda()
+    s = Solver(n, n, prec=prec, bc=("nee", "nee"), scheme="A")
+    s.set_coeffs(conv=2, power=1, u=bf["u"], diff=0, K=(bf["K"], 0.0, bf["K"]), s=W.s9(), src_family=1, b=bf["b"])
+    red = torch.zeros(8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def job():
+        s.set_phi(phi0)
+        s.set_dirichlet(bv)
+        s.step(lbm_steps)
+        s.reduce_async(exact, out=red)
+
+    for _ in range(args.warmup):
+        job()
+    torch.cuda.synchronize()
+    clk = clocks_sampler()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in ev:
+        s.set_phi(phi0)
+        s.set_dirichlet(bv)
+        a.record(stream)
+        s.step(lbm_steps)
+        b.record(stream)
+        s.reduce_async(exact, out=red)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clocks_summary(clk)
+    ms = t0.elapsed_time(t1) / args.steps
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev) / lbm_steps
+    cells = n * n
+    value = cells * lbm_steps / (ms / 1e3) / 1e6
+    g = red.cpu().tolist()
+    # end to end with host buffers
+    host_in = torch.from_numpy(bf["phi0"]).to(tdt).pin_memory()
+    host_out = torch.empty((n, n), dtype=tdt).pin_memory()
+    s.set_phi_host(host_in)
+    s.set_dirichlet(bv)
+    s.step(lbm_steps)
+    s.phi_host(host_out)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_phi_host(host_in)
+        s.set_dirichlet(bv)
+        s.step(lbm_steps)
+        s.phi_host(host_out)
+    e2e_ms = 1e3 * (time.perf_counter() - w0) / args.steps
+    esz = 8 if prec == "f64" else 4
+    bpu = 9 * 2 * esz + 2 * esz          # populations read + written, phi(t_n) plane read + written
+    peak, src = measured_peak()
+    achieved = bpu * cells / (launch_ms / 1e3) / 1e9
+    out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": prec, "data": "synthetic",
+           "config": {"workload": f"burgers_fisher_4096: Scheme A, B = a phi^2/2 (a = 4 along x), R = b phi (1 - phi), "
+                                  f"kappa = 0.12, [-1,2]^2 at 4096x4096 (c = 40), extrapolated Dirichlet walls from "
+                                  f"Eq. 47, {lbm_steps} steps per job",
+                      "nx": n, "ny": n, "lattice": {"u": bf["u"], "K": bf["K"], "b": bf["b"]},
+                      "l2": "inputs larger than L2 (two population buffers of 604 MB each, FP32)"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "kernel": "k_step_g (general one-step kernel, Scheme A)",
+                        "algorithmic_bytes_per_update": bpu, "avg_launch_ms": launch_ms,
+                        "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src},
+           "e2e": {"value": cells * lbm_steps / (e2e_ms / 1e3) / 1e6, "unit": "MLUPS",
+                   "h2d_bytes_per_step": int(host_in.numel() * esz), "d2h_bytes_per_step": int(host_out.numel() * esz)},
+           "gre_vs_eq47": g[1] / g[2],
+           "gpu_launches": args.steps * (1 + lbm_steps + 2)}
+    if clocks is not None:
+        out["clocks"] = clocks
+    if not args.no_cpu_baseline:
+        import oracle as O
+        sp = O.Spec(nx=n, ny=n, bc_x=2, bc_y=2, conv=2, u=bf["u"], diff=0, K=(bf["K"], 0.0, bf["K"]), s=W.s9(),
+                    scheme=1, power=1, src_family=1, b=bf["b"])
+        F, P = O.init_x(sp, bf["phi0"])
+        k = 8
+        w0 = time.perf_counter()
+        for j in range(k):
+            F, P = O.step_x(sp, F, P, bf["bvals"][j])
+        dt = time.perf_counter() - w0
+        out["cpu_baseline"] = {"value": cells * k / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(),
+                               "kind": "oracle", "sample": f"the same 4096x4096 problem, {k} time steps ({dt:.1f} s), FP64"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -355,6 +460,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "adjoint_512":
         return run_adjoint(args)
+    if args.workload == "burgers_fisher_4096":
+        return run_burgers_fisher(args)
     import torch
     import torch.distributed as dist
 

@@ -6,9 +6,10 @@
  * The equation solved is Eq. 1,
  *     d_t phi + div B(phi) = div[K . (div D(phi))] + R,
  * with D(phi) = g(phi) I and the closed coefficient families of lbm_coeffs.
- * Every time step is one fused pull-stream / collide sweep (Eq. 34, Scheme B)
- * on the D2Q9 lattice (Eq. 5), in lattice units c = dx/dt = 1, c_s^2 = 1/3,
- * d = 1.
+ * Every time step is one fused pull-stream / collide sweep on the D2Q9
+ * lattice (Eq. 5), in lattice units c = dx/dt = 1, c_s^2 = 1/3, d = 1: Scheme B
+ * (Eq. 34, the default) or Scheme A (Remark II: gamma = 0, theta = 1,
+ * Btilde = (I - A/2) B', the time derivative of R_k by a backward difference).
  *
  * Conventions for every entry point:
  *  - Return value: LBM_OK (0) or an error code; lbm_last_error() gives a
@@ -22,7 +23,8 @@
  *  - Fields: phi arrays are row-major (ny rows of nx), element (x, y) at
  *    y * nx + x, no padding. Precision tags: LBM_F64 = double, LBM_F32 = float.
  *  - State: after lbm_set_phi and after every lbm_step the stored state is the
- *    post-collision shifted population fbar*(x, t_n) (Eq. 33-34).
+ *    post-collision shifted population fbar*(x, t_n) (Eq. 33-34); with Scheme A
+ *    the post-collision phi*_k(x, t_n) of Eq. 2 plus the plane phi(x, t_n).
  */
 #ifndef LBM_H
 #define LBM_H
@@ -54,6 +56,18 @@ extern "C" {
 #define LBM_ABB 1           /* anti-bounce-back Dirichlet wall half-way between
                                the boundary node and its missing neighbour
                                (Sec. 3.6)                                        */
+#define LBM_NEE 2           /* non-equilibrium extrapolation (cited in Sec. 3 as
+                               the default boundary): the first and last node
+                               rows of the axis are Dirichlet nodes; each takes
+                               feq(phi_b) plus the non-equilibrium part of its
+                               inward neighbour (stored variable), then collides.
+                               phi_b per step from lbm_set_dirichlet. The other
+                               axis must be LBM_PERIODIC or LBM_NEE; the axis
+                               needs >= 3 nodes                                  */
+
+/* time-stepping scheme (lbm_desc.scheme) */
+#define LBM_SCHEME_B 0      /* gamma = 1 (Eq. 31-35), affine sources             */
+#define LBM_SCHEME_A 1      /* gamma = 0 (Remark II), any source family          */
 
 typedef struct lbm_solver *lbm_handle;
 
@@ -61,7 +75,7 @@ typedef struct lbm_solver *lbm_handle;
 typedef struct {
     int nx, ny;             /* nodes per axis, each >= 2                          */
     int prec;               /* LBM_F64, LBM_F32 or LBM_BF16S                      */
-    int bc_x, bc_y;         /* LBM_PERIODIC or LBM_ABB on the x and y walls       */
+    int bc_x, bc_y;         /* LBM_PERIODIC, LBM_ABB or LBM_NEE per axis          */
     double phi_wall[4];     /* Dirichlet values: west, east, south, north         */
     int steps_per_pass;     /* 1, or 2: two time steps per sweep through memory
                                (F32 and BF16S with periodic or ABB walls)         */
@@ -79,13 +93,20 @@ typedef struct {
                                warp marches are 16 * block_rows (0: 64); for the
                                two-step tile kernel 4 selects 30 x 30 tiles,
                                other values 30 x 62                               */
+    int scheme;             /* LBM_SCHEME_B (0) or LBM_SCHEME_A. Scheme A, LBM_NEE
+                               and the flux family conv 2 run the general
+                               one-node-per-thread kernel: LBM_F64 or LBM_F32,
+                               steps_per_pass 1, kernel_variant 0 or 1            */
 } lbm_desc;
 
 /* Coefficient families of Eq. 1 (Sec. 2.1), source and relaxation rates. */
 typedef struct {
     int conv;               /* 0: B = u phi, C = u u^T phi;
-                               1: B = a phi^2/2, C = a a^T phi^3/3 (Eq. 7)        */
-    double u[2];            /* u (conv 0) or a (conv 1)                          */
+                               1: B = a phi^2/2, C = a a^T phi^3/3 (Eq. 7);
+                               2: B = a phi^(delta+1)/(delta+1),
+                                  C = a a^T phi^(2 delta+1)/(2 delta+1)
+                                  (Eq. 49-50), delta = power                      */
+    double u[2];            /* u (conv 0) or a (conv 1, 2)                       */
     int diff;               /* D = g(phi) I, g = 0: phi, 1: phi + phi^2/2,
                                2: phi + phi^3/3                                   */
     double K[3];            /* constant tensor (Kxx, Kxy, Kyy), symmetric positive
@@ -94,8 +115,13 @@ typedef struct {
                                A = (K / (d c_s^2) + I/2)^-1                       */
     double s[9];            /* s0..s8 of Eq. 17; entries 3 and 5 are ignored
                                (they come from K); all others in (0, 2)           */
-    double r0, r1;          /* source R = r0 + r1 phi; phi from Eq. 35 in closed
-                               form phi = (sum fbar + r0/2) / (1 - r1/2)          */
+    double r0, r1;          /* source R = r0 + r1 phi (src_family 0); Scheme B
+                               takes phi from Eq. 35 in closed form
+                               phi = (sum fbar + r0/2) / (1 - r1/2)               */
+    int src_family;         /* 0: R = r0 + r1 phi; 1: R = b phi (1 - phi^delta)
+                               (Eq. 46, Scheme A only; r0 = r1 = 0)               */
+    int power;              /* delta in 1..16 for conv 2 and src_family 1        */
+    double b;               /* Fisher source coefficient (src_family 1)          */
 } lbm_coeffs;
 
 /* Bytes of device workspace lbm_create needs for this description. */
@@ -117,8 +143,9 @@ int lbm_set_coeffs(lbm_handle h, const lbm_coeffs *c);
 int lbm_set_K_field(lbm_handle h, const double *dev_K, void *stream);
 
 /* Initial condition phi(x, 0) (Eq. 40): fbar = feq(phi0) - R_k/2 (Eq. 33), then
-   one collision, so that the stored state is fbar*(x, t_0). dev_phi: nx*ny
-   values of precision `prec` (LBM_F64 or LBM_F32). */
+   one collision, so that the stored state is fbar*(x, t_0); Scheme A: phi_k =
+   feq(phi0), then one collision with d_t R_k = 0. dev_phi: nx*ny values of
+   precision `prec` (LBM_F64 or LBM_F32). */
 int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream);
 
 /* Advance nsteps time steps (fused pull-stream + collide of Eq. 34 with the
@@ -128,6 +155,16 @@ int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream);
    therefore replays consistently. The first call on a device configures kernel
    attributes: make it before any stream capture. */
 int lbm_step(lbm_handle h, int nsteps, void *stream);
+
+/* Dirichlet data of the LBM_NEE axes. dev_values: device array of nrec >= 1
+   records, each 2 (nx + ny) doubles laid out west[ny], east[ny], south[nx],
+   north[nx] (a corner node takes its west/east value); the caller owns it and
+   keeps it alive while steps run. Record j is used by the step that produces
+   time level t0 + j + 1, t0 being the step count (since lbm_set_phi) at this
+   call; after the last record the last one is reused (nrec = 1: constant
+   values). lbm_set_phi itself takes the boundary values from phi0. A stream
+   capture of lbm_step records the record pointers of the captured steps. */
+int lbm_set_dirichlet(lbm_handle h, const double *dev_values, int nrec);
 
 /* phi(t_n) of the current state into dev_out (nx*ny values of `prec`). */
 int lbm_get_phi(lbm_handle h, void *dev_out, int prec, void *stream);

@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(HERE, "liblbm_checked.so" if os.environ.get("LBM_LIBRARY
 
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EUNSUPPORTED = range(6)
 LBM_F64, LBM_F32, LBM_BF16S = 0, 1, 2
-LBM_PERIODIC, LBM_ABB = 0, 1
+LBM_PERIODIC, LBM_ABB, LBM_NEE = 0, 1, 2
+LBM_SCHEME_B, LBM_SCHEME_A = 0, 1
 PREC = {"f64": LBM_F64, "f32": LBM_F32, "bf16s": LBM_BF16S}
 
 
@@ -30,13 +31,14 @@ class Desc(ctypes.Structure):
                 ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
                 ("phi_wall", ctypes.c_double * 4), ("steps_per_pass", ctypes.c_int),
                 ("per_cell_K", ctypes.c_int), ("kernel_variant", ctypes.c_int),
-                ("block_rows", ctypes.c_int)]
+                ("block_rows", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 class Coeffs(ctypes.Structure):
     _fields_ = [("conv", ctypes.c_int), ("u", ctypes.c_double * 2), ("diff", ctypes.c_int),
                 ("K", ctypes.c_double * 3), ("s", ctypes.c_double * 9),
-                ("r0", ctypes.c_double), ("r1", ctypes.c_double)]
+                ("r0", ctypes.c_double), ("r1", ctypes.c_double),
+                ("src_family", ctypes.c_int), ("power", ctypes.c_int), ("b", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -53,6 +55,7 @@ SIGNATURES = {
     "lbm_set_phi": [_VP, _VP, _I, _VP],
     "lbm_set_phi_host": [_VP, _VP, _I, _VP],
     "lbm_step": [_VP, _I, _VP],
+    "lbm_set_dirichlet": [_VP, _VP, _I],
     "lbm_get_phi": [_VP, _VP, _I, _VP],
     "lbm_get_phi_host": [_VP, _VP, _I, _VP],
     "lbm_reduce": [_VP, _VP, _VP, _VP],

@@ -83,6 +83,7 @@ __device__ __forceinline__ double node_phi(const Params<typename Store<PREC>::C>
 {
     using S = Store<PREC>;
     using C = typename S::C;
+    if (!S::kPhiPlane && p.scheme_a) return (double)((const C *)phiplane)[own];   // Scheme A keeps phi(t_n)
     C sum = S::ld(f, own, phiplane, wgt<C>(0));
 #pragma unroll
     for (int k = 1; k < 9; ++k) sum += S::ld(f + k * p.plane, own, phiplane, wgt<C>(k));

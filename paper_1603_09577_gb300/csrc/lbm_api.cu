@@ -38,7 +38,10 @@ int make_layout(const lbm_desc *d, Layout *L)
     L->esize = d->prec == LBM_F64 ? 8 : (d->prec == LBM_F32 ? 4 : 2);
     L->csize = d->prec == LBM_F64 ? 8 : 4;
     L->pop_bytes = up256(9 * (size_t)L->plane * L->esize);
-    L->phi_bytes = d->prec == LBM_BF16S ? up256((size_t)L->plane * 4) : 0;
+    // BF16S: the float shift plane; Scheme A: the plane phi(t_n) in the compute type
+    L->phi_bytes = d->prec == LBM_BF16S          ? up256((size_t)L->plane * 4)
+                   : d->scheme == LBM_SCHEME_A ? up256((size_t)L->plane * L->csize)
+                                               : 0;
     size_t off = 0;
     for (int b = 0; b < 2; ++b) {
         L->off_pop[b] = off;
@@ -68,8 +71,16 @@ static int check_desc(const lbm_desc *d)
     if (d->nx < 2 || d->ny < 2) return fail(LBM_EINVAL, "nx and ny must be >= 2");
     if ((long long)d->nx * d->ny > (1LL << 31)) return fail(LBM_EINVAL, "grid larger than 2^31 nodes");
     if (d->prec != LBM_F64 && d->prec != LBM_F32 && d->prec != LBM_BF16S) return fail(LBM_EINVAL, "unknown precision");
-    if ((d->bc_x != LBM_PERIODIC && d->bc_x != LBM_ABB) || (d->bc_y != LBM_PERIODIC && d->bc_y != LBM_ABB))
+    if (d->bc_x < LBM_PERIODIC || d->bc_x > LBM_NEE || d->bc_y < LBM_PERIODIC || d->bc_y > LBM_NEE)
         return fail(LBM_EINVAL, "unknown boundary kind");
+    if (d->scheme != LBM_SCHEME_B && d->scheme != LBM_SCHEME_A) return fail(LBM_EINVAL, "unknown scheme");
+    if ((d->bc_x == LBM_NEE && (d->nx < 3 || d->bc_y == LBM_ABB)) || (d->bc_y == LBM_NEE && (d->ny < 3 || d->bc_x == LBM_ABB)))
+        return fail(LBM_EINVAL, "extrapolation needs >= 3 nodes on its axis and a periodic or extrapolated other axis");
+    if (d->scheme == LBM_SCHEME_A || d->bc_x == LBM_NEE || d->bc_y == LBM_NEE) {
+        if (d->prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "Scheme A and extrapolation are built for LBM_F64 and LBM_F32");
+        if (d->steps_per_pass != 1) return fail(LBM_EUNSUPPORTED, "Scheme A and extrapolation run one step per pass");
+        if (d->kernel_variant > 1) return fail(LBM_EUNSUPPORTED, "Scheme A and extrapolation run kernel_variant 0 or 1");
+    }
     for (int i = 0; i < 4; ++i)
         if (!isfinite(d->phi_wall[i])) return fail(LBM_EINVAL, "non-finite wall value");
     if (d->steps_per_pass != 1 && d->steps_per_pass != 2) return fail(LBM_EINVAL, "steps_per_pass must be 1 or 2");
@@ -130,11 +141,33 @@ Params<C> make_params(const lbm_solver *s)
     for (int i = 0; i < 4; ++i) p.phi_wall[i] = (C)s->d.phi_wall[i];
     p.Afield = s->d.per_cell_K ? (const C *)s->afield : nullptr;
     p.err = s->err;
+    p.scheme_a = s->d.scheme == LBM_SCHEME_A;
+    p.fisher = c.src_family == 1;
+    p.power = c.power > 0 ? c.power : 1;
+    p.b = (C)c.b;
+    p.nee_x = s->d.bc_x == LBM_NEE;
+    p.nee_y = s->d.bc_y == LBM_NEE;
+    p.bv = nullptr;
+    if (p.fisher) p.has_src = 1;
     return p;
 }
 
 template Params<float> make_params<float>(const lbm_solver *);
 template Params<double> make_params<double>(const lbm_solver *);
+
+// the general kernel serves Scheme A, extrapolation walls and the power-law flux
+static bool general_path(const lbm_solver *s)
+{
+    return s->d.scheme == LBM_SCHEME_A || s->d.bc_x == LBM_NEE || s->d.bc_y == LBM_NEE || s->c.conv == 2;
+}
+
+static cudaError_t launch_general(const lbm_solver *s, int src, const double *bv, const void *phi0, int in_prec,
+                                  cudaStream_t st)
+{
+    if (s->d.prec == LBM_F64) return launch_general_f64(s, src, bv, phi0, in_prec, st);
+    if (s->d.prec == LBM_F32) return launch_general_f32(s, src, bv, phi0, in_prec, st);
+    return cudaErrorInvalidValue;
+}
 
 static int check_handle(lbm_handle h)
 {
@@ -208,7 +241,20 @@ int lbm_set_coeffs(lbm_handle h, const lbm_coeffs *c)
 {
     if (check_handle(h)) return LBM_EINVAL;
     if (!c) return fail(LBM_EINVAL, "null lbm_coeffs");
-    if (c->conv != 0 && c->conv != 1) return fail(LBM_EINVAL, "conv must be 0 or 1");
+    if (c->conv < 0 || c->conv > 2) return fail(LBM_EINVAL, "conv must be 0, 1 or 2");
+    if (c->src_family != 0 && c->src_family != 1) return fail(LBM_EINVAL, "src_family must be 0 or 1");
+    if ((c->conv == 2 || c->src_family == 1) && (c->power < 1 || c->power > 16))
+        return fail(LBM_EINVAL, "power (delta) must be in 1..16");
+    if (!isfinite(c->b)) return fail(LBM_EINVAL, "non-finite coefficient");
+    if (c->src_family == 1) {
+        if (h->d.scheme != LBM_SCHEME_A) return fail(LBM_EINVAL, "the Fisher source needs Scheme A (Eq. 35 has no closed form)");
+        if (c->r0 != 0.0 || c->r1 != 0.0) return fail(LBM_EINVAL, "src_family 1 takes b; r0 and r1 must be 0");
+    }
+    if (c->conv == 2) {
+        if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "conv 2 is built for LBM_F64 and LBM_F32");
+        if (h->d.steps_per_pass != 1 || h->d.kernel_variant > 1)
+            return fail(LBM_EUNSUPPORTED, "conv 2 runs one step per pass with kernel_variant 0 or 1");
+    }
     if (c->diff < 0 || c->diff > 2) return fail(LBM_EINVAL, "diff must be 0, 1 or 2");
     for (int i = 0; i < 9; ++i) {
         if (i == 3 || i == 5) continue;
@@ -250,7 +296,9 @@ int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream)
     if (!dev_phi) return fail(LBM_EINVAL, "null phi");
     if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "phi must be LBM_F64 or LBM_F32");
     if (int rc = cuda_check(cudaMemsetAsync(h->err, 0, sizeof(int), (cudaStream_t)stream), "lbm_set_phi")) return rc;
-    if (int rc = cuda_check(launch_init(h, dev_phi, prec, (cudaStream_t)stream), "lbm_set_phi")) return rc;
+    const cudaError_t e = general_path(h) ? launch_general(h, h->cur, nullptr, dev_phi, prec, (cudaStream_t)stream)
+                                          : launch_init(h, dev_phi, prec, (cudaStream_t)stream);
+    if (int rc = cuda_check(e, "lbm_set_phi")) return rc;
     h->phi_set = 1;
     h->t = 0;
     return LBM_OK;
@@ -275,6 +323,23 @@ int lbm_step(lbm_handle h, int nsteps, void *stream)
     if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
     cudaStream_t st = (cudaStream_t)stream;
     int done = 0;
+    if (general_path(h)) {
+        const bool nee = h->d.bc_x == LBM_NEE || h->d.bc_y == LBM_NEE;
+        if (nee && !h->dir_vals) return fail(LBM_EINVAL, "lbm_set_dirichlet has not been called");
+        const size_t rec = 2 * ((size_t)h->d.nx + h->d.ny);
+        for (; done < nsteps; ++done) {
+            const double *bv = nullptr;
+            if (nee) {
+                long long j = h->t - h->dir_t0;
+                j = j < 0 ? 0 : (j >= h->dir_nrec ? h->dir_nrec - 1 : j);
+                bv = h->dir_vals + (size_t)j * rec;
+            }
+            if (int rc = cuda_check(launch_general(h, h->cur, bv, nullptr, 0, st), "lbm_step (general)")) return rc;
+            h->cur ^= 1;
+            h->t += 1;
+        }
+        return LBM_OK;
+    }
     if (h->d.steps_per_pass == 2) {
         for (; done + 2 <= nsteps; done += 2) {
             const cudaError_t e = h->d.kernel_variant == 3   ? launch_step2m(h, h->cur, st)
@@ -291,6 +356,17 @@ int lbm_step(lbm_handle h, int nsteps, void *stream)
         h->cur ^= 1;
         h->t += 1;
     }
+    return LBM_OK;
+}
+
+int lbm_set_dirichlet(lbm_handle h, const double *dev_values, int nrec)
+{
+    if (check_handle(h)) return LBM_EINVAL;
+    if (h->d.bc_x != LBM_NEE && h->d.bc_y != LBM_NEE) return fail(LBM_EINVAL, "no axis uses LBM_NEE");
+    if (!dev_values || nrec < 1) return fail(LBM_EINVAL, "need a device array of nrec >= 1 records");
+    h->dir_vals = dev_values;
+    h->dir_nrec = nrec;
+    h->dir_t0 = h->t;
     return LBM_OK;
 }
 
@@ -401,8 +477,9 @@ static int adjoint_supported(lbm_handle h)
     if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "the adjoint is built for LBM_F64 and LBM_F32");
     if (h->d.bc_x != LBM_PERIODIC || h->d.bc_y != LBM_PERIODIC)
         return fail(LBM_EUNSUPPORTED, "the adjoint is built for periodic boundaries");
-    if (h->c.conv != 0 || h->c.diff != 0 || h->c.r0 != 0.0 || h->c.r1 != 0.0)
+    if (h->c.conv != 0 || h->c.diff != 0 || h->c.r0 != 0.0 || h->c.r1 != 0.0 || h->c.src_family != 0)
         return fail(LBM_EUNSUPPORTED, "the adjoint is built for the linear family (conv 0, diff 0) without source");
+    if (h->d.scheme != LBM_SCHEME_B) return fail(LBM_EUNSUPPORTED, "the adjoint is built for Scheme B");
     return LBM_OK;
 }
 

@@ -57,6 +57,13 @@ struct Params {
     C phi_wall[4];          // west, east, south, north
     const C *Afield;        // per-cell blocks: 3 planes (A3, A35, A5) or null
     int *err;               // checked builds: device word that records index faults
+    // general path: Scheme A, power-law flux, Fisher source, extrapolation walls
+    int scheme_a;           // 1: Scheme A (Remark II); phi(t_n) kept in a plane
+    int fisher;             // 1: R = b phi (1 - phi^power) (Eq. 46)
+    int power;              // delta of the power-law flux (conv 2) and the Fisher source
+    C b;
+    int nee_x, nee_y;       // 1: non-equilibrium extrapolation on that axis
+    const double *bv;       // Dirichlet record of this step: west, east, south, north
 };
 
 // ---- checked builds ------------------------------------------------------------
@@ -151,10 +158,19 @@ struct Coef {
     {
         C Cxx, Cxy, Cyy;
         const C third = C(1.0 / 3.0);
-        if (CONV == 0) {
+        if constexpr (CONV == 0) {
             Bx = p.ux * phi; By = p.uy * phi;
             Bpx = p.ux; Bpy = p.uy;
             Cxx = p.uxx * phi; Cxy = p.uxy * phi; Cyy = p.uyy * phi;
+        } else if constexpr (CONV == 2) {
+            // Eq. 49-50: B = a phi^(d+1)/(d+1), B' = a phi^d, C = a a phi^(2d+1)/(2d+1)
+            C pd = phi;
+            for (int i = 1; i < p.power; ++i) pd = pd * phi;
+            const C pb = pd * phi / C(p.power + 1);
+            const C pc = pd * pd * phi / C(2 * p.power + 1);
+            Bx = p.ux * pb; By = p.uy * pb;
+            Bpx = p.ux * pd; Bpy = p.uy * pd;
+            Cxx = p.uxx * pc; Cxy = p.uxy * pc; Cyy = p.uyy * pc;
         } else {
             const C phi2 = phi * phi;
             Bx = C(0.5) * p.ux * phi2; By = C(0.5) * p.uy * phi2;
@@ -188,25 +204,65 @@ __device__ __forceinline__ C wall_term(const Params<C> &p, int k, C phiw)
 // ---- the collision (Eq. 34 in moment space) ---------------------------------
 // In: pre-collision shifted populations f (pulled). Out: f overwritten with the
 // post-collision fbar*, phi = Eq. 35. A3, A35, A5: relaxation block of the cell.
+// Moments m = M0 f (Eq. 15): rho, e, eps, jx, qx, jy, qy, pxx, pxy.
+template <class C>
+struct Mom {
+    C rho, e, eps, jx, qx, jy, qy, pxx, pxy;
+    __device__ __forceinline__ explicit Mom(const C f[9])
+    {
+        const C ax = f[1] + f[3], ay = f[2] + f[4];
+        const C axis = ax + ay;
+        const C s57 = f[5] + f[7], s68 = f[6] + f[8];
+        const C dg = s57 + s68;
+        rho = f[0] + axis + dg;
+        e = mad(C(2), dg, mad(C(-4), f[0], -axis));
+        eps = mad(C(4), f[0], mad(C(-2), axis, dg));
+        const C dx1 = f[1] - f[3], dy1 = f[2] - f[4];
+        const C d57 = f[5] - f[7];
+        const C dxd = d57 + (f[8] - f[6]);
+        const C dyd = d57 + (f[6] - f[8]);
+        jx = dx1 + dxd; qx = mad(C(-2), dx1, dxd);
+        jy = dy1 + dyd; qy = mad(C(-2), dy1, dyd);
+        pxx = ax - ay;
+        pxy = s57 - s68;
+    }
+};
+
+// f += M0^-1 dm, M0^-1 = M0^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+template <class C>
+__device__ __forceinline__ void add_moment_change(C f[9], C drho, C de, C deps, C djx, C dqx, C djy, C dqy, C dpxx,
+                                                  C dpxy)
+{
+    const C r = drho * C(1.0 / 9.0);
+    const C ee = de * C(1.0 / 36.0);
+    const C pp = deps * C(1.0 / 36.0);
+    const C jxn = djx * C(1.0 / 6.0), qxn = dqx * C(1.0 / 12.0);
+    const C jyn = djy * C(1.0 / 6.0), qyn = dqy * C(1.0 / 12.0);
+    const C pxxn = dpxx * C(0.25), pxyn = dpxy * C(0.25);
+    f[0] += mad(C(4), pp - ee, r);
+    const C base_a = mad(C(-2), pp, r - ee);
+    const C X1 = mad(C(-2), qxn, jxn), Y1 = mad(C(-2), qyn, jyn);
+    const C ba_p = base_a + pxxn, ba_m = base_a - pxxn;
+    f[1] += ba_p + X1;
+    f[3] += ba_p - X1;
+    f[2] += ba_m + Y1;
+    f[4] += ba_m - Y1;
+    const C base_d = mad(C(2), ee, r + pp);
+    const C X2 = jxn + qxn, Y2 = jyn + qyn;
+    const C bd_p = base_d + pxyn, bd_m = base_d - pxyn;
+    const C XpY = X2 + Y2, XmY = X2 - Y2;
+    f[5] += bd_p + XpY;
+    f[6] += bd_m - XmY;
+    f[7] += bd_p - XpY;
+    f[8] += bd_m + XmY;
+}
+
 template <class C, int CONV, int DIFF>
 __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35, C A5, C &phi_out)
 {
-    // moments m = M0 f (Eq. 15): rho, e, eps, jx, qx, jy, qy, pxx, pxy
-    const C ax = f[1] + f[3], ay = f[2] + f[4];
-    const C axis = ax + ay;
-    const C s57 = f[5] + f[7], s68 = f[6] + f[8];
-    const C dg = s57 + s68;
-    const C rho = f[0] + axis + dg;
-    const C e = mad(C(2), dg, mad(C(-4), f[0], -axis));
-    const C eps = mad(C(4), f[0], mad(C(-2), axis, dg));
-    const C dx1 = f[1] - f[3], dy1 = f[2] - f[4];
-    const C d57 = f[5] - f[7];
-    const C dxd = d57 + (f[8] - f[6]);
-    const C dyd = d57 + (f[6] - f[8]);
-    const C jx = dx1 + dxd, qx = mad(C(-2), dx1, dxd);
-    const C jy = dy1 + dyd, qy = mad(C(-2), dy1, dyd);
-    const C pxx = ax - ay;
-    const C pxy = s57 - s68;
+    const Mom<C> mo(f);
+    const C rho = mo.rho, e = mo.e, eps = mo.eps, jx = mo.jx, qx = mo.qx, jy = mo.jy, qy = mo.qy, pxx = mo.pxx,
+            pxy = mo.pxy;
 
     // Eq. 35 for R = r0 + r1 phi
     const C phi = (rho + p.half_r0) * p.inv_den;
@@ -246,29 +302,8 @@ __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35,
         djy += sy - C(0.5) * mad(A35, sx, A5 * sy);
     }
 
-    // f* = f + M0^-1 dm, M0^-1 = M0^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-    const C r = drho * C(1.0 / 9.0);
-    const C ee = de * C(1.0 / 36.0);
-    const C pp = deps * C(1.0 / 36.0);
-    const C jxn = djx * C(1.0 / 6.0), qxn = dqx * C(1.0 / 12.0);
-    const C jyn = djy * C(1.0 / 6.0), qyn = dqy * C(1.0 / 12.0);
-    const C pxxn = dpxx * C(0.25), pxyn = dpxy * C(0.25);
-    f[0] += mad(C(4), pp - ee, r);
-    const C base_a = mad(C(-2), pp, r - ee);
-    const C X1 = mad(C(-2), qxn, jxn), Y1 = mad(C(-2), qyn, jyn);
-    const C ba_p = base_a + pxxn, ba_m = base_a - pxxn;
-    f[1] += ba_p + X1;
-    f[3] += ba_p - X1;
-    f[2] += ba_m + Y1;
-    f[4] += ba_m - Y1;
-    const C base_d = mad(C(2), ee, r + pp);
-    const C X2 = jxn + qxn, Y2 = jyn + qyn;
-    const C bd_p = base_d + pxyn, bd_m = base_d - pxyn;
-    const C XpY = X2 + Y2, XmY = X2 - Y2;
-    f[5] += bd_p + XpY;
-    f[6] += bd_m - XmY;
-    f[7] += bd_p - XpY;
-    f[8] += bd_m + XmY;
+    // f* = f + M0^-1 dm
+    add_moment_change<C>(f, drho, de, deps, djx, dqx, djy, dqy, dpxx, dpxy);
 }
 
 // Equilibrium populations of Eq. 3 (used only at initialisation).

@@ -45,6 +45,10 @@ struct lbm_solver {
     int *err = nullptr;             // index-fault word of checked builds
     int cur = 0;
     long long t = 0;
+    // Dirichlet records of the extrapolated axes (caller-owned device memory)
+    const double *dir_vals = nullptr;
+    int dir_nrec = 0;
+    long long dir_t0 = 0;
     // adjoint (caller-provided second workspace)
     char *adj = nullptr;
     void *lam[2] = {nullptr, nullptr};
@@ -69,6 +73,12 @@ cudaError_t launch_step2(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2m(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2_tma(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step_ptr(const lbm_solver *s, const void *src, void *dst, cudaStream_t st);
+// general path (Scheme A, extrapolation walls, power-law flux): a step when
+// phi0 is null, else the initialisation from phi0
+cudaError_t launch_general_f64(const lbm_solver *s, int src, const double *bv, const void *phi0, int in_prec,
+                               cudaStream_t st);
+cudaError_t launch_general_f32(const lbm_solver *s, int src, const double *bv, const void *phi0, int in_prec,
+                               cudaStream_t st);
 bool step_v4_supported(const lbm_solver *s);
 bool step_v4_preferred(const lbm_solver *s);
 cudaError_t launch_step_v4(const lbm_solver *s, int src, cudaStream_t st);

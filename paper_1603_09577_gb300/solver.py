@@ -9,7 +9,9 @@ import torch
 
 from . import _lib as C
 
-BC = {"periodic": C.LBM_PERIODIC, "abb": C.LBM_ABB, 0: C.LBM_PERIODIC, 1: C.LBM_ABB}
+BC = {"periodic": C.LBM_PERIODIC, "abb": C.LBM_ABB, "nee": C.LBM_NEE,
+      0: C.LBM_PERIODIC, 1: C.LBM_ABB, 2: C.LBM_NEE}
+SCHEME = {"B": C.LBM_SCHEME_B, "A": C.LBM_SCHEME_A}
 REDUCE_KEYS = ("sum", "abs_err", "abs_ref", "sq_err", "sq_ref", "max_abs", "nonfinite", "sum_sq")
 
 
@@ -33,13 +35,15 @@ def _prec_of(t: torch.Tensor) -> int:
 class Solver:
     """One D2Q9 lattice of nx x ny nodes (see include/lbm.h for the contract).
 
-    prec: "f64", "f32" or "bf16s"; bc: (x, y) boundary kinds "periodic"/"abb";
-    phi_wall: (west, east, south, north) Dirichlet values.
+    prec: "f64", "f32" or "bf16s"; bc: (x, y) boundary kinds "periodic", "abb"
+    (anti-bounce-back walls with the constant phi_wall values: west, east, south,
+    north) or "nee" (extrapolated Dirichlet nodes, values from set_dirichlet);
+    scheme: "B" (Eq. 34) or "A" (Remark II).
     """
 
     def __init__(self, nx: int, ny: int, prec: str = "f32", bc=("periodic", "periodic"),
                  phi_wall=(0.0, 0.0, 0.0, 0.0), steps_per_pass: int = 1, per_cell_K: bool = False,
-                 kernel_variant: int = 0, block_rows: int = 0, device=None):
+                 kernel_variant: int = 0, block_rows: int = 0, scheme: str = "B", device=None):
         self.lib = C.lib()
         self.nx, self.ny, self.prec = int(nx), int(ny), prec
         self.device = torch.device(device if device is not None else "cuda")
@@ -50,6 +54,7 @@ class Solver:
         d.steps_per_pass = int(steps_per_pass)
         d.per_cell_K = int(bool(per_cell_K))
         d.kernel_variant, d.block_rows = int(kernel_variant), int(block_rows)
+        d.scheme = SCHEME[scheme]
         self.desc = d
         size = ctypes.c_size_t()
         C.check(self.lib.lbm_workspace_size(ctypes.byref(d), ctypes.byref(size)))
@@ -70,13 +75,17 @@ class Solver:
 
     # -- set-up ------------------------------------------------------------
     def set_coeffs(self, conv: int = 0, u=(0.0, 0.0), diff: int = 0, K=(0.0, 0.0, 0.0),
-                   s=(1.0, 1.2, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1), r0: float = 0.0, r1: float = 0.0):
+                   s=(1.0, 1.2, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1), r0: float = 0.0, r1: float = 0.0,
+                   src_family: int = 0, power: int = 1, b: float = 0.0):
+        """conv 0 / 1 / 2 (power-law flux of degree `power`), diff 0 / 1 / 2;
+        src_family 0: R = r0 + r1 phi, 1: R = b phi (1 - phi^power) (Scheme A)."""
         c = C.Coeffs()
         c.conv, c.diff = int(conv), int(diff)
         c.u[:] = [float(v) for v in u]
         c.K[:] = [float(v) for v in K]
         c.s[:] = [float(v) for v in s]
         c.r0, c.r1 = float(r0), float(r1)
+        c.src_family, c.power, c.b = int(src_family), int(power), float(b)
         C.check(self.lib.lbm_set_coeffs(self.h, ctypes.byref(c)))
         self.coeffs = c
         return self
@@ -96,6 +105,18 @@ class Solver:
     def set_phi_host(self, phi0: torch.Tensor, stream=None):
         assert phi0.shape == (self.ny, self.nx) and not phi0.is_cuda and phi0.is_contiguous()
         C.check(self.lib.lbm_set_phi_host(self.h, _ptr(phi0), _prec_of(phi0), _stream(stream)))
+        return self
+
+    def set_dirichlet(self, values: torch.Tensor):
+        """Dirichlet records of the extrapolated axes: (nrec, 2 (nx + ny)) float64
+        on the device, each record west[ny], east[ny], south[nx], north[nx];
+        record j serves the step that produces the j + 1-th time level from now."""
+        v = values.to(device=self.device, dtype=torch.float64).contiguous()
+        if v.dim() == 1:
+            v = v.view(1, -1)
+        assert v.shape[1] == 2 * (self.nx + self.ny), v.shape
+        self._dirichlet = v
+        C.check(self.lib.lbm_set_dirichlet(self.h, _ptr(v), int(v.shape[0])))
         return self
 
     # -- time stepping -------------------------------------------------------

@@ -1,0 +1,183 @@
+"""Parity of the general CUDA path (Scheme A of Remark II, the power-law flux of
+Eq. 49-50, the Fisher source of Eq. 46 and the non-equilibrium extrapolation
+boundary) with the FP64 oracle's general path, through the C ABI.
+
+Bars (relative L2 of phi): FP64 <= 1e-12, FP32 <= 1e-5. Sizes span several
+32 x 8 blocks with ragged tails; every boundary combination the path accepts,
+both schemes, every flux family, both source families, per-cell tensors, and
+time-dependent Dirichlet records. The Burgers-Fisher workload (Eq. 47) runs at
+its full size and step count.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from paper_1603_09577_gb300 import LBMError, Solver
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+BCN = {0: "periodic", 1: "abb", 2: "nee"}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gre(a, e):
+    return float(np.abs(a - e).sum() / np.abs(e).sum())
+
+
+def records(nx, ny, steps, seed):
+    """Smooth time-dependent Dirichlet records (west, east, south, north)."""
+    rng = np.random.default_rng(seed)
+    base = rng.uniform(0.3, 0.7, 2 * (nx + ny))
+    t = np.arange(1, steps + 1)[:, None]
+    return base[None, :] * (1.0 + 0.05 * np.sin(0.07 * t + base[None, :] * 3.0))
+
+
+_CACHE = {}
+
+
+def oracle_run(sp, phi0, steps, bv):
+    key = (repr(sp), steps, hash(np.ascontiguousarray(phi0).tobytes()),
+           None if bv is None else hash(np.ascontiguousarray(bv).tobytes()),
+           None if sp.Kfield is None else hash(sp.Kfield.tobytes()))
+    if key not in _CACHE:
+        _CACHE[key] = O.run_x(sp, phi0, steps, bv)
+    return _CACHE[key]
+
+
+def run_pair(prec, nx, ny, phi0, steps, bc, scheme, coef, bv=None, walls=(0.2, 0.6, 0.1, 0.4), Kfield=None,
+             block_rows=0):
+    sp = O.Spec(nx=nx, ny=ny, bc_x=bc[0], bc_y=bc[1], phi_wall=walls, Kfield=Kfield, s=W.s9(),
+                scheme=1 if scheme == "A" else 0, **coef)
+    ref = oracle_run(sp, phi0, steps, bv)
+    s = Solver(nx, ny, prec=prec, bc=(BCN[bc[0]], BCN[bc[1]]), phi_wall=walls, scheme=scheme,
+               per_cell_K=Kfield is not None, block_rows=block_rows)
+    s.set_coeffs(s=W.s9(), **coef)
+    if Kfield is not None:
+        s.set_K_field(torch.from_numpy(Kfield).cuda())
+    if bv is not None:
+        s.set_dirichlet(torch.from_numpy(bv).cuda())
+    s.set_phi(torch.from_numpy(np.ascontiguousarray(phi0)).cuda())
+    s.step(steps)
+    return s.phi().cpu().numpy(), ref, s
+
+
+COEFS = {
+    "lin": dict(conv=0, u=(0.06, -0.03), diff=0, K=(0.03, 0.01, 0.02)),
+    "burgers-src": dict(conv=1, u=(0.08, 0.05), diff=2, K=(0.02, 0.004, 0.015), r0=0.001, r1=-0.02),
+    "power2-fisher": dict(conv=2, power=2, u=(0.1, 0.03), diff=1, K=(0.04, 0.0, 0.03), src_family=1, b=0.02),
+    "power1-fisher": dict(conv=2, power=1, u=(0.1, 0.0), diff=0, K=(0.05, 0.0, 0.05), src_family=1, b=0.01),
+    "power3-affine": dict(conv=2, power=3, u=(-0.05, 0.07), diff=2, K=(0.03, -0.008, 0.02), r1=-0.01),
+}
+CASES = [(67, 41, (2, 2)), (40, 33, (2, 0)), (35, 70, (0, 2)), (64, 24, (0, 0)), (52, 19, (1, 1)), (3, 5, (2, 2))]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["A", "B"])
+@pytest.mark.parametrize("name", list(COEFS))
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}" for c in CASES])
+def test_general_parity(prec, scheme, name, case):
+    coef = COEFS[name]
+    if scheme == "B" and coef.get("src_family", 0) == 1:
+        pytest.skip("the Fisher source needs Scheme A")
+    nx, ny, bc = case
+    rng = np.random.default_rng(nx * 7 + ny)
+    phi0 = W.jacobi_smooth(rng.uniform(0.1, 0.9, (ny, nx)), 2)
+    steps = 50
+    bv = records(nx, ny, steps, nx + ny) if 2 in bc else None
+    got, ref, _ = run_pair(prec, nx, ny, phi0, steps, bc, scheme, coef, bv)
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_general_per_cell_tensor_and_block_rows(prec):
+    nx, ny = 70, 45
+    Kf, phi0, _ = W.adjoint_inputs(nx, seed=21, ny=ny)
+    coef = dict(conv=2, power=1, u=(0.05, 0.02), diff=0, K=(0.0, 0.0, 0.0), src_family=1, b=0.01)
+    bv = records(nx, ny, 40, 5)
+    for br in (1, 4, 8):
+        got, ref, _ = run_pair(prec, nx, ny, phi0, 40, (2, 2), "A", coef, bv, Kfield=Kf, block_rows=br)
+        assert rel(got, ref) <= TOL[prec], (br, rel(got, ref))
+
+
+def test_dirichlet_records_advance_and_clamp():
+    """Record j serves the step to t0 + j + 1; past the last record it is reused."""
+    nx, ny = 30, 22
+    rng = np.random.default_rng(2)
+    phi0 = W.jacobi_smooth(rng.uniform(0.2, 0.8, (ny, nx)), 2)
+    coef = COEFS["power1-fisher"]
+    bv = records(nx, ny, 10, 9)
+    full = np.concatenate([bv, np.repeat(bv[-1:], 15, axis=0)])
+    s = Solver(nx, ny, prec="f64", bc=("nee", "nee"), scheme="A").set_coeffs(s=W.s9(), **coef)
+    s.set_dirichlet(torch.from_numpy(bv).cuda())
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    s.step(25)
+    ref = O.run_x(O.Spec(nx=nx, ny=ny, bc_x=2, bc_y=2, s=W.s9(), scheme=1, **coef), phi0, 25, full)
+    assert rel(s.phi().cpu().numpy(), ref) <= 1e-12
+    # a new set of records restarts the count at the current step
+    bv2 = records(nx, ny, 5, 10)
+    s.set_dirichlet(torch.from_numpy(bv2).cuda())
+    s.step(5)
+    sp = O.Spec(nx=nx, ny=ny, bc_x=2, bc_y=2, s=W.s9(), scheme=1, **coef)
+    ref2 = O.run_x(sp, phi0, 30, np.concatenate([full, bv2]))
+    assert rel(s.phi().cpu().numpy(), ref2) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_burgers_fisher_workload(prec):
+    """The Burgers-Fisher problem of Eq. 46-51 (a = 4, b = 1, kappa = 0.12,
+    delta = 1, 301^2 on [-1, 2]^2, c = 40, T = 1: 4000 steps) against the
+    oracle at the full step count, and against Eq. 47."""
+    bf = W.burgers_fisher(300, 1.0)
+    coef = dict(conv=2, power=1, u=bf["u"], diff=0, K=(bf["K"], 0.0, bf["K"]), src_family=1, b=bf["b"])
+    got, ref, s = run_pair(prec, bf["nx"], bf["ny"], bf["phi0"], bf["steps"], (2, 2), "A", coef, bf["bvals"])
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+    assert gre(got, bf["exact"]) < 5e-4
+    # read-out paths agree: the reduction's sum and the phi plane
+    red = s.reduce(torch.from_numpy(bf["exact"]).cuda())
+    assert abs(red["sum"] - got.sum()) <= 1e-9 * abs(got.sum())
+    assert abs(red["abs_err"] / red["abs_ref"] - gre(got, bf["exact"])) < 1e-9
+
+
+def test_scheme_a_save_load_roundtrip():
+    """The Scheme A state includes the phi(t_n) plane: save / load / continue
+    equals an uninterrupted run."""
+    nx, ny = 48, 36
+    rng = np.random.default_rng(4)
+    phi0 = W.jacobi_smooth(rng.uniform(0.1, 0.9, (ny, nx)), 2)
+    coef = COEFS["power2-fisher"]
+    a = Solver(nx, ny, prec="f64", scheme="A").set_coeffs(s=W.s9(), **coef)
+    a.set_phi(torch.from_numpy(phi0).cuda())
+    a.step(10)
+    snap = a.save()
+    a.step(10)
+    b = Solver(nx, ny, prec="f64", scheme="A").set_coeffs(s=W.s9(), **coef)
+    b.set_phi(torch.from_numpy(phi0).cuda())
+    b.load(snap)
+    b.step(10)
+    assert torch.equal(a.phi(), b.phi())
+
+
+def test_general_path_argument_errors():
+    with pytest.raises(LBMError):                      # extrapolation next to an anti-bounce-back axis
+        Solver(20, 20, prec="f32", bc=("nee", "abb"))
+    with pytest.raises(LBMError):                      # BF16S storage
+        Solver(20, 20, prec="bf16s", scheme="A")
+    with pytest.raises(LBMError):                      # two steps per pass
+        Solver(20, 20, prec="f32", bc=("nee", "nee"), steps_per_pass=2)
+    with pytest.raises(LBMError):                      # Fisher source with Scheme B
+        Solver(20, 20, prec="f32").set_coeffs(conv=0, K=(0.02, 0, 0.02), src_family=1, b=0.1, power=1)
+    s = Solver(20, 20, prec="f32", bc=("nee", "periodic")).set_coeffs(conv=0, K=(0.02, 0, 0.02))
+    s.set_phi(torch.full((20, 20), 0.5, device="cuda"))
+    with pytest.raises(LBMError):                      # no Dirichlet records yet
+        s.step(1)
+    with pytest.raises(LBMError):                      # a record of the wrong length is caught in Python
+        try:
+            s.set_dirichlet(torch.zeros(3, 10, device="cuda", dtype=torch.float64))
+        except AssertionError:
+            raise LBMError(1, "shape")
