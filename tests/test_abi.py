@@ -148,3 +148,44 @@ def test_per_cell_field_required():
     assert L.lbm_set_phi(h, ctypes.c_void_p(16), C.LBM_F64, None) == C.LBM_EINVAL
     assert b"K_field" in L.lbm_last_error()
     L.lbm_destroy(h)
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(bc_x=C.LBM_NEE, bc_y=C.LBM_ABB), C.LBM_EINVAL),          # extrapolation beside an anti-bounce-back axis
+    (dict(bc_x=C.LBM_NEE, nx=2), C.LBM_EINVAL),                    # no inward neighbour
+    (dict(scheme=2), C.LBM_EINVAL),
+    (dict(scheme=C.LBM_SCHEME_A, prec=C.LBM_BF16S), C.LBM_EUNSUPPORTED),
+    (dict(bc_y=C.LBM_NEE, steps_per_pass=2), C.LBM_EUNSUPPORTED),
+    (dict(scheme=C.LBM_SCHEME_A, kernel_variant=2), C.LBM_EUNSUPPORTED)])
+def test_general_path_descriptions(bad, code):
+    rc, _ = ws_size(desc(**bad))
+    assert rc == code
+
+
+def test_scheme_a_workspace_holds_the_phi_plane():
+    _, n = ws_size(desc())
+    _, na = ws_size(desc(scheme=C.LBM_SCHEME_A))
+    assert na >= n + 2 * 12 * 64 * 4            # one float plane per buffer
+    _, n64 = ws_size(desc(prec=C.LBM_F64))
+    _, na64 = ws_size(desc(prec=C.LBM_F64, scheme=C.LBM_SCHEME_A))
+    assert na64 >= n64 + 2 * 12 * 64 * 8
+
+
+def test_general_path_coefficients():
+    L = C.lib()
+    h, ws = make(desc(scheme=C.LBM_SCHEME_A, bc_x=C.LBM_NEE))
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=2, power=2, src_family=1, b=0.1))) == 0
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=2, power=0))) == C.LBM_EINVAL
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(src_family=1, power=1, b=0.1, r1=0.2))) == C.LBM_EINVAL
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(src_family=2))) == C.LBM_EINVAL
+    arr = (ctypes.c_double * 64)()
+    assert L.lbm_set_dirichlet(h, ctypes.cast(arr, ctypes.c_void_p), 0) == C.LBM_EINVAL
+    assert L.lbm_set_dirichlet(h, ctypes.cast(arr, ctypes.c_void_p), 1) == 0
+    L.lbm_destroy(h)
+    h, ws = make(desc())                               # Scheme B, periodic
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(src_family=1, power=1, b=0.1))) == C.LBM_EINVAL
+    assert L.lbm_set_dirichlet(h, ctypes.cast(arr, ctypes.c_void_p), 1) == C.LBM_EINVAL
+    h2, ws2 = make(desc(prec=C.LBM_BF16S))
+    assert L.lbm_set_coeffs(h2, ctypes.byref(coeffs(conv=2, power=1))) == C.LBM_EUNSUPPORTED
+    L.lbm_destroy(h)
+    L.lbm_destroy(h2)
