@@ -55,6 +55,7 @@ class Problem(ctypes.Structure):
         ("collision", ctypes.c_int),
         ("scheme", ctypes.c_int), ("power", ctypes.c_int),
         ("src_family", ctypes.c_int), ("b", ctypes.c_double),
+        ("cfree", ctypes.c_int),
     ]
 
 
@@ -119,6 +120,7 @@ class Spec:
     power: int = 1                # delta of conv 2 and of the Fisher source
     src_family: int = 0           # 0 R = r0 + r1 phi, 1 R = b phi (1 - phi^delta)
     b: float = 0.0
+    cfree: int = 0                # 1: Remark III variant (C = 0 plus G_k; Scheme A)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> Problem:
@@ -143,6 +145,7 @@ class Spec:
         p.src_par[:] = sp
         p.collision = self.collision
         p.scheme, p.power, p.src_family, p.b = self.scheme, self.power, self.src_family, float(self.b)
+        p.cfree = self.cfree
         return p
 
 

@@ -27,6 +27,10 @@
  *                                  Btilde = (I - A/2) B' and the source term of
  *                                  Eq. 2 is dt R_k + dt^2/2 d_t R_k with the
  *                                  backward difference of Remark II
+ *   C-free variant ............... Remark III: C = 0 in the equilibrium (Eq. 38) and
+ *                                  the source G_k of Eq. 36-37, d_t B by the backward
+ *                                  difference of Remark II
+ *   Buckley-Leverett flux ........ Eq. 54 (conv 3, scaled by u = dt/dx per axis)
  *   extrapolation boundary ....... non-equilibrium extrapolation (cited in Sec. 3,
  *                                  Guo, Zheng & Shi 2002): a boundary node takes
  *                                  feq(phi_b) plus the non-equilibrium part of
@@ -116,12 +120,23 @@ static void flux(const oracle_problem *p, double phi, double B[2], double Bp[2],
         B[0] = ax * pb;             B[1] = ay * pb;
         Bp[0] = ax * pd;            Bp[1] = ay * pd;
         C[0] = ax * ax * pc;        C[1] = ax * ay * pc;       C[2] = ay * ay * pc;
+    } else if (p->conv == 3) {
+        /* Eq. 54: f = phi^2 / (phi^2 + (1 - phi)^2), g = f (1 - 5 (1 - phi)^2);
+           no closed-form C is used (Remark III variant) */
+        const double q = 1.0 - phi, den = phi * phi + q * q;
+        const double f = phi * phi / den;
+        const double fp = 2.0 * phi * q / (den * den);
+        const double h = 1.0 - 5.0 * q * q;
+        B[0] = ax * f;              B[1] = ay * f * h;
+        Bp[0] = ax * fp;            Bp[1] = ay * (fp * h + f * 10.0 * q);
+        C[0] = C[1] = C[2] = 0.0;
     } else {
         B[0] = ax * phi * phi / 2;  B[1] = ay * phi * phi / 2;
         Bp[0] = ax * phi;           Bp[1] = ay * phi;
         double p3 = phi * phi * phi / 3;
         C[0] = ax * ax * p3;        C[1] = ax * ay * p3;       C[2] = ay * ay * p3;
     }
+    if (p->cfree) C[0] = C[1] = C[2] = 0.0;       /* Eq. 38 */
 }
 
 /* Diffusion function D(phi) = g(phi) I. */
@@ -522,6 +537,18 @@ int oracle_collide_cell_x(const oracle_problem *p, const double K[3], const doub
         }
         matvec_M0inv(ms, relaxed);
         for (int k = 0; k < Q; ++k) fout[k] = relaxed[k] + Rk[k] + 0.5 * (Rk[k] - Rk0[k]);
+        if (p->cfree) {
+            /* Eq. 36-37: + dt G_k, G_k = w_k c_k . (I - A/2) d_t B / c_s^2 with
+               d_t B = [B(phi) - B(phi_prev)] / dt */
+            double B1[2], B0[2], Bp[2], C[3], dB[2], G[2];
+            flux(p, phi, B1, Bp, C);
+            flux(p, phi_prev, B0, Bp, C);
+            dB[0] = B1[0] - B0[0];
+            dB[1] = B1[1] - B0[1];
+            G[0] = dB[0] - 0.5 * (A[0] * dB[0] + A[1] * dB[1]);
+            G[1] = dB[1] - 0.5 * (A[2] * dB[0] + A[3] * dB[1]);
+            for (int k = 0; k < Q; ++k) fout[k] += WK[k] * (CX[k] * G[0] + CY[k] * G[1]) / CS2;
+        }
     } else {
         /* Scheme B (Eq. 34-35), affine source only */
         if (p->src_family != 0) return 1;
@@ -539,6 +566,8 @@ static int check_problem_x(const oracle_problem *p)
     if (p->nx < 1 || p->ny < 1 || p->src != 0 || p->collision != 0) return 1;
     if (p->scheme != 0 && p->scheme != 1) return 1;
     if (p->src_family == 1 && p->scheme != 1) return 1;
+    if (p->cfree && p->scheme != 1) return 1;       /* d_t B needs phi(t_n): Scheme A's plane */
+    if (p->conv == 3 && !p->cfree) return 1;
     if ((p->conv == 2 || p->src_family == 1) && p->power < 1) return 1;
     if (p->bc_x < 0 || p->bc_x > 2 || p->bc_y < 0 || p->bc_y > 2) return 1;
     /* extrapolation needs an inward neighbour inside the domain, and the other

@@ -25,7 +25,9 @@ typedef struct {
     int bc_x, bc_y;         /* 0: periodic, 1: anti-bounce-back Dirichlet wall    */
     double phi_wall[4];     /* wall values: west, east, south, north              */
     int conv;               /* 0: B = u phi, C = u u phi; 1: B = a phi^2/2,
-                               C = a a phi^3/3 (Eq. 7)                            */
+                               C = a a phi^3/3 (Eq. 7); 2: power law (Eq. 49-50);
+                               3: Buckley-Leverett B = (u_x f, u_y g) of Eq. 54
+                               (C-free variant only)                              */
     double u[2];            /* u (conv 0) or a (conv 1)                           */
     int diff;               /* D = g(phi) I with g = 0: phi, 1: phi + phi^2/2,
                                2: phi + phi^3/3                                   */
@@ -48,6 +50,9 @@ typedef struct {
     int src_family;         /* 0: R = r0 + r1 phi; 1: R = b phi (1 - phi^delta)
                                (Eq. 46; Scheme A only)                            */
     double b;               /* Fisher source coefficient                          */
+    int cfree;              /* 1: Remark III variant (Scheme A only): C = 0 in the
+                               equilibrium (Eq. 38) and the extra source G_k of
+                               Eq. 37 with d_t B by a backward difference          */
 } oracle_problem;
 
 /* Status: 0 ok, nonzero invalid argument. */

@@ -203,3 +203,114 @@ def test_general_path_rejects_invalid_problems():
         O.init_x(O.Spec(**base, scheme=1, bc_x=2, bc_y=1), phi0)
     with pytest.raises(ValueError):      # delta must be >= 1
         O.init_x(O.Spec(**{**base, "power": 0}, scheme=1), phi0)
+
+
+# ---- Remark III variant (C = 0 plus G_k) and the Buckley-Leverett flux --------------
+
+def bl_flux(phi, u):
+    """Eq. 54 scaled per axis by u."""
+    f = phi ** 2 / (phi ** 2 + (1 - phi) ** 2)
+    return np.array([u[0] * f, u[1] * f * (1 - 5 * (1 - phi) ** 2)])
+
+
+@pytest.mark.parametrize("conv", [0, 1, 3])
+def test_cfree_source_moments(conv):
+    """Remark III: the equilibrium carries no C (Eq. 38: second moment c_s^2 d D),
+    and with R = 0 the collision of feq adds only dt G_k (Eq. 36-37), whose
+    moments are 0, (I - A/2)[B(phi) - B(phi_prev)] and 0."""
+    K = (0.04, 0.012, 0.02)
+    u = (0.07, -0.04)
+    sp = O.Spec(nx=4, ny=4, conv=conv, u=u, diff=2, K=K, s=W.s9(), scheme=1, cfree=1)
+    A = O.relax_block(K)
+    phi, prev = 0.63, 0.41
+    f = O.feq(sp, phi)
+    g = phi + phi ** 3 / 3
+    second = np.array([[(CX * CX * f).sum(), (CX * CY * f).sum()], [(CY * CX * f).sum(), (CY * CY * f).sum()]])
+    assert np.abs(second - g / 3.0 * np.eye(2)).max() < 1e-15
+    out, _ = O.collide_cell_x(sp, f, phi_prev=prev)
+    d = out - f
+    B = {0: lambda v: np.array(u) * v, 1: lambda v: np.array(u) * v * v / 2, 3: lambda v: bl_flux(v, u)}[conv]
+    want = (np.eye(2) - 0.5 * A) @ (B(phi) - B(prev))
+    assert abs(d.sum()) < 1e-15
+    assert np.abs(np.array([(CX * d).sum(), (CY * d).sum()]) - want).max() < 1e-15
+    assert np.abs(np.array([(CX * CX * d).sum(), (CX * CY * d).sum(), (CY * CY * d).sum()])).max() < 1e-15
+
+
+def test_buckley_leverett_flux_derivative():
+    """B' of the Buckley-Leverett family (used by the source populations, Eq. 9)
+    is the derivative of Eq. 54: through Eq. 10, sum c_k R_k = (I - A/2) B' R."""
+    K = (0.03, 0.0, 0.03)
+    u = (0.05, 0.05)
+    sp = O.Spec(nx=4, ny=4, conv=3, u=u, diff=0, K=K, s=W.s9(), scheme=1, cfree=1, r0=0.01)
+    A = O.relax_block(K)
+    for phi in (0.2, 0.5, 0.77):
+        f = O.feq(sp, phi)
+        out, _ = O.collide_cell_x(sp, f, phi_prev=phi)       # d_t B = 0, R constant
+        d = out - f
+        h = 1e-6
+        Bp = (bl_flux(phi + h, u) - bl_flux(phi - h, u)) / (2 * h)
+        want = (np.eye(2) - 0.5 * A) @ Bp * 0.01
+        assert np.abs(np.array([(CX * d).sum(), (CY * d).sum()]) - want).max() < 1e-12
+
+
+def test_cfree_recovers_the_diffusion_tensor():
+    """Dropping C from the equilibrium alone adds a spurious diffusion
+    (A^-1 - I/2) B' B'^T-type term; Remark III's G_k removes it. For linear
+    advection-diffusion the hill's mean must move by u per step and its
+    covariance grow by 2 K per step (the diffusion tensor of Eq. 1), as for the
+    scheme with the exact C (checked beside it)."""
+    n, K, u = 128, (0.004, 0.001, 0.003), (0.12, -0.07)
+    x = np.arange(n)
+    X, Y = np.meshgrid(x, x)
+
+    def moments(phi):
+        m = phi.sum()
+        mx, my = (X * phi).sum() / m, (Y * phi).sum() / m
+        return np.array([m, mx, my, ((X - mx) ** 2 * phi).sum() / m, ((X - mx) * (Y - my) * phi).sum() / m,
+                         ((Y - my) ** 2 * phi).sum() / m])
+
+    phi0 = np.exp(-((X - 40.0) ** 2 + (Y - 80.0) ** 2) / 50.0)
+    rates = {}
+    for cf in (0, 1):
+        sp = O.Spec(nx=n, ny=n, conv=0, u=u, K=K, s=W.s9(), scheme=1, cfree=cf)
+        F, P = O.init_x(sp, phi0)
+        snaps = []
+        for t in range(300):
+            F, P = O.step_x(sp, F, P)
+            if t in (99, 299):
+                snaps.append(moments(P))
+        rates[cf] = (snaps[1] - snaps[0]) / 200
+    for cf, r in rates.items():
+        assert abs(r[0]) < 1e-12 * phi0.sum()                               # mass
+        assert abs(r[1] - u[0]) < 1e-5 and abs(r[2] - u[1]) < 1e-5          # drift
+        assert np.abs(r[3:] - 2 * np.array(K)).max() < 4e-5, (cf, r[3:])    # 2 K per step, 0.5 %
+    assert np.abs(rates[1][3:] - rates[0][3:]).max() < 1e-5
+
+
+def test_cfree_burgers_fisher_second_order():
+    """Remark III's variant on the travelling wave of Eq. 47: second order, with
+    errors close to those of the exact-C scheme."""
+    errs = []
+    for N in (60, 120, 240):
+        bf = W.burgers_fisher(N, 0.25, c=40.0 * N / 60)
+        sp = bf_spec(bf, 1)
+        sp.cfree = 1
+        errs.append(gre(O.run_x(sp, bf["phi0"], bf["steps"], bf["bvals"]), bf["exact"]))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 1e-4 and all(1.8 < o < 2.2 for o in orders), (errs, orders)
+
+
+def test_buckley_leverett_mass_and_bounds():
+    """Eq. 52-54 (no source, no closed form): on a periodic domain the C-free
+    scheme conserves mass exactly; with kappa = 0.1 (Pe = 30) phi stays in [0, 1]."""
+    N, L = 150, 3.0
+    dx = L / N
+    xs = -1.5 + dx * np.arange(N)
+    X, Y = np.meshgrid(xs, xs)
+    phi0 = np.where(X ** 2 + Y ** 2 < 0.5, 1.0, 0.0)                # Eq. 53
+    dt = dx / 20.0
+    kl = 0.1 * dt / dx ** 2
+    sp = O.Spec(nx=N, ny=N, conv=3, u=(dt / dx, dt / dx), diff=0, K=(kl, 0.0, kl), s=W.s9(), scheme=1, cfree=1)
+    phi = O.run_x(sp, phi0, int(round(0.5 / dt)))
+    assert abs(phi.sum() - phi0.sum()) < 1e-12 * phi0.sum()
+    assert phi.min() > -1e-12 and phi.max() < 1.0
