@@ -105,8 +105,12 @@ typedef struct {
                                1: B = a phi^2/2, C = a a^T phi^3/3 (Eq. 7);
                                2: B = a phi^(delta+1)/(delta+1),
                                   C = a a^T phi^(2 delta+1)/(2 delta+1)
-                                  (Eq. 49-50), delta = power                      */
-    double u[2];            /* u (conv 0) or a (conv 1, 2)                       */
+                                  (Eq. 49-50), delta = power;
+                               3: Buckley-Leverett B = (u_x f, u_y f h),
+                                  f = phi^2/(phi^2 + (1-phi)^2), h = 1 - 5(1-phi)^2
+                                  (Eq. 54), only with cfree = 1                   */
+    double u[2];            /* u (conv 0), a (conv 1, 2) or the per-axis scale
+                               dt/dx (conv 3)                                    */
     int diff;               /* D = g(phi) I, g = 0: phi, 1: phi + phi^2/2,
                                2: phi + phi^3/3                                   */
     double K[3];            /* constant tensor (Kxx, Kxy, Kyy), symmetric positive
@@ -122,6 +126,10 @@ typedef struct {
                                (Eq. 46, Scheme A only; r0 = r1 = 0)               */
     int power;              /* delta in 1..16 for conv 2 and src_family 1        */
     double b;               /* Fisher source coefficient (src_family 1)          */
+    int cfree;              /* 1: Remark III variant, Scheme A only: C = 0 in the
+                               equilibrium (Eq. 38) plus dt G_k (Eq. 36-37),
+                               G_k = w_k c_k . (I - A/2) d_t B / c_s^2 with d_t B
+                               by the backward difference of Remark II           */
 } lbm_coeffs;
 
 /* Bytes of device workspace lbm_create needs for this description. */

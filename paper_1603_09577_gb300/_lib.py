@@ -38,7 +38,8 @@ class Coeffs(ctypes.Structure):
     _fields_ = [("conv", ctypes.c_int), ("u", ctypes.c_double * 2), ("diff", ctypes.c_int),
                 ("K", ctypes.c_double * 3), ("s", ctypes.c_double * 9),
                 ("r0", ctypes.c_double), ("r1", ctypes.c_double),
-                ("src_family", ctypes.c_int), ("power", ctypes.c_int), ("b", ctypes.c_double)]
+                ("src_family", ctypes.c_int), ("power", ctypes.c_int), ("b", ctypes.c_double),
+                ("cfree", ctypes.c_int)]
 
 
 _lock = threading.Lock()

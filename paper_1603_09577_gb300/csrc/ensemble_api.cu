@@ -101,6 +101,7 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
         for (int j = 1; j < 9; ++j)
             if (j != 3 && j != 5 && !(c.s[j] > 0.0 && c.s[j] < 2.0))
                 return fail(LBM_EINVAL, "instance " + std::to_string(i) + ": relaxation rates must lie in (0, 2)");
+        if (c.cfree) return fail(LBM_EUNSUPPORTED, "ensemble instances use the exact-C equilibrium");
         if (c.r0 != 0.0 || c.r1 != 0.0 || c.src_family != 0)
             return fail(LBM_EUNSUPPORTED, "ensemble instances carry no source term");
         double A3, A35, A5;

@@ -31,17 +31,40 @@ __device__ __forceinline__ C source_value(const Params<C> &p, C phi)
 template <class C, int CONV>
 __device__ __forceinline__ void bprime(const Params<C> &p, C phi, C &bx, C &by)
 {
-    if constexpr (CONV == 0) {
+    constexpr int FAM = conv_family<CONV>();
+    if constexpr (FAM == 0) {
         bx = p.ux;
         by = p.uy;
-    } else if constexpr (CONV == 1) {
+    } else if constexpr (FAM == 1) {
         bx = p.ux * phi;
         by = p.uy * phi;
-    } else {
+    } else if constexpr (FAM == 2) {
         C pd = phi;
         for (int i = 1; i < p.power; ++i) pd = pd * phi;
         bx = p.ux * pd;
         by = p.uy * pd;
+    } else {
+        const Coef<C, CONV, 0> q(p, phi);
+        bx = q.Bpx;
+        by = q.Bpy;
+    }
+}
+
+// B(phi) of the flux family (the C-free variant's d_t B)
+template <class C, int CONV>
+__device__ __forceinline__ void flux_b(const Params<C> &p, C phi, C &bx, C &by)
+{
+    constexpr int FAM = conv_family<CONV>();
+    if constexpr (FAM == 0) {
+        bx = p.ux * phi;
+        by = p.uy * phi;
+    } else if constexpr (FAM == 1) {
+        bx = C(0.5) * p.ux * phi * phi;
+        by = C(0.5) * p.uy * phi * phi;
+    } else {
+        const Coef<C, CONV, 0> q(p, phi);
+        bx = q.Bx;
+        by = q.By;
     }
 }
 
@@ -49,6 +72,8 @@ __device__ __forceinline__ void bprime(const Params<C> &p, C phi, C &bx, C &by)
 // Eq. 17, and the source term dt R_k + dt/2 [R_k(t) - R_k(t - dt)], i.e.
 // 3/2 M0 R_vec(t) - 1/2 M0 R_vec(t - dt) with M0 R_vec = (R, -2R, R, Bt_x R,
 // -Bt_x R, Bt_y R, -Bt_y R, 0, 0) and Bt = (I - A/2) B' (Eq. 28, gamma = 0).
+// C-free variant (CONV >= 3, Remark III): + dt G_k of Eq. 37, whose moments are
+// (0, 0, 0, G_x, -G_x, G_y, -G_y, 0, 0), G = (I - A/2) [B(phi) - B(phi_prev)].
 template <class C, int CONV, int DIFF>
 __device__ __forceinline__ void collide_a(const Params<C> &p, C f[9], C A3, C A35, C A5, C phi_prev, C &phi_out)
 {
@@ -88,6 +113,17 @@ __device__ __forceinline__ void collide_a(const Params<C> &p, C f[9], C A3, C A3
         dqx -= Sx;
         djy += Sy;
         dqy -= Sy;
+    }
+    if constexpr (conv_cfree<CONV>()) {
+        C b0x, b0y;
+        flux_b<C, CONV>(p, phi_prev, b0x, b0y);
+        const C dbx = q.Bx - b0x, dby = q.By - b0y;
+        const C gx = dbx - C(0.5) * mad(A3, dbx, A35 * dby);
+        const C gy = dby - C(0.5) * mad(A35, dbx, A5 * dby);
+        djx += gx;
+        dqx -= gx;
+        djy += gy;
+        dqy -= gy;
     }
     add_moment_change<C>(f, drho, de, deps, djx, dqx, djy, dqy, dpxx, dpxy);
 }
@@ -254,12 +290,36 @@ static cudaError_t general_t(const lbm_solver *s, int src, const double *bv, con
     return cudaGetLastError();
 }
 
-// dispatch over the flux / diffusion families and the scheme
+// dispatch over the flux / diffusion families and the scheme; the C-free
+// variant (Scheme A only) maps families 0, 1, 2 to codes 4, 5, 6, and the
+// Buckley-Leverett flux is code 3
 template <int PREC>
 static cudaError_t general_p(const lbm_solver *s, int src, const double *bv, const void *phi0, int in_prec,
                              cudaStream_t st)
 {
     const bool sa = s->d.scheme == LBM_SCHEME_A;
+    if (s->c.cfree) {
+        if (!sa) return cudaErrorInvalidValue;
+        const int code = s->c.conv == 3 ? 3 : s->c.conv + 4;
+#define LBM_GEN_CF(CV, DF) \
+    case CV * 3 + DF: return general_t<PREC, CV, DF, true>(s, src, bv, phi0, in_prec, st);
+        switch (code * 3 + s->c.diff) {
+            LBM_GEN_CF(3, 0)
+            LBM_GEN_CF(3, 1)
+            LBM_GEN_CF(3, 2)
+            LBM_GEN_CF(4, 0)
+            LBM_GEN_CF(4, 1)
+            LBM_GEN_CF(4, 2)
+            LBM_GEN_CF(5, 0)
+            LBM_GEN_CF(5, 1)
+            LBM_GEN_CF(5, 2)
+            LBM_GEN_CF(6, 0)
+            LBM_GEN_CF(6, 1)
+            LBM_GEN_CF(6, 2)
+        }
+#undef LBM_GEN_CF
+        return cudaErrorInvalidValue;
+    }
 #define LBM_GEN_CASE(CV, DF)                                                                    \
     case CV * 3 + DF:                                                                           \
         return sa ? general_t<PREC, CV, DF, true>(s, src, bv, phi0, in_prec, st)                \

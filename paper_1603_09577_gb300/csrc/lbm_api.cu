@@ -144,6 +144,8 @@ Params<C> make_params(const lbm_solver *s)
     p.scheme_a = s->d.scheme == LBM_SCHEME_A;
     p.fisher = c.src_family == 1;
     p.power = c.power > 0 ? c.power : 1;
+    p.inv_p1 = (C)(1.0 / (p.power + 1));
+    p.inv_p2 = (C)(1.0 / (2 * p.power + 1));
     p.b = (C)c.b;
     p.nee_x = s->d.bc_x == LBM_NEE;
     p.nee_y = s->d.bc_y == LBM_NEE;
@@ -158,7 +160,7 @@ template Params<double> make_params<double>(const lbm_solver *);
 // the general kernel serves Scheme A, extrapolation walls and the power-law flux
 static bool general_path(const lbm_solver *s)
 {
-    return s->d.scheme == LBM_SCHEME_A || s->d.bc_x == LBM_NEE || s->d.bc_y == LBM_NEE || s->c.conv == 2;
+    return s->d.scheme == LBM_SCHEME_A || s->d.bc_x == LBM_NEE || s->d.bc_y == LBM_NEE || s->c.conv >= 2;
 }
 
 static cudaError_t launch_general(const lbm_solver *s, int src, const double *bv, const void *phi0, int in_prec,
@@ -241,7 +243,11 @@ int lbm_set_coeffs(lbm_handle h, const lbm_coeffs *c)
 {
     if (check_handle(h)) return LBM_EINVAL;
     if (!c) return fail(LBM_EINVAL, "null lbm_coeffs");
-    if (c->conv < 0 || c->conv > 2) return fail(LBM_EINVAL, "conv must be 0, 1 or 2");
+    if (c->conv < 0 || c->conv > 3) return fail(LBM_EINVAL, "conv must be 0, 1, 2 or 3");
+    if (c->cfree != 0 && c->cfree != 1) return fail(LBM_EINVAL, "cfree must be 0 or 1");
+    if (c->cfree && h->d.scheme != LBM_SCHEME_A)
+        return fail(LBM_EINVAL, "the C-free variant needs Scheme A (its d_t B uses the phi(t_n) plane)");
+    if (c->conv == 3 && !c->cfree) return fail(LBM_EINVAL, "the Buckley-Leverett flux (conv 3) needs cfree = 1");
     if (c->src_family != 0 && c->src_family != 1) return fail(LBM_EINVAL, "src_family must be 0 or 1");
     if ((c->conv == 2 || c->src_family == 1) && (c->power < 1 || c->power > 16))
         return fail(LBM_EINVAL, "power (delta) must be in 1..16");
@@ -250,10 +256,10 @@ int lbm_set_coeffs(lbm_handle h, const lbm_coeffs *c)
         if (h->d.scheme != LBM_SCHEME_A) return fail(LBM_EINVAL, "the Fisher source needs Scheme A (Eq. 35 has no closed form)");
         if (c->r0 != 0.0 || c->r1 != 0.0) return fail(LBM_EINVAL, "src_family 1 takes b; r0 and r1 must be 0");
     }
-    if (c->conv == 2) {
-        if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "conv 2 is built for LBM_F64 and LBM_F32");
+    if (c->conv >= 2) {
+        if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "conv 2 and 3 are built for LBM_F64 and LBM_F32");
         if (h->d.steps_per_pass != 1 || h->d.kernel_variant > 1)
-            return fail(LBM_EUNSUPPORTED, "conv 2 runs one step per pass with kernel_variant 0 or 1");
+            return fail(LBM_EUNSUPPORTED, "conv 2 and 3 run one step per pass with kernel_variant 0 or 1");
     }
     if (c->diff < 0 || c->diff > 2) return fail(LBM_EINVAL, "diff must be 0, 1 or 2");
     for (int i = 0; i < 9; ++i) {
@@ -477,7 +483,7 @@ static int adjoint_supported(lbm_handle h)
     if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "the adjoint is built for LBM_F64 and LBM_F32");
     if (h->d.bc_x != LBM_PERIODIC || h->d.bc_y != LBM_PERIODIC)
         return fail(LBM_EUNSUPPORTED, "the adjoint is built for periodic boundaries");
-    if (h->c.conv != 0 || h->c.diff != 0 || h->c.r0 != 0.0 || h->c.r1 != 0.0 || h->c.src_family != 0)
+    if (h->c.conv != 0 || h->c.diff != 0 || h->c.r0 != 0.0 || h->c.r1 != 0.0 || h->c.src_family != 0 || h->c.cfree)
         return fail(LBM_EUNSUPPORTED, "the adjoint is built for the linear family (conv 0, diff 0) without source");
     if (h->d.scheme != LBM_SCHEME_B) return fail(LBM_EUNSUPPORTED, "the adjoint is built for Scheme B");
     return LBM_OK;

@@ -61,6 +61,7 @@ struct Params {
     int scheme_a;           // 1: Scheme A (Remark II); phi(t_n) kept in a plane
     int fisher;             // 1: R = b phi (1 - phi^power) (Eq. 46)
     int power;              // delta of the power-law flux (conv 2) and the Fisher source
+    C inv_p1, inv_p2;       // 1 / (delta + 1), 1 / (2 delta + 1)
     C b;
     int nee_x, nee_y;       // 1: non-equilibrium extrapolation on that axis
     const double *bv;       // Dirichlet record of this step: west, east, south, north
@@ -151,23 +152,41 @@ template <> struct Store<LBM_BF16S> {
 
 // ---- coefficient families (Eq. 1, Eq. 7) ------------------------------------
 // Second-moment tensor Cbar = C(phi) + d c_s^2 g(phi) I, flux B and B'.
+// CONV codes: 0 linear, 1 Burgers, 2 power law (Eq. 49-50), with C of Eq. 7;
+// 3 Buckley-Leverett (Eq. 54) and 4, 5, 6 = families 0, 1, 2 in the C-free
+// variant of Remark III (C = 0 in the equilibrium, Eq. 38).
+template <int CONV> constexpr int conv_family() { return CONV >= 4 ? CONV - 4 : CONV; }
+template <int CONV> constexpr bool conv_cfree() { return CONV >= 3; }
+
 template <class C, int CONV, int DIFF>
 struct Coef {
     C Bx, By, Bpx, Bpy, Cbxx, Cbxy, Cbyy;
     __device__ __forceinline__ Coef(const Params<C> &p, C phi)
     {
+        constexpr int FAM = conv_family<CONV>();
         C Cxx, Cxy, Cyy;
         const C third = C(1.0 / 3.0);
-        if constexpr (CONV == 0) {
+        if constexpr (FAM == 3) {
+            // Eq. 54 scaled per axis: B = (u_x f, u_y f h), f = phi^2 / (phi^2 + (1 - phi)^2),
+            // h = 1 - 5 (1 - phi)^2
+            const C q = C(1) - phi, den = mad(phi, phi, q * q);
+            const C rden = C(1) / den;
+            const C f = phi * phi * rden;
+            const C fp = C(2) * phi * q * rden * rden;
+            const C h = mad(C(-5) * q, q, C(1));
+            Bx = p.ux * f; By = p.uy * f * h;
+            Bpx = p.ux * fp; Bpy = p.uy * mad(fp, h, f * C(10) * q);
+            Cxx = C(0); Cxy = C(0); Cyy = C(0);
+        } else if constexpr (FAM == 0) {
             Bx = p.ux * phi; By = p.uy * phi;
             Bpx = p.ux; Bpy = p.uy;
             Cxx = p.uxx * phi; Cxy = p.uxy * phi; Cyy = p.uyy * phi;
-        } else if constexpr (CONV == 2) {
+        } else if constexpr (FAM == 2) {
             // Eq. 49-50: B = a phi^(d+1)/(d+1), B' = a phi^d, C = a a phi^(2d+1)/(2d+1)
             C pd = phi;
             for (int i = 1; i < p.power; ++i) pd = pd * phi;
-            const C pb = pd * phi / C(p.power + 1);
-            const C pc = pd * pd * phi / C(2 * p.power + 1);
+            const C pb = pd * phi * p.inv_p1;
+            const C pc = pd * pd * phi * p.inv_p2;
             Bx = p.ux * pb; By = p.uy * pb;
             Bpx = p.ux * pd; Bpy = p.uy * pd;
             Cxx = p.uxx * pc; Cxy = p.uxy * pc; Cyy = p.uyy * pc;
@@ -177,6 +196,9 @@ struct Coef {
             Bpx = p.ux * phi; Bpy = p.uy * phi;
             const C p3 = phi2 * phi * third;
             Cxx = p.uxx * p3; Cxy = p.uxy * p3; Cyy = p.uyy * p3;
+        }
+        if constexpr (conv_cfree<CONV>()) {
+            Cxx = C(0); Cxy = C(0); Cyy = C(0);
         }
         C g;
         if (DIFF == 0) g = phi;

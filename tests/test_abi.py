@@ -189,3 +189,15 @@ def test_general_path_coefficients():
     assert L.lbm_set_coeffs(h2, ctypes.byref(coeffs(conv=2, power=1))) == C.LBM_EUNSUPPORTED
     L.lbm_destroy(h)
     L.lbm_destroy(h2)
+
+
+def test_cfree_and_buckley_leverett_coefficients():
+    L = C.lib()
+    h, ws = make(desc(scheme=C.LBM_SCHEME_A))
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=3, cfree=1))) == 0
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=3))) == C.LBM_EINVAL       # conv 3 needs cfree
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=1, cfree=2))) == C.LBM_EINVAL
+    L.lbm_destroy(h)
+    h, ws = make(desc())                                                          # Scheme B
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=0, cfree=1))) == C.LBM_EINVAL
+    L.lbm_destroy(h)

@@ -54,7 +54,10 @@ def run_pair(prec, nx, ny, phi0, steps, bc, scheme, coef, bv=None, walls=(0.2, 0
              block_rows=0):
     sp = O.Spec(nx=nx, ny=ny, bc_x=bc[0], bc_y=bc[1], phi_wall=walls, Kfield=Kfield, s=W.s9(),
                 scheme=1 if scheme == "A" else 0, **coef)
-    ref = oracle_run(sp, phi0, steps, bv)
+    bv_all = bv
+    if bv is not None and len(bv) < steps:          # the library reuses the last record
+        bv_all = np.concatenate([bv, np.repeat(bv[-1:], steps - len(bv), axis=0)])
+    ref = oracle_run(sp, phi0, steps, bv_all)
     s = Solver(nx, ny, prec=prec, bc=(BCN[bc[0]], BCN[bc[1]]), phi_wall=walls, scheme=scheme,
                per_cell_K=Kfield is not None, block_rows=block_rows)
     s.set_coeffs(s=W.s9(), **coef)
@@ -73,6 +76,10 @@ COEFS = {
     "power2-fisher": dict(conv=2, power=2, u=(0.1, 0.03), diff=1, K=(0.04, 0.0, 0.03), src_family=1, b=0.02),
     "power1-fisher": dict(conv=2, power=1, u=(0.1, 0.0), diff=0, K=(0.05, 0.0, 0.05), src_family=1, b=0.01),
     "power3-affine": dict(conv=2, power=3, u=(-0.05, 0.07), diff=2, K=(0.03, -0.008, 0.02), r1=-0.01),
+    "bl-cfree": dict(conv=3, u=(0.06, 0.06), diff=0, K=(0.03, 0.0, 0.03), cfree=1),
+    "burgers-cfree-src": dict(conv=1, u=(0.08, -0.05), diff=1, K=(0.02, 0.005, 0.015), r1=-0.02, cfree=1),
+    "power2-fisher-cfree": dict(conv=2, power=2, u=(0.1, 0.03), diff=2, K=(0.04, 0.0, 0.03), src_family=1, b=0.02,
+                                cfree=1),
 }
 CASES = [(67, 41, (2, 2)), (40, 33, (2, 0)), (35, 70, (0, 2)), (64, 24, (0, 0)), (52, 19, (1, 1)), (3, 5, (2, 2))]
 
@@ -83,8 +90,8 @@ CASES = [(67, 41, (2, 2)), (40, 33, (2, 0)), (35, 70, (0, 2)), (64, 24, (0, 0)),
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}" for c in CASES])
 def test_general_parity(prec, scheme, name, case):
     coef = COEFS[name]
-    if scheme == "B" and coef.get("src_family", 0) == 1:
-        pytest.skip("the Fisher source needs Scheme A")
+    if scheme == "B" and (coef.get("src_family", 0) == 1 or coef.get("cfree", 0)):
+        pytest.skip("the Fisher source and the C-free variant need Scheme A")
     nx, ny, bc = case
     rng = np.random.default_rng(nx * 7 + ny)
     phi0 = W.jacobi_smooth(rng.uniform(0.1, 0.9, (ny, nx)), 2)
@@ -142,6 +149,18 @@ def test_burgers_fisher_workload(prec):
     red = s.reduce(torch.from_numpy(bf["exact"]).cuda())
     assert abs(red["sum"] - got.sum()) <= 1e-9 * abs(got.sum())
     assert abs(red["abs_err"] / red["abs_ref"] - gre(got, bf["exact"])) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kappa", [0.1, 0.01])
+def test_buckley_leverett_workload(prec, kappa):
+    """The Buckley-Leverett problem of Eq. 52-54 (301^2 on [-1.5, 1.5]^2, the
+    disc of Eq. 53, T = 0.5, c = 20: 1000 steps) with the C-free variant of
+    Remark III, against the oracle at the full step count."""
+    bl = W.buckley_leverett(300, kappa, 0.5)
+    coef = dict(conv=3, u=bl["u"], diff=0, K=(bl["K"], 0.0, bl["K"]), cfree=1)
+    got, ref, s = run_pair(prec, bl["nx"], bl["ny"], bl["phi0"], bl["steps"], (2, 2), "A", coef, bl["bvals"])
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
 def test_scheme_a_save_load_roundtrip():

@@ -17,6 +17,9 @@ Workloads (sizes, parameters and seeds):
                        u = (0.03, 0), 500 steps, smooth seeded fields (seed 4)
   ensemble_256         256 nonlinear CDE instances, sides log-uniform in [64, 1024],
                        |u| <= 0.1, D(phi) = D0 (1 + phi), D0 in [0.001, 0.05] (seed 5)
+  buckley_leverett_*   2-D Buckley-Leverett equation (Eq. 52-54) on [-1.5, 1.5]^2, the disc
+                       of Eq. 53 as initial data, kappa = 0.1 or 0.01, C-free variant
+                       (Remark III) with zero-valued extrapolated walls
   burgers_fisher_*     2-D Burgers-Fisher equation (Eq. 46-51) on [-1, 2]^2 with the
                        travelling-wave solution of Eq. 47-48 as initial and Dirichlet
                        data, a = 4, b = 1, delta = 1, kappa = 0.12 (Pe = La/kappa = 100,
@@ -202,3 +205,19 @@ def burgers_fisher(N: int, T: float, c: float = 40.0, a: float = 4.0, b: float =
         bv[s, 3 * n:4 * n] = ex(xs, xs[-1], t)     # north
     return dict(nx=n, ny=n, dx=dx, dt=dt, steps=steps, u=(a * dt / dx, 0.0), K=kappa * dt / dx ** 2,
                 b=b * dt, power=delta, phi0=ex(X, Y, 0.0), bvals=bv, exact=ex(X, Y, steps * dt))
+
+
+# ---- Buckley-Leverett (Eq. 52-54) -------------------------------------------------
+
+def buckley_leverett(N: int, kappa: float, T: float, c: float = 20.0, L: float = 3.0) -> dict:
+    """The Buckley-Leverett problem on [-L/2, L/2]^2 with N intervals (N + 1
+    nodes per side), lattice speed c = dx/dt, to time T. Lattice units: the flux
+    is scaled by dt/dx per axis and kappa by dt/dx^2. Walls: zero Dirichlet
+    values (the disc of Eq. 53 stays far from them up to T = 0.5)."""
+    dx = L / N
+    dt = dx / c
+    xs = -L / 2 + dx * np.arange(N + 1)
+    X, Y = np.meshgrid(xs, xs)
+    n = N + 1
+    return dict(nx=n, ny=n, dx=dx, dt=dt, steps=int(round(T / dt)), u=(dt / dx, dt / dx), K=kappa * dt / dx ** 2,
+                phi0=np.where(X ** 2 + Y ** 2 < 0.5, 1.0, 0.0), bvals=np.zeros((1, 4 * n)))
