@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--ens-count", type=int, default=256, help="instances of the ensemble workload")
     ap.add_argument("--ens-spp", type=int, default=2, help="time steps per persistent ensemble launch (1 or 2)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "ensemble_256", "adjoint_512", "burgers_fisher_4096"],
+                    choices=[WORKLOAD, "ensemble_256", "adjoint_512", "burgers_fisher_4096", "stability_sweep"],
                     help="the default is the headline workload; the others print their own line")
     return ap.parse_args()
 
@@ -452,6 +452,50 @@ def run_burgers_fisher(args):
     print(json.dumps(out), flush=True)
 
 
+def run_stability_sweep(args):
+    """Sec. 3.6's stability comparison as a sweep: the fully anisotropic
+    Gaussian hill (Eq. 75, second approach D = Dm phi, u = (0.1, 0.1), 400^2,
+    c = 1, T = 5: 1000 steps) for decreasing kappa, with the MRT rates of Eq. 76
+    (s = 0.6) and with every rate s3 (BGK). Each run reports its GRE against
+    Eq. 60, or "unstable" (a non-finite phi or max |phi| > 10)."""
+    import torch
+
+    from paper_1603_09577_gb300 import Solver
+    import oracle as O
+    prec = args.prec if args.prec in ("f32", "f64") else "f64"
+    rows = []
+    ms_all, updates = 0.0, 0
+    for kap in (1e-3, 5e-4, 2e-4, 1e-4, 5e-5, 2e-5, 1e-5):
+        g = W.gaussian_hill_square((kap, kap, 2 * kap), (0.1, 0.1), 5.0)
+        kl = g["K"][0]
+        sj = float(O.relax_block((kl, 0.0, kl))[0, 0])
+        phi0 = torch.from_numpy(g["phi0"]).cuda()
+        ex = torch.from_numpy(g["exact"]).cuda()
+        row = {"kappa": kap, "kappa_lattice": kl, "s3": sj}
+        for name, rates in (("mrt", (0.0, 0.6, 0.6, 0.0, 0.6, 0.0, 0.6, 0.6, 0.6)), ("bgk", (sj,) * 9)):
+            s = Solver(g["n"], g["n"], prec=prec)
+            s.set_coeffs(conv=0, u=g["u"], diff=3, Dm=(1.0, 1.0, 2.0), K=(kl, 0.0, kl), s=rates)
+            s.set_phi(phi0)
+            st = torch.cuda.current_stream()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            s.step(g["steps"])
+            b.record(st)
+            r = s.reduce(ex)
+            ms_all += a.elapsed_time(b)
+            updates += g["n"] ** 2 * g["steps"]
+            ok = r["nonfinite"] == 0 and r["max_abs"] <= 10.0
+            row[name] = r["abs_err"] / r["abs_ref"] if ok else "unstable"
+        rows.append(row)
+    out = {"metric": "MLUPS", "value": updates / (ms_all / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
+           "higher_is_better": True, "dtype": prec, "data": "synthetic",
+           "config": {"workload": "stability_sweep: Sec. 3.6 fully anisotropic Gaussian hill (Eq. 75), second "
+                                  "approach D = [[1,1],[1,2]] phi, u = (0.1, 0.1), 400x400, c = 1, 1000 steps per run, "
+                                  "MRT (Eq. 76, s = 0.6) against BGK (all rates s3)"},
+           "sweep": rows, "gpu_launches": len(rows) * 2 * (1 + 1000 + 2)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -462,6 +506,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "burgers_fisher_4096":
         return run_burgers_fisher(args)
+    if args.workload == "stability_sweep":
+        return run_stability_sweep(args)
     import torch
     import torch.distributed as dist
 

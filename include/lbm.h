@@ -112,7 +112,9 @@ typedef struct {
     double u[2];            /* u (conv 0), a (conv 1, 2) or the per-axis scale
                                dt/dx (conv 3)                                    */
     int diff;               /* D = g(phi) I, g = 0: phi, 1: phi + phi^2/2,
-                               2: phi + phi^3/3                                   */
+                               2: phi + phi^3/3; 3: D = Dm phi with the constant
+                               symmetric tensor Dm (the isotropic form of Eq. 62,
+                               Dm = K / kappa with K = kappa I here)              */
     double K[3];            /* constant tensor (Kxx, Kxy, Kyy), symmetric positive
                                definite; the block A = [[s3, s35], [s53, s5]] of
                                Eq. 17 follows from Eq. 26:
@@ -126,6 +128,7 @@ typedef struct {
                                (Eq. 46, Scheme A only; r0 = r1 = 0)               */
     int power;              /* delta in 1..16 for conv 2 and src_family 1        */
     double b;               /* Fisher source coefficient (src_family 1)          */
+    double Dm[3];           /* Dm_xx, Dm_xy, Dm_yy of diff 3                     */
     int cfree;              /* 1: Remark III variant, Scheme A only: C = 0 in the
                                equilibrium (Eq. 38) plus dt G_k (Eq. 36-37),
                                G_k = w_k c_k . (I - A/2) d_t B / c_s^2 with d_t B

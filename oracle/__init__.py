@@ -55,7 +55,7 @@ class Problem(ctypes.Structure):
         ("collision", ctypes.c_int),
         ("scheme", ctypes.c_int), ("power", ctypes.c_int),
         ("src_family", ctypes.c_int), ("b", ctypes.c_double),
-        ("cfree", ctypes.c_int),
+        ("Dm", ctypes.c_double * 3), ("cfree", ctypes.c_int),
     ]
 
 
@@ -121,6 +121,7 @@ class Spec:
     src_family: int = 0           # 0 R = r0 + r1 phi, 1 R = b phi (1 - phi^delta)
     b: float = 0.0
     cfree: int = 0                # 1: Remark III variant (C = 0 plus G_k; Scheme A)
+    Dm: tuple = (1.0, 0.0, 1.0)   # diff 3: D = Dm phi (Eq. 62's isotropic form)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> Problem:
@@ -146,6 +147,7 @@ class Spec:
         p.collision = self.collision
         p.scheme, p.power, p.src_family, p.b = self.scheme, self.power, self.src_family, float(self.b)
         p.cfree = self.cfree
+        p.Dm[:] = list(self.Dm)
         return p
 
 

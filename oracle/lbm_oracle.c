@@ -11,7 +11,8 @@
  *
  * What each function follows:
  *   lattice, weights ............ Eq. 5 (D2Q9), c = 1, c_s^2 = c^2/3
- *   equilibrium .................. Eq. 3 with D = g(phi) I, d = 1 (Sec. 3)
+ *   equilibrium .................. Eq. 3 with D = g(phi) I or D = Dm phi (Eq. 62),
+ *                                  d = 1 (Sec. 3)
  *   C(phi) from B'(phi) .......... Eq. 7
  *   discrete source .............. Eq. 9 with Btilde = B' (Scheme B, Eq. 28)
  *   M0, moments .................. Eq. 8, Eq. 14-15 (M^-1 S M = M0^-1 S M0, Eq. 18)
@@ -153,11 +154,17 @@ int oracle_feq(const oracle_problem *p, double phi, double feq[9])
 {
     double B[2], Bp[2], C[3];
     flux(p, phi, B, Bp, C);
-    double g = gdiff(p, phi);
+    /* D(phi): g(phi) I, or Dm phi (diff 3, the isotropic form of Eq. 62) */
+    double Dxx, Dxy, Dyy;
+    if (p->diff == 3) {
+        Dxx = p->Dm[0] * phi; Dxy = p->Dm[1] * phi; Dyy = p->Dm[2] * phi;
+    } else {
+        Dxx = Dyy = gdiff(p, phi); Dxy = 0.0;
+    }
     /* (C + d c_s^2 D - c_s^2 phi I), Eq. 3 */
-    double Qxx = C[0] + DPAR * CS2 * g - CS2 * phi;
-    double Qxy = C[1];
-    double Qyy = C[2] + DPAR * CS2 * g - CS2 * phi;
+    double Qxx = C[0] + DPAR * CS2 * Dxx - CS2 * phi;
+    double Qxy = C[1] + DPAR * CS2 * Dxy;
+    double Qyy = C[2] + DPAR * CS2 * Dyy - CS2 * phi;
     for (int k = 0; k < Q; ++k) {
         double cx = CX[k], cy = CY[k];
         double cB = cx * B[0] + cy * B[1];
@@ -568,6 +575,7 @@ static int check_problem_x(const oracle_problem *p)
     if (p->src_family == 1 && p->scheme != 1) return 1;
     if (p->cfree && p->scheme != 1) return 1;       /* d_t B needs phi(t_n): Scheme A's plane */
     if (p->conv == 3 && !p->cfree) return 1;
+    if (p->diff < 0 || p->diff > 3) return 1;
     if ((p->conv == 2 || p->src_family == 1) && p->power < 1) return 1;
     if (p->bc_x < 0 || p->bc_x > 2 || p->bc_y < 0 || p->bc_y > 2) return 1;
     /* extrapolation needs an inward neighbour inside the domain, and the other

@@ -30,7 +30,9 @@ typedef struct {
                                (C-free variant only)                              */
     double u[2];            /* u (conv 0) or a (conv 1)                           */
     int diff;               /* D = g(phi) I with g = 0: phi, 1: phi + phi^2/2,
-                               2: phi + phi^3/3                                   */
+                               2: phi + phi^3/3; 3: D = Dm phi, a constant
+                               symmetric tensor (the isotropic form of Eq. 62,
+                               D = K phi / kappa; general path only)              */
     double K[3];            /* constant diffusion tensor Kxx, Kxy, Kyy            */
     const double *Kfield;   /* optional per-cell tensor, 3 planes of nx*ny
                                (Kxx, Kxy, Kyy); overrides K when not NULL         */
@@ -50,6 +52,7 @@ typedef struct {
     int src_family;         /* 0: R = r0 + r1 phi; 1: R = b phi (1 - phi^delta)
                                (Eq. 46; Scheme A only)                            */
     double b;               /* Fisher source coefficient                          */
+    double Dm[3];           /* Dm_xx, Dm_xy, Dm_yy of diff 3                      */
     int cfree;              /* 1: Remark III variant (Scheme A only): C = 0 in the
                                equilibrium (Eq. 38) and the extra source G_k of
                                Eq. 37 with d_t B by a backward difference          */

@@ -39,7 +39,7 @@ class Coeffs(ctypes.Structure):
                 ("K", ctypes.c_double * 3), ("s", ctypes.c_double * 9),
                 ("r0", ctypes.c_double), ("r1", ctypes.c_double),
                 ("src_family", ctypes.c_int), ("power", ctypes.c_int), ("b", ctypes.c_double),
-                ("cfree", ctypes.c_int)]
+                ("Dm", ctypes.c_double * 3), ("cfree", ctypes.c_int)]
 
 
 _lock = threading.Lock()

@@ -302,38 +302,45 @@ static cudaError_t general_p(const lbm_solver *s, int src, const double *bv, con
         if (!sa) return cudaErrorInvalidValue;
         const int code = s->c.conv == 3 ? 3 : s->c.conv + 4;
 #define LBM_GEN_CF(CV, DF) \
-    case CV * 3 + DF: return general_t<PREC, CV, DF, true>(s, src, bv, phi0, in_prec, st);
-        switch (code * 3 + s->c.diff) {
+    case CV * 4 + DF: return general_t<PREC, CV, DF, true>(s, src, bv, phi0, in_prec, st);
+        switch (code * 4 + s->c.diff) {
             LBM_GEN_CF(3, 0)
             LBM_GEN_CF(3, 1)
             LBM_GEN_CF(3, 2)
+            LBM_GEN_CF(3, 3)
             LBM_GEN_CF(4, 0)
             LBM_GEN_CF(4, 1)
             LBM_GEN_CF(4, 2)
+            LBM_GEN_CF(4, 3)
             LBM_GEN_CF(5, 0)
             LBM_GEN_CF(5, 1)
             LBM_GEN_CF(5, 2)
+            LBM_GEN_CF(5, 3)
             LBM_GEN_CF(6, 0)
             LBM_GEN_CF(6, 1)
             LBM_GEN_CF(6, 2)
+            LBM_GEN_CF(6, 3)
         }
 #undef LBM_GEN_CF
         return cudaErrorInvalidValue;
     }
 #define LBM_GEN_CASE(CV, DF)                                                                    \
-    case CV * 3 + DF:                                                                           \
+    case CV * 4 + DF:                                                                           \
         return sa ? general_t<PREC, CV, DF, true>(s, src, bv, phi0, in_prec, st)                \
                   : general_t<PREC, CV, DF, false>(s, src, bv, phi0, in_prec, st);
-    switch (s->c.conv * 3 + s->c.diff) {
+    switch (s->c.conv * 4 + s->c.diff) {
         LBM_GEN_CASE(0, 0)
         LBM_GEN_CASE(0, 1)
         LBM_GEN_CASE(0, 2)
+        LBM_GEN_CASE(0, 3)
         LBM_GEN_CASE(1, 0)
         LBM_GEN_CASE(1, 1)
         LBM_GEN_CASE(1, 2)
+        LBM_GEN_CASE(1, 3)
         LBM_GEN_CASE(2, 0)
         LBM_GEN_CASE(2, 1)
         LBM_GEN_CASE(2, 2)
+        LBM_GEN_CASE(2, 3)
     }
 #undef LBM_GEN_CASE
     return cudaErrorInvalidValue;

@@ -146,6 +146,9 @@ Params<C> make_params(const lbm_solver *s)
     p.power = c.power > 0 ? c.power : 1;
     p.inv_p1 = (C)(1.0 / (p.power + 1));
     p.inv_p2 = (C)(1.0 / (2 * p.power + 1));
+    p.dmxx = (C)c.Dm[0];
+    p.dmxy = (C)c.Dm[1];
+    p.dmyy = (C)c.Dm[2];
     p.b = (C)c.b;
     p.nee_x = s->d.bc_x == LBM_NEE;
     p.nee_y = s->d.bc_y == LBM_NEE;
@@ -160,7 +163,8 @@ template Params<double> make_params<double>(const lbm_solver *);
 // the general kernel serves Scheme A, extrapolation walls and the power-law flux
 static bool general_path(const lbm_solver *s)
 {
-    return s->d.scheme == LBM_SCHEME_A || s->d.bc_x == LBM_NEE || s->d.bc_y == LBM_NEE || s->c.conv >= 2;
+    return s->d.scheme == LBM_SCHEME_A || s->d.bc_x == LBM_NEE || s->d.bc_y == LBM_NEE || s->c.conv >= 2 ||
+           s->c.diff == 3;
 }
 
 static cudaError_t launch_general(const lbm_solver *s, int src, const double *bv, const void *phi0, int in_prec,
@@ -261,7 +265,14 @@ int lbm_set_coeffs(lbm_handle h, const lbm_coeffs *c)
         if (h->d.steps_per_pass != 1 || h->d.kernel_variant > 1)
             return fail(LBM_EUNSUPPORTED, "conv 2 and 3 run one step per pass with kernel_variant 0 or 1");
     }
-    if (c->diff < 0 || c->diff > 2) return fail(LBM_EINVAL, "diff must be 0, 1 or 2");
+    if (c->diff < 0 || c->diff > 3) return fail(LBM_EINVAL, "diff must be 0, 1, 2 or 3");
+    if (c->diff == 3) {
+        if (!isfinite(c->Dm[0]) || !isfinite(c->Dm[1]) || !isfinite(c->Dm[2]))
+            return fail(LBM_EINVAL, "non-finite diffusion tensor Dm");
+        if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "diff 3 is built for LBM_F64 and LBM_F32");
+        if (h->d.steps_per_pass != 1 || h->d.kernel_variant > 1)
+            return fail(LBM_EUNSUPPORTED, "diff 3 runs one step per pass with kernel_variant 0 or 1");
+    }
     for (int i = 0; i < 9; ++i) {
         if (i == 3 || i == 5) continue;
         if (!(c->s[i] > 0.0 && c->s[i] < 2.0) && !(i == 0 && c->s[i] == 0.0))

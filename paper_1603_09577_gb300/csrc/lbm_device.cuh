@@ -62,6 +62,7 @@ struct Params {
     int fisher;             // 1: R = b phi (1 - phi^power) (Eq. 46)
     int power;              // delta of the power-law flux (conv 2) and the Fisher source
     C inv_p1, inv_p2;       // 1 / (delta + 1), 1 / (2 delta + 1)
+    C dmxx, dmxy, dmyy;     // diff 3: D = Dm phi (the isotropic form of Eq. 62)
     C b;
     int nee_x, nee_y;       // 1: non-equilibrium extrapolation on that axis
     const double *bv;       // Dirichlet record of this step: west, east, south, north
@@ -200,12 +201,18 @@ struct Coef {
         if constexpr (conv_cfree<CONV>()) {
             Cxx = C(0); Cxy = C(0); Cyy = C(0);
         }
-        C g;
-        if (DIFF == 0) g = phi;
-        else if (DIFF == 1) g = mad(C(0.5) * phi, phi, phi);
-        else g = mad(phi * phi * third, phi, phi);
-        const C cg = g * third;              // d c_s^2 g with d = 1
-        Cbxx = Cxx + cg; Cbyy = Cyy + cg; Cbxy = Cxy;
+        if constexpr (DIFF == 3) {
+            // D = Dm phi: d c_s^2 D with d = 1
+            const C pt = phi * third;
+            Cbxx = mad(p.dmxx, pt, Cxx); Cbxy = mad(p.dmxy, pt, Cxy); Cbyy = mad(p.dmyy, pt, Cyy);
+        } else {
+            C g;
+            if (DIFF == 0) g = phi;
+            else if (DIFF == 1) g = mad(C(0.5) * phi, phi, phi);
+            else g = mad(phi * phi * third, phi, phi);
+            const C cg = g * third;              // d c_s^2 g with d = 1
+            Cbxx = Cxx + cg; Cbyy = Cyy + cg; Cbxy = Cxy;
+        }
     }
 };
 

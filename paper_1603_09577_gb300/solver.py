@@ -76,10 +76,11 @@ class Solver:
     # -- set-up ------------------------------------------------------------
     def set_coeffs(self, conv: int = 0, u=(0.0, 0.0), diff: int = 0, K=(0.0, 0.0, 0.0),
                    s=(1.0, 1.2, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1), r0: float = 0.0, r1: float = 0.0,
-                   src_family: int = 0, power: int = 1, b: float = 0.0, cfree: int = 0):
+                   src_family: int = 0, power: int = 1, b: float = 0.0, cfree: int = 0, Dm=(1.0, 0.0, 1.0)):
         """conv 0 / 1 / 2 (power-law flux of degree `power`) / 3 (Buckley-Leverett,
         cfree only), diff 0 / 1 / 2; src_family 0: R = r0 + r1 phi, 1: R = b phi
-        (1 - phi^power) (Scheme A); cfree 1: the C-free variant of Remark III."""
+        (1 - phi^power) (Scheme A); cfree 1: the C-free variant of Remark III;
+        diff 3: D = Dm phi (Dm = (xx, xy, yy))."""
         c = C.Coeffs()
         c.conv, c.diff = int(conv), int(diff)
         c.u[:] = [float(v) for v in u]
@@ -88,6 +89,7 @@ class Solver:
         c.r0, c.r1 = float(r0), float(r1)
         c.src_family, c.power, c.b = int(src_family), int(power), float(b)
         c.cfree = int(cfree)
+        c.Dm[:] = [float(v) for v in Dm]
         C.check(self.lib.lbm_set_coeffs(self.h, ctypes.byref(c)))
         self.coeffs = c
         return self

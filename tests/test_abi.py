@@ -97,7 +97,7 @@ def coeffs(**kw):
     c.K[:] = [0.01, 0.0, 0.01]
     c.s[:] = [1.0, 1.2, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1]
     for k, v in kw.items():
-        if k in ("u", "K", "s"):
+        if k in ("u", "K", "s", "Dm"):
             getattr(c, k)[:] = v
         else:
             setattr(c, k, v)
@@ -200,4 +200,16 @@ def test_cfree_and_buckley_leverett_coefficients():
     L.lbm_destroy(h)
     h, ws = make(desc())                                                          # Scheme B
     assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=0, cfree=1))) == C.LBM_EINVAL
+    L.lbm_destroy(h)
+
+
+def test_tensor_diffusion_coefficients():
+    L = C.lib()
+    h, ws = make(desc())
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=3, Dm=[1.0, 1.0, 2.0]))) == 0
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=4))) == C.LBM_EINVAL
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=3, Dm=[float("inf"), 0.0, 1.0]))) == C.LBM_EINVAL
+    L.lbm_destroy(h)
+    h, ws = make(desc(steps_per_pass=2))
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=3, Dm=[1.0, 0.0, 1.0]))) == C.LBM_EUNSUPPORTED
     L.lbm_destroy(h)

@@ -221,3 +221,48 @@ def buckley_leverett(N: int, kappa: float, T: float, c: float = 20.0, L: float =
     n = N + 1
     return dict(nx=n, ny=n, dx=dx, dt=dt, steps=int(round(T / dt)), u=(dt / dx, dt / dx), K=kappa * dt / dx ** 2,
                 phi0=np.where(X ** 2 + Y ** 2 < 0.5, 1.0, 0.0), bvals=np.zeros((1, 4 * n)))
+
+
+# ---- Gaussian hill of Sec. 3.4 / 3.6 (Eq. 58-60) -------------------------------------
+
+def gaussian_hill_square(K, u, T, n: int = 400, sigma0: float = 0.01, L: float = 2.0) -> dict:
+    """The Gaussian hill of Eq. 60 on the periodic square [-L/2, L/2)^2 with n
+    nodes per side (dx = L / n, c = 1 so dt = dx), physical K (Kxx, Kxy, Kyy)
+    and u, run to time T. Returns lattice units (u dt/dx, K dt/dx^2), the
+    initial field and Eq. 60 at the final time, each summed over the 3 x 3
+    nearest periodic images. phi0 = 2 pi sigma0^2 makes the peak 1."""
+    dx = L / n
+    dt = dx
+    steps = int(round(T / dt))
+    xs = -L / 2 + dx * np.arange(n)
+    X, Y = np.meshgrid(xs, xs)
+
+    def hill(t):
+        S = sigma0 ** 2 * np.eye(2) + 2 * np.array([[K[0], K[1]], [K[1], K[2]]]) * t
+        Si = np.linalg.inv(S)
+        out = np.zeros((n, n))
+        for mx in (-1, 0, 1):
+            for my in (-1, 0, 1):
+                ddx = X - u[0] * t + mx * L
+                ddy = Y - u[1] * t + my * L
+                out += np.exp(-(Si[0, 0] * ddx * ddx + 2 * Si[0, 1] * ddx * ddy + Si[1, 1] * ddy * ddy) / 2)
+        return sigma0 ** 2 / math.sqrt(np.linalg.det(S)) * out
+
+    return dict(n=n, dx=dx, dt=dt, steps=steps, u=(u[0] * dt / dx, u[1] * dt / dx),
+                K=tuple(k * dt / dx ** 2 for k in K), phi0=hill(0.0), exact=hill(steps * dt))
+
+
+S_EQ41 = (0.0, 1.0, 1.0, 0.0, 1.0, 0.0, 1.0, 1.0, 1.0)   # Eq. 41 (s3, s5 come from K)
+
+
+def read_golden(name: str) -> dict:
+    """case -> printed value from a tests/golden table (comment lines start with #)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", name)
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                key, val = line.split()[:2]
+                out[key] = float(val)
+    return out
