@@ -37,6 +37,12 @@ BYTES_PER_UPDATE = {"f32": 72, "bf16s": 44, "f64": 144}
 KERNEL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
               for f in ("kernels_step.cu", "kernels_step_vec.cu", "kernels_step2.cuh", "kernels_step2_f32.cu",
                         "kernels_step2_bf16.cu", "lbm_device.cuh")]
+GENERAL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
+               for f in ("kernels_general.cuh", "kernels_general_f32.cu", "kernels_general_f64.cu", "lbm_device.cuh")]
+
+
+def src_sha(files) -> str:
+    return hashlib.sha256(b"".join(open(f, "rb").read() for f in files)).hexdigest()
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -166,10 +172,12 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def traffic_per_launch(kernel_sha):
+def traffic_per_launch(kernel_sha, key="k_step2"):
+    """DRAM bytes per launch from the committed ncu capture of this kernel, or
+    None when the kernel's sources changed since the capture."""
     try:
         with open(TRAFFIC_FILE) as f:
-            t = json.load(f)
+            t = json.load(f)[key]
         if t.get("kernel_src_sha256") != kernel_sha:
             return None
         return t["dram_bytes_per_full_launch"]
@@ -428,7 +436,8 @@ def run_burgers_fisher(args):
                       "nx": n, "ny": n, "lattice": {"u": bf["u"], "K": bf["K"], "b": bf["b"]},
                       "l2": "inputs larger than L2 (two population buffers of 604 MB each, FP32)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": None, "kernel": "k_step_g (general one-step kernel, Scheme A)",
+                        "traffic": traffic_per_launch(src_sha(GENERAL_SRC), "k_step_g") if prec == "f32" else None,
+                        "kernel": "k_step_g (general one-step kernel, Scheme A)",
                         "algorithmic_bytes_per_update": bpu, "avg_launch_ms": launch_ms,
                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src},
            "e2e": {"value": cells * lbm_steps / (e2e_ms / 1e3) / 1e6, "unit": "MLUPS",
@@ -597,7 +606,7 @@ def main():
         alg_bytes = BYTES_PER_UPDATE[args.prec] * cells
         achieved = alg_bytes / (launch_ms / 1e3) / 1e9
         peak, src = measured_peak()
-        sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRC)).hexdigest()
+        sha = src_sha(KERNEL_SRC)
         kernel = ("k_step2 (two fused pull-stream + collide steps per sweep)" if args.spp == 2 else
                   "k_step_v4 (fused pull-stream + collide, four nodes per thread)" if args.variant == 2 or
                   (args.variant == 0 and args.prec == "bf16s") else "k_step (fused pull-stream + collide)")
