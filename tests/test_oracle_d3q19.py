@@ -1,0 +1,114 @@
+"""Pins of the D3Q19 oracle (oracle/d3q19.py): the moment conditions of
+Eq. 10 in three dimensions, the three-dimensional Gaussian hill of Eq. 60 with
+second-order convergence, exact invariants, and the claim that the moment
+reading (plain-orthogonal basis with rho and j rows, one rate for the other
+moments) is the paper's D2Q9 model when applied to D2Q9."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle import d3q19 as D
+
+
+def gre(a, e):
+    return float(np.abs(a - e).sum() / np.abs(e).sum())
+
+
+@pytest.mark.parametrize("conv,diff", [(0, 0), (1, 1), (1, 2), (0, 2)])
+def test_equilibrium_and_source_moments(conv, diff):
+    """Eq. 10 in 3-D: sum feq = phi, sum c feq = B, sum c c feq = C + d c_s^2 D,
+    sum R_k = R, sum c R_k = B' R."""
+    sp = D.Spec3(nx=1, ny=1, nz=1, conv=conv, u=(0.07, -0.04, 0.03), diff=diff)
+    a = np.array(sp.u)
+    for phi in (0.3, 0.9):
+        f = D.feq(sp, np.array([phi]))[:, 0]
+        B = a * phi if conv == 0 else a * phi ** 2 / 2
+        Cm = np.outer(a, a) * (phi if conv == 0 else phi ** 3 / 3)
+        g = [phi, phi + phi ** 2 / 2, phi + phi ** 3 / 3][diff]
+        assert abs(f.sum() - phi) < 1e-15
+        assert np.abs(D.C.T @ f - B).max() < 1e-15
+        assert np.abs(np.einsum("k,ka,kb->ab", f, D.C, D.C) - (Cm + g / 3 * np.eye(3))).max() < 1e-15
+        Rk = D.source_pop(sp, np.array([phi]), np.array([0.2]))[:, 0]
+        Bp = a if conv == 0 else a * phi
+        assert abs(Rk.sum() - 0.2) < 1e-15
+        assert np.abs(D.C.T @ Rk - 0.2 * Bp).max() < 1e-15
+
+
+def test_reading_reduces_to_the_d2q9_model():
+    """The same construction on D2Q9 -- P = s_e I + (s0 - s_e) Pi_rho
+    + Pi_j (A - s_e I) with plain-orthogonal projectors onto (1) and (c_x, c_y) --
+    is the paper's M0 model (Eq. 15-17) with s1 = s2 = s4 = s6 = s7 = s8 = s_e."""
+    se, s0 = 1.15, 0.7
+    K = (0.03, 0.011, 0.02)
+    sp = O.Spec(nx=1, ny=1, conv=1, u=(0.06, -0.02), diff=1, K=K, s=(s0, se, se, 0, se, 0, se, se, se), r1=-0.05)
+    A = O.relax_block(K)
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1.0])
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1.0])
+    Cm = np.stack([cx, cy], 1)
+    P = se * np.eye(9) + (s0 - se) * np.ones((9, 9)) / 9 + Cm @ (A - se * np.eye(2)) @ Cm.T / 6
+    Qm = (1 - se / 2) * np.eye(9) - 0.5 * (s0 - se) * np.ones((9, 9)) / 9 - 0.5 * Cm @ (A - se * np.eye(2)) @ Cm.T / 6
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        f = O.feq(sp, 0.6) + rng.normal(0, 0.01, 9)
+        out, phi = O.collide_cell(sp, f)
+        fe = O.feq(sp, phi)
+        Rk = O.source_pop(sp, phi, sp.r1 * phi)
+        want = f - P @ (f - fe) + Qm @ Rk
+        assert np.abs(out - want).max() < 1e-15
+
+
+def gaussian3(n, c0, sigma0, u, K, t):
+    """Eq. 60 in three dimensions, summed over the 27 nearest periodic images."""
+    Km = D.k_matrix(K)
+    Sig = sigma0 ** 2 * np.eye(3) + 2 * Km * t
+    Si = np.linalg.inv(Sig)
+    x = np.arange(n, dtype=np.float64)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    out = np.zeros((n, n, n))
+    for mz in (-1, 0, 1):
+        for my in (-1, 0, 1):
+            for mx in (-1, 0, 1):
+                d = np.stack([X - c0 - u[0] * t + mx * n, Y - c0 - u[1] * t + my * n, Z - c0 - u[2] * t + mz * n])
+                out += np.exp(-0.5 * np.einsum("a...,ab,b...->...", d, Si, d))
+    return sigma0 ** 3 / math.sqrt(np.linalg.det(Sig)) * out
+
+
+def test_gaussian_hill_3d_second_order():
+    """Linear anisotropic advection-diffusion (full 3 x 3 K) against Eq. 60 in
+    3-D under diffusive refinement: observed order in [1.8, 2.2]."""
+    K = (0.02, 0.006, 0.004, 0.015, 0.003, 0.01)
+    errs = []
+    for n in (12, 24, 48):
+        r = n // 12
+        steps, sig, u = 10 * r * r, n / 8, (0.04 / r, 0.02 / r, -0.03 / r)
+        sp = D.Spec3(nx=n, ny=n, nz=n, conv=0, u=u, K=K, se=1.1)
+        phi0 = gaussian3(n, n / 2, sig, u, K, 0.0)
+        errs.append(gre(D.run(sp, phi0, steps), gaussian3(n, n / 2, sig, u, K, steps)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 <= o <= 2.2 for o in orders), (errs, orders)
+
+
+def test_invariants_3d():
+    """Mass (R = 0), s0 independence (Scheme B), a uniform fixed point, and the
+    x -> y -> z axis rotation of field, u and K."""
+    rng = np.random.default_rng(3)
+    nx, ny, nz = 9, 7, 6
+    phi0 = rng.uniform(0.2, 0.8, (nz, ny, nx))
+    base = dict(conv=1, u=(0.05, -0.03, 0.02), diff=2, K=(0.02, 0.004, -0.003, 0.015, 0.002, 0.012), se=1.2)
+    sp = D.Spec3(nx=nx, ny=ny, nz=nz, **base)
+    phi = D.run(sp, phi0, 15)
+    assert abs(phi.sum() - phi0.sum()) < 1e-13 * phi0.sum()
+    src = D.Spec3(nx=nx, ny=ny, nz=nz, **{**base, "s0": 0.5}, r0=0.001, r1=-0.03)
+    src1 = D.Spec3(nx=nx, ny=ny, nz=nz, **{**base, "s0": 1.5}, r0=0.001, r1=-0.03)
+    assert np.abs(D.run(src, phi0, 10) - D.run(src1, phi0, 10)).max() < 1e-14
+    flat = D.run(sp, np.full((nz, ny, nx), 0.4), 5)
+    assert np.abs(flat - 0.4).max() < 1e-15
+    # rotation (x, y, z) -> (y, z, x): field axes (z, y, x) -> (x, z, y)
+    kxx, kxy, kxz, kyy, kyz, kzz = base["K"]
+    rot = D.Spec3(nx=ny, ny=nz, nz=nx, conv=1, u=(base["u"][1], base["u"][2], base["u"][0]), diff=2,
+                  K=(kyy, kyz, kxy, kzz, kxz, kxx), se=1.2)
+    phir = D.run(rot, np.transpose(phi0, (2, 0, 1)), 15)
+    assert np.abs(phir - np.transpose(phi, (2, 0, 1))).max() < 1e-13
