@@ -9,5 +9,6 @@ from . import adjoint, ensemble, tune  # noqa: F401
 from ._lib import LBMError, lib  # noqa: F401
 from .ensemble import Ensemble  # noqa: F401
 from .solver import Solver  # noqa: F401
+from .solver3 import Solver3  # noqa: F401
 
-__all__ = ["Solver", "Ensemble", "LBMError", "lib", "adjoint", "ensemble", "tune"]
+__all__ = ["Solver", "Solver3", "Ensemble", "LBMError", "lib", "adjoint", "ensemble", "tune"]

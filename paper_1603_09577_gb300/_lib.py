@@ -42,6 +42,17 @@ class Coeffs(ctypes.Structure):
                 ("Dm", ctypes.c_double * 3), ("cfree", ctypes.c_int)]
 
 
+class Desc3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("prec", ctypes.c_int),
+                ("block_rows", ctypes.c_int)]
+
+
+class Coeffs3(ctypes.Structure):
+    _fields_ = [("conv", ctypes.c_int), ("u", ctypes.c_double * 3), ("diff", ctypes.c_int),
+                ("K", ctypes.c_double * 6), ("s0", ctypes.c_double), ("se", ctypes.c_double),
+                ("r0", ctypes.c_double), ("r1", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -72,6 +83,14 @@ SIGNATURES = {
     "lbm_adjoint_step": [_VP, _VP, _VP],
     "lbm_adjoint_end": [_VP, _VP, _I, _VP, _VP, _VP, _VP],
     "lbm_adjoint_segment": [_VP, _VP, _I, _VP, _SZ, _VP],
+    "lbm3_workspace_size": [ctypes.POINTER(Desc3), ctypes.POINTER(_SZ)],
+    "lbm3_create": [ctypes.POINTER(_VP), ctypes.POINTER(Desc3), _VP, _SZ],
+    "lbm3_destroy": [_VP],
+    "lbm3_set_coeffs": [_VP, ctypes.POINTER(Coeffs3)],
+    "lbm3_set_phi": [_VP, _VP, _I, _VP],
+    "lbm3_step": [_VP, _I, _VP],
+    "lbm3_get_phi": [_VP, _VP, _I, _VP],
+    "lbm3_reduce": [_VP, _VP, _VP, _VP],
     "lbm_ensemble_workspace_size": [_I, _VP, _VP, ctypes.POINTER(_SZ)],
     "lbm_ensemble_create": [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, _SZ],
     "lbm_ensemble_destroy": [_VP],

@@ -231,6 +231,39 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce2(const double *__rest
     block_reduce(v, out);
 }
 
+// the same statistics over a plain FP64 field (the D3Q19 solver's phi)
+__global__ void __launch_bounds__(kReduceThreads)
+k_reduce_field1(const double *__restrict__ field, long long n, const double *__restrict__ ref,
+                double *__restrict__ partials)
+{
+    double v[kNacc] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double ph = field[i];
+        if (!isfinite(ph)) { v[6] += 1.0; continue; }
+        v[0] += ph;
+        v[7] += ph * ph;
+        v[5] = fmax(v[5], fabs(ph));
+        if (ref) {
+            const double r = ref[i], d = ph - r;
+            v[1] += fabs(d);
+            v[2] += fabs(r);
+            v[3] += d * d;
+            v[4] += r * r;
+        }
+    }
+    block_reduce(v, partials + (size_t)blockIdx.x * kNacc);
+}
+
+cudaError_t launch_reduce_field(const double *field, long long n, const double *ref, double *partials, double *out,
+                                cudaStream_t st)
+{
+    k_reduce_field1<<<kReduceBlocks, kReduceThreads, 0, st>>>(field, n, ref, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce2<<<1, kReduceThreads, 0, st>>>(partials, kReduceBlocks, out);
+    return cudaGetLastError();
+}
+
 template <int PREC>
 static cudaError_t reduce_p(const lbm_solver *s, const double *ref, double *out, cudaStream_t st)
 {

@@ -1,0 +1,457 @@
+// lbm3_d3q19.cu -- the three-dimensional (D3Q19) fused stream-collide step,
+// its initialisation and read-out, and the lbm3_* C ABI (include/lbm3.h).
+//
+// One thread per node, x fastest (warps of 32 along x), a grid of
+// (x tiles, y tiles, z). Every step pulls the 19 populations f_k(x) =
+// f*_k(x - c_k) with periodic wrap (19 reads and 19 writes per update: 152 B
+// in FP32), then collides in the projector form of the moment reading (see
+// lbm3.h): feq of Eq. 3 per direction, the flux block acting on j - B, and the
+// Scheme B source.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "lbm3.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Eq. 6: D3Q19 velocities in the paper's order and weights
+__host__ __device__ constexpr int c3x(int k)
+{
+    constexpr int v[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1, 0, 0, 0, 0};
+    return v[k];
+}
+__host__ __device__ constexpr int c3y(int k)
+{
+    constexpr int v[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return v[k];
+}
+__host__ __device__ constexpr int c3z(int k)
+{
+    constexpr int v[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1};
+    return v[k];
+}
+template <class C>
+__host__ __device__ constexpr C w3(int k)
+{
+    return k == 0 ? C(1) / C(3) : (k <= 6 ? C(1) / C(18) : C(1) / C(36));
+}
+
+template <class C>
+struct Params3 {
+    int nx, ny, nz;
+    long long pitch, plane;          // plane = pitch * ny * nz
+    C se, hse;                       // s_e and 1 - s_e/2
+    C G[6];                          // A - s_e I: xx, xy, xz, yy, yz, zz
+    C ux, uy, uz;
+    C r0, r1, half_r0, inv_den, inv_post;
+    int has_src;
+};
+
+template <int CONV, int DIFF, class C>
+__device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_out)
+{
+    C rho = C(0), jx = C(0), jy = C(0), jz = C(0);
+#pragma unroll
+    for (int k = 0; k < 19; ++k) {
+        rho += f[k];
+        if (c3x(k)) jx += C(c3x(k)) * f[k];
+        if (c3y(k)) jy += C(c3y(k)) * f[k];
+        if (c3z(k)) jz += C(c3z(k)) * f[k];
+    }
+    const C phi = (rho + p.half_r0) * p.inv_den;                 // Eq. 35
+    phi_out = phi;
+    // B, B' and C (Eq. 7 families), g(phi)
+    C Bx, By, Bz, bpx, bpy, bpz, cphi;
+    if (CONV == 0) {
+        Bx = p.ux * phi; By = p.uy * phi; Bz = p.uz * phi;
+        bpx = p.ux; bpy = p.uy; bpz = p.uz;
+        cphi = phi;
+    } else {
+        const C h = C(0.5) * phi * phi;
+        Bx = p.ux * h; By = p.uy * h; Bz = p.uz * h;
+        bpx = p.ux * phi; bpy = p.uy * phi; bpz = p.uz * phi;
+        cphi = phi * phi * phi * C(1.0 / 3.0);
+    }
+    C g;
+    if (DIFF == 0) g = phi;
+    else if (DIFF == 1) g = phi + C(0.5) * phi * phi;
+    else g = phi + phi * phi * phi * C(1.0 / 3.0);
+    // Q = C + c_s^2 g I - c_s^2 phi I; feq_k = w_k [phi + 3 c.B + 4.5 (c Q c - trQ/3)]
+    const C diag = (g - phi) * C(1.0 / 3.0);
+    const C Qxx = p.ux * p.ux * cphi + diag, Qyy = p.uy * p.uy * cphi + diag, Qzz = p.uz * p.uz * cphi + diag;
+    const C Qxy = p.ux * p.uy * cphi, Qxz = p.ux * p.uz * cphi, Qyz = p.uy * p.uz * cphi;
+    const C tr3 = (Qxx + Qyy + Qzz) * C(1.0 / 3.0);
+    C R = C(0);
+    if (p.has_src) R = p.r1 * phi + p.r0;
+    // G = (A - s_e I) [(j - B) + B' R / 2]
+    const C vx = (jx - Bx) + C(0.5) * bpx * R, vy = (jy - By) + C(0.5) * bpy * R, vz = (jz - Bz) + C(0.5) * bpz * R;
+    const C Gx = (p.G[0] * vx + p.G[1] * vy + p.G[2] * vz) * C(0.1);
+    const C Gy = (p.G[1] * vx + p.G[3] * vy + p.G[4] * vz) * C(0.1);
+    const C Gz = (p.G[2] * vx + p.G[4] * vy + p.G[5] * vz) * C(0.1);
+#pragma unroll
+    for (int k = 0; k < 19; ++k) {
+        const C cx_ = C(c3x(k)), cy_ = C(c3y(k)), cz_ = C(c3z(k));
+        const C cB = cx_ * Bx + cy_ * By + cz_ * Bz;
+        const C cQc = cx_ * cx_ * Qxx + cy_ * cy_ * Qyy + cz_ * cz_ * Qzz +
+                      C(2) * (cx_ * cy_ * Qxy + cx_ * cz_ * Qxz + cy_ * cz_ * Qyz);
+        const C fe = w3<C>(k) * (phi + C(3) * cB + C(4.5) * (cQc - tr3));
+        const C cG = cx_ * Gx + cy_ * Gy + cz_ * Gz;
+        C v = f[k] - p.se * (f[k] - fe) - cG;
+        if (p.has_src) v += p.hse * w3<C>(k) * (C(1) + C(3) * (cx_ * bpx + cy_ * bpy + cz_ * bpz)) * R;
+        f[k] = v;
+    }
+}
+
+template <class T, int CONV, int DIFF>
+__global__ void __launch_bounds__(256)
+k_step3(const Params3<T> p, const T *__restrict__ src, T *__restrict__ dst)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+    const long long P = p.plane;
+    T f[19];
+#pragma unroll
+    for (int k = 0; k < 19; ++k) {
+        // source node x - c_k
+        const int xs = c3x(k) > 0 ? xm : (c3x(k) < 0 ? xp : x);
+        const int ys = c3y(k) > 0 ? ym : (c3y(k) < 0 ? yp : y);
+        const int zs = c3z(k) > 0 ? zm : (c3z(k) < 0 ? zp : z);
+        f[k] = __ldg(src + k * P + ((long long)zs * p.ny + ys) * p.pitch + xs);
+    }
+    T phi;
+    collide3<CONV, DIFF, T>(p, f, phi);
+    const long long own = ((long long)z * p.ny + y) * p.pitch + x;
+#pragma unroll
+    for (int k = 0; k < 19; ++k) __stcs(dst + k * P + own, f[k]);
+}
+
+template <class T, int CONV, int DIFF>
+__global__ void __launch_bounds__(256)
+k_init3(const Params3<T> p, const void *__restrict__ phi_in, int in_prec, T *__restrict__ dst)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long in = ((long long)z * p.ny + y) * p.nx + x;
+    const T phi0 = in_prec == LBM_F64 ? T(((const double *)phi_in)[in]) : T(((const float *)phi_in)[in]);
+    // fbar = feq(phi0) - R_k/2 (Eq. 40, 33): build feq and the source populations
+    // as the collision does, with j = B - B' R / 2 so that G vanishes, then collide
+    T f[19];
+    {
+        const T phi = phi0;
+        T Bx, By, Bz, bpx, bpy, bpz, cphi;
+        if (CONV == 0) {
+            Bx = p.ux * phi; By = p.uy * phi; Bz = p.uz * phi;
+            bpx = p.ux; bpy = p.uy; bpz = p.uz;
+            cphi = phi;
+        } else {
+            const T h = T(0.5) * phi * phi;
+            Bx = p.ux * h; By = p.uy * h; Bz = p.uz * h;
+            bpx = p.ux * phi; bpy = p.uy * phi; bpz = p.uz * phi;
+            cphi = phi * phi * phi * T(1.0 / 3.0);
+        }
+        T g;
+        if (DIFF == 0) g = phi;
+        else if (DIFF == 1) g = phi + T(0.5) * phi * phi;
+        else g = phi + phi * phi * phi * T(1.0 / 3.0);
+        const T diag = (g - phi) * T(1.0 / 3.0);
+        const T Qxx = p.ux * p.ux * cphi + diag, Qyy = p.uy * p.uy * cphi + diag, Qzz = p.uz * p.uz * cphi + diag;
+        const T Qxy = p.ux * p.uy * cphi, Qxz = p.ux * p.uz * cphi, Qyz = p.uy * p.uz * cphi;
+        const T tr3 = (Qxx + Qyy + Qzz) * T(1.0 / 3.0);
+        T R = T(0);
+        if (p.has_src) R = p.r1 * phi + p.r0;
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+            const T cx_ = T(c3x(k)), cy_ = T(c3y(k)), cz_ = T(c3z(k));
+            const T cB = cx_ * Bx + cy_ * By + cz_ * Bz;
+            const T cQc = cx_ * cx_ * Qxx + cy_ * cy_ * Qyy + cz_ * cz_ * Qzz +
+                          T(2) * (cx_ * cy_ * Qxy + cx_ * cz_ * Qxz + cy_ * cz_ * Qyz);
+            const T Rk = w3<T>(k) * (T(1) + T(3) * (cx_ * bpx + cy_ * bpy + cz_ * bpz)) * R;
+            f[k] = w3<T>(k) * (phi + T(3) * cB + T(4.5) * (cQc - tr3)) - T(0.5) * Rk;
+        }
+    }
+    T phi;
+    collide3<CONV, DIFF, T>(p, f, phi);
+    const long long own = ((long long)z * p.ny + y) * p.pitch + x;
+#pragma unroll
+    for (int k = 0; k < 19; ++k) dst[k * p.plane + own] = f[k];
+}
+
+// phi(t_n) = (sum fbar* - r0/2) / (1 + r1/2) into an FP64 or FP32 field
+template <class T>
+__global__ void __launch_bounds__(256)
+k_get_phi3(const Params3<T> p, const T *__restrict__ f, void *__restrict__ out, int out_prec)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long own = ((long long)z * p.ny + y) * p.pitch + x;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 19; ++k) s += f[k * p.plane + own];
+    const double v = (double)((s - p.half_r0) * p.inv_post);
+    const long long o = ((long long)z * p.ny + y) * p.nx + x;
+    if (out_prec == LBM_F64) ((double *)out)[o] = v;
+    else ((float *)out)[o] = (float)v;
+}
+
+}  // namespace lbm
+
+struct lbm3_solver {
+    lbm3_desc d;
+    lbm3_coeffs c;
+    int coeffs_set = 0, phi_set = 0;
+    long long pitch = 0, plane = 0;
+    size_t esize = 0;
+    void *pop[2] = {nullptr, nullptr};
+    double *staging = nullptr;
+    double *partials = nullptr;
+    int cur = 0;
+    double G[6] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace lbm {
+namespace {
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int check_desc3(const lbm3_desc *d)
+{
+    if (!d) return fail(LBM_EINVAL, "null lbm3_desc");
+    if (d->nx < 2 || d->ny < 2 || d->nz < 2) return fail(LBM_EINVAL, "nx, ny and nz must be >= 2");
+    if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) return fail(LBM_EINVAL, "grid larger than 2^31 nodes");
+    if (d->prec != LBM_F64 && d->prec != LBM_F32) return fail(LBM_EINVAL, "D3Q19 storage is LBM_F64 or LBM_F32");
+    const int b = d->block_rows;
+    if (!(b == 0 || b == 1 || b == 2 || b == 4 || b == 8)) return fail(LBM_EINVAL, "block_rows must be 0, 1, 2, 4 or 8");
+    if (d->ny > 65535 * 8 || d->nz > 65535) return fail(LBM_EINVAL, "ny or nz exceeds the launch grid");
+    return LBM_OK;
+}
+
+struct Layout3 {
+    long long pitch, plane;
+    size_t esize, pop_bytes, off_stage, off_part, total;
+};
+
+Layout3 layout3(const lbm3_desc *d)
+{
+    Layout3 L;
+    L.pitch = ((long long)d->nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+    L.plane = L.pitch * d->ny * d->nz;
+    L.esize = d->prec == LBM_F64 ? 8 : 4;
+    L.pop_bytes = up256(19 * (size_t)L.plane * L.esize);
+    L.off_stage = 2 * L.pop_bytes;
+    L.off_part = L.off_stage + up256((size_t)d->nx * d->ny * d->nz * 8);
+    L.total = L.off_part + up256((size_t)kReduceBlocks * 8 * sizeof(double));
+    return L;
+}
+
+// Eq. 26 in 3-D: A = (K / (d c_s^2) + I/2)^-1 (Cholesky test of K, adjugate inverse)
+bool relax_block3(const double K[6], double A[6])
+{
+    const double kxx = K[0], kxy = K[1], kxz = K[2], kyy = K[3], kyz = K[4], kzz = K[5];
+    const double m1 = kxx, m2 = kxx * kyy - kxy * kxy;
+    const double m3 = kxx * (kyy * kzz - kyz * kyz) - kxy * (kxy * kzz - kyz * kxz) + kxz * (kxy * kyz - kyy * kxz);
+    if (!(m1 > 0.0 && m2 > 0.0 && m3 > 0.0)) return false;
+    const double a = 3 * kxx + 0.5, b = 3 * kxy, c = 3 * kxz, d = 3 * kyy + 0.5, e = 3 * kyz, f = 3 * kzz + 0.5;
+    const double det = a * (d * f - e * e) - b * (b * f - e * c) + c * (b * e - d * c);
+    A[0] = (d * f - e * e) / det;    // xx
+    A[1] = (c * e - b * f) / det;    // xy
+    A[2] = (b * e - c * d) / det;    // xz
+    A[3] = (a * f - c * c) / det;    // yy
+    A[4] = (b * c - a * e) / det;    // yz
+    A[5] = (a * d - b * b) / det;    // zz
+    return true;
+}
+
+template <class T>
+Params3<T> params3(const lbm3_solver *s)
+{
+    Params3<T> p;
+    p.nx = s->d.nx; p.ny = s->d.ny; p.nz = s->d.nz;
+    p.pitch = s->pitch; p.plane = s->plane;
+    p.se = (T)s->c.se;
+    p.hse = (T)(1.0 - 0.5 * s->c.se);
+    for (int i = 0; i < 6; ++i) p.G[i] = (T)s->G[i];
+    p.ux = (T)s->c.u[0]; p.uy = (T)s->c.u[1]; p.uz = (T)s->c.u[2];
+    p.r0 = (T)s->c.r0; p.r1 = (T)s->c.r1;
+    p.half_r0 = (T)(0.5 * s->c.r0);
+    p.inv_den = (T)(1.0 / (1.0 - 0.5 * s->c.r1));
+    p.inv_post = (T)(1.0 / (1.0 + 0.5 * s->c.r1));
+    p.has_src = s->c.r0 != 0.0 || s->c.r1 != 0.0;
+    return p;
+}
+
+dim3 block3(const lbm3_solver *s) { return dim3(32, s->d.block_rows > 0 ? s->d.block_rows : 8); }
+dim3 grid3(const lbm3_solver *s)
+{
+    const dim3 b = block3(s);
+    return dim3((s->d.nx + 31) / 32, (s->d.ny + b.y - 1) / b.y, s->d.nz);
+}
+
+template <class T, int CONV, int DIFF>
+cudaError_t launch3_t(const lbm3_solver *s, const void *phi0, int in_prec, cudaStream_t st)
+{
+    const Params3<T> p = params3<T>(s);
+    if (phi0) k_init3<T, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, phi0, in_prec, (T *)s->pop[s->cur]);
+    else k_step3<T, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, (const T *)s->pop[s->cur], (T *)s->pop[s->cur ^ 1]);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch3_p(const lbm3_solver *s, const void *phi0, int in_prec, cudaStream_t st)
+{
+    switch (s->c.conv * 3 + s->c.diff) {
+    case 0: return launch3_t<T, 0, 0>(s, phi0, in_prec, st);
+    case 1: return launch3_t<T, 0, 1>(s, phi0, in_prec, st);
+    case 2: return launch3_t<T, 0, 2>(s, phi0, in_prec, st);
+    case 3: return launch3_t<T, 1, 0>(s, phi0, in_prec, st);
+    case 4: return launch3_t<T, 1, 1>(s, phi0, in_prec, st);
+    case 5: return launch3_t<T, 1, 2>(s, phi0, in_prec, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch3(const lbm3_solver *s, const void *phi0, int in_prec, cudaStream_t st)
+{
+    return s->d.prec == LBM_F64 ? launch3_p<double>(s, phi0, in_prec, st) : launch3_p<float>(s, phi0, in_prec, st);
+}
+
+cudaError_t get_phi3(const lbm3_solver *s, void *out, int out_prec, cudaStream_t st)
+{
+    if (s->d.prec == LBM_F64)
+        k_get_phi3<double><<<grid3(s), block3(s), 0, st>>>(params3<double>(s), (const double *)s->pop[s->cur], out,
+                                                           out_prec);
+    else
+        k_get_phi3<float><<<grid3(s), block3(s), 0, st>>>(params3<float>(s), (const float *)s->pop[s->cur], out,
+                                                         out_prec);
+    return cudaGetLastError();
+}
+
+int ready3(lbm3_handle h)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    if (!h->coeffs_set) return fail(LBM_EINVAL, "lbm3_set_coeffs has not been called");
+    return LBM_OK;
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+int lbm3_workspace_size(const lbm3_desc *desc, size_t *bytes)
+{
+    if (int rc = check_desc3(desc)) return rc;
+    if (!bytes) return fail(LBM_EINVAL, "null size pointer");
+    *bytes = layout3(desc).total;
+    return LBM_OK;
+}
+
+int lbm3_create(lbm3_handle *h, const lbm3_desc *desc, void *dev_workspace, size_t bytes)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle pointer");
+    *h = nullptr;
+    if (int rc = check_desc3(desc)) return rc;
+    const Layout3 L = layout3(desc);
+    if (!dev_workspace || ((uintptr_t)dev_workspace & 255) != 0)
+        return fail(LBM_EINVAL, "workspace null or not 256-byte aligned");
+    if (bytes < L.total) return fail(LBM_EINVAL, "workspace smaller than lbm3_workspace_size");
+    lbm3_solver *s = new (std::nothrow) lbm3_solver();
+    if (!s) return fail(LBM_EINVAL, "out of host memory");
+    char *ws = (char *)dev_workspace;
+    s->d = *desc;
+    s->pitch = L.pitch;
+    s->plane = L.plane;
+    s->esize = L.esize;
+    s->pop[0] = ws;
+    s->pop[1] = ws + L.pop_bytes;
+    s->staging = (double *)(ws + L.off_stage);
+    s->partials = (double *)(ws + L.off_part);
+    *h = s;
+    return LBM_OK;
+}
+
+int lbm3_destroy(lbm3_handle h)
+{
+    delete h;
+    return LBM_OK;
+}
+
+int lbm3_set_coeffs(lbm3_handle h, const lbm3_coeffs *c)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    if (!c) return fail(LBM_EINVAL, "null lbm3_coeffs");
+    if (c->conv != 0 && c->conv != 1) return fail(LBM_EINVAL, "conv must be 0 or 1");
+    if (c->diff < 0 || c->diff > 2) return fail(LBM_EINVAL, "diff must be 0, 1 or 2");
+    if (!(c->se > 0.0 && c->se < 2.0)) return fail(LBM_EINVAL, "s_e must lie in (0, 2)");
+    if (!(c->s0 >= 0.0 && c->s0 < 2.0)) return fail(LBM_EINVAL, "s0 must lie in [0, 2)");
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(c->u[i])) return fail(LBM_EINVAL, "non-finite coefficient");
+    if (!isfinite(c->r0) || !isfinite(c->r1) || !(c->r1 > -2.0 && c->r1 < 2.0))
+        return fail(LBM_EINVAL, "source coefficients must be finite with |r1| < 2");
+    double A[6];
+    if (!relax_block3(c->K, A)) return fail(LBM_EINVAL, "K is not symmetric positive definite");
+    h->c = *c;
+    // G = A - s_e I
+    h->G[0] = A[0] - c->se; h->G[1] = A[1]; h->G[2] = A[2];
+    h->G[3] = A[3] - c->se; h->G[4] = A[4]; h->G[5] = A[5] - c->se;
+    h->coeffs_set = 1;
+    return LBM_OK;
+}
+
+int lbm3_set_phi(lbm3_handle h, const void *dev_phi, int prec, void *stream)
+{
+    if (int rc = ready3(h)) return rc;
+    if (!dev_phi) return fail(LBM_EINVAL, "null phi");
+    if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "phi must be LBM_F64 or LBM_F32");
+    if (int rc = cuda_check(launch3(h, dev_phi, prec, (cudaStream_t)stream), "lbm3_set_phi")) return rc;
+    h->phi_set = 1;
+    return LBM_OK;
+}
+
+int lbm3_step(lbm3_handle h, int nsteps, void *stream)
+{
+    if (int rc = ready3(h)) return rc;
+    if (!h->phi_set) return fail(LBM_EINVAL, "lbm3_set_phi has not been called");
+    if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
+    for (int i = 0; i < nsteps; ++i) {
+        if (int rc = cuda_check(launch3(h, nullptr, 0, (cudaStream_t)stream), "lbm3_step")) return rc;
+        h->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+int lbm3_get_phi(lbm3_handle h, void *dev_out, int prec, void *stream)
+{
+    if (int rc = ready3(h)) return rc;
+    if (!h->phi_set) return fail(LBM_EINVAL, "lbm3_set_phi has not been called");
+    if (!dev_out) return fail(LBM_EINVAL, "null output");
+    if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "output must be LBM_F64 or LBM_F32");
+    return cuda_check(get_phi3(h, dev_out, prec, (cudaStream_t)stream), "lbm3_get_phi");
+}
+
+int lbm3_reduce(lbm3_handle h, const double *dev_ref, double *dev_out, void *stream)
+{
+    if (int rc = ready3(h)) return rc;
+    if (!h->phi_set) return fail(LBM_EINVAL, "lbm3_set_phi has not been called");
+    if (!dev_out) return fail(LBM_EINVAL, "null output");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(get_phi3(h, h->staging, LBM_F64, st), "lbm3_reduce")) return rc;
+    const long long n = (long long)h->d.nx * h->d.ny * h->d.nz;
+    return cuda_check(launch_reduce_field(h->staging, n, dev_ref, h->partials, dev_out, st), "lbm3_reduce");
+}
+
+}  // extern "C"

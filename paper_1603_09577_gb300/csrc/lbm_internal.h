@@ -85,6 +85,10 @@ cudaError_t launch_step_v4(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_get_phi(const lbm_solver *s, void *out, int out_prec, cudaStream_t st);
 cudaError_t launch_reduce(const lbm_solver *s, const double *ref, double *out, cudaStream_t st);
 cudaError_t launch_kfield(const lbm_solver *s, const double *K, cudaStream_t st);
+// the eight deterministic FP64 statistics of a plain FP64 field (partials:
+// kReduceBlocks * 8 doubles)
+cudaError_t launch_reduce_field(const double *field, long long n, const double *ref, double *partials, double *out,
+                                cudaStream_t st);
 
 int adjoint_blocks(const lbm_solver *s);
 cudaError_t launch_adjoint_begin(const lbm_solver *s, const void *dphi, int in_prec, void *lam, cudaStream_t st);

@@ -17,7 +17,7 @@ def declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        names |= set(re.findall(r"^\s*(?:int|const char \*|void)\s*\**\s*(lbm_\w+)\s*\(", txt, flags=re.M))
+        names |= set(re.findall(r"^\s*(?:int|const char \*|void)\s*\**\s*(lbm3?_\w+)\s*\(", txt, flags=re.M))
     return sorted(names)
 
 
@@ -213,3 +213,36 @@ def test_tensor_diffusion_coefficients():
     h, ws = make(desc(steps_per_pass=2))
     assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=3, Dm=[1.0, 0.0, 1.0]))) == C.LBM_EUNSUPPORTED
     L.lbm_destroy(h)
+
+
+def test_d3q19_descriptions_and_coefficients():
+    L = C.lib()
+
+    def d3(**kw):
+        d = C.Desc3()
+        d.nx, d.ny, d.nz, d.prec = 12, 10, 8, C.LBM_F32
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+
+    n = ctypes.c_size_t()
+    assert L.lbm3_workspace_size(ctypes.byref(d3()), ctypes.byref(n)) == 0
+    assert n.value >= 2 * 19 * 10 * 8 * 64 * 4
+    for bad in (dict(nz=1), dict(prec=C.LBM_BF16S), dict(block_rows=3)):
+        assert L.lbm3_workspace_size(ctypes.byref(d3(**bad)), ctypes.byref(n)) == C.LBM_EINVAL
+    d = d3()
+    L.lbm3_workspace_size(ctypes.byref(d), ctypes.byref(n))
+    ws = FakeWorkspace(n.value)
+    h = ctypes.c_void_p()
+    assert L.lbm3_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(ws.ptr), n.value) == 0
+    c = C.Coeffs3()
+    c.K[:] = [0.02, 0.004, 0.002, 0.015, 0.003, 0.01]
+    c.se, c.s0 = 1.1, 1.0
+    assert L.lbm3_set_coeffs(h, ctypes.byref(c)) == 0
+    c.K[:] = [0.02, 0.03, 0.0, 0.015, 0.0, 0.01]            # not positive definite
+    assert L.lbm3_set_coeffs(h, ctypes.byref(c)) == C.LBM_EINVAL
+    c.K[:] = [0.02, 0.0, 0.0, 0.02, 0.0, 0.02]
+    c.se = 2.0
+    assert L.lbm3_set_coeffs(h, ctypes.byref(c)) == C.LBM_EINVAL
+    assert L.lbm3_step(h, 1, None) == C.LBM_EINVAL           # no initial phi
+    L.lbm3_destroy(h)
