@@ -525,8 +525,10 @@ def run_gaussian3d(args):
         Km = torch.tensor([[K[0], K[1], K[2]], [K[1], K[3], K[4]], [K[2], K[4], K[5]]], dtype=torch.float64)
         Sig = sig ** 2 * torch.eye(3, dtype=torch.float64) + 2 * Km * t
         Si = torch.linalg.inv(Sig).cuda()
-        d = torch.stack([X - n / 2 - u[0] * t, Y - n / 2 - u[1] * t, Z - n / 2 - u[2] * t])
-        q = torch.einsum("a...,ab,b...->...", d, Si, d)
+        dx, dy, dz = X - n / 2 - u[0] * t, Y - n / 2 - u[1] * t, Z - n / 2 - u[2] * t
+        S = Si.cpu().tolist()
+        q = (S[0][0] * dx * dx + S[1][1] * dy * dy + S[2][2] * dz * dz
+             + 2 * (S[0][1] * dx * dy + S[0][2] * dx * dz + S[1][2] * dy * dz))
         return (sig ** 3 / math.sqrt(float(torch.linalg.det(Sig)))) * torch.exp(-0.5 * q)
 
     phi0 = hill(0.0).to(torch.float64 if prec == "f64" else torch.float32).contiguous()
