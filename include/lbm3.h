@@ -71,6 +71,10 @@ int lbm3_get_phi(lbm3_handle h, void *dev_out, int prec, void *stream);
 /* The eight FP64 statistics of lbm_reduce over phi(t_n) (dev_ref: nx*ny*nz
    doubles or NULL; dev_out: 8 doubles on the device); deterministic. */
 int lbm3_reduce(lbm3_handle h, const double *dev_ref, double *dev_out, void *stream);
+/* Index-fault word of the bounds-checked build (see lbm_debug_flags): 0 when
+   every neighbour coordinate stayed in range since lbm3_set_phi; always 0 in
+   the release build. Synchronises `stream`. */
+int lbm3_debug_flags(lbm3_handle h, int *flags, void *stream);
 
 #ifdef __cplusplus
 }

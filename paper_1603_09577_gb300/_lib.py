@@ -91,6 +91,7 @@ SIGNATURES = {
     "lbm3_step": [_VP, _I, _VP],
     "lbm3_get_phi": [_VP, _VP, _I, _VP],
     "lbm3_reduce": [_VP, _VP, _VP, _VP],
+    "lbm3_debug_flags": [_VP, ctypes.POINTER(_I), _VP],
     "lbm_ensemble_workspace_size": [_I, _VP, _VP, ctypes.POINTER(_SZ)],
     "lbm_ensemble_create": [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, _SZ],
     "lbm_ensemble_destroy": [_VP],

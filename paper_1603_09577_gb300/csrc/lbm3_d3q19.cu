@@ -49,6 +49,7 @@ struct Params3 {
     C ux, uy, uz;
     C r0, r1, half_r0, inv_den, inv_post;
     int has_src;
+    int *err;                        // checked builds: index-fault word
 };
 
 template <int CONV, int DIFF, class C>
@@ -114,9 +115,15 @@ k_step3(const Params3<T> p, const T *__restrict__ src, T *__restrict__ dst)
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
-    const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+    int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+    int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+    int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+    LBM_CHK(xm, p.nx, p.err, kErrX);
+    LBM_CHK(xp, p.nx, p.err, kErrX);
+    LBM_CHK(ym, p.ny, p.err, kErrY);
+    LBM_CHK(yp, p.ny, p.err, kErrY);
+    LBM_CHK(zm, p.nz, p.err, kErrIndex);
+    LBM_CHK(zp, p.nz, p.err, kErrIndex);
     const long long P = p.plane;
     T f[19];
 #pragma unroll
@@ -217,6 +224,7 @@ struct lbm3_solver {
     void *pop[2] = {nullptr, nullptr};
     double *staging = nullptr;
     double *partials = nullptr;
+    int *err = nullptr;
     int cur = 0;
     double G[6] = {0, 0, 0, 0, 0, 0};
 };
@@ -240,7 +248,7 @@ int check_desc3(const lbm3_desc *d)
 
 struct Layout3 {
     long long pitch, plane;
-    size_t esize, pop_bytes, off_stage, off_part, total;
+    size_t esize, pop_bytes, off_stage, off_part, off_err, total;
 };
 
 Layout3 layout3(const lbm3_desc *d)
@@ -252,7 +260,8 @@ Layout3 layout3(const lbm3_desc *d)
     L.pop_bytes = up256(19 * (size_t)L.plane * L.esize);
     L.off_stage = 2 * L.pop_bytes;
     L.off_part = L.off_stage + up256((size_t)d->nx * d->ny * d->nz * 8);
-    L.total = L.off_part + up256((size_t)kReduceBlocks * 8 * sizeof(double));
+    L.off_err = L.off_part + up256((size_t)kReduceBlocks * 8 * sizeof(double));
+    L.total = L.off_err + 256;
     return L;
 }
 
@@ -289,6 +298,7 @@ Params3<T> params3(const lbm3_solver *s)
     p.inv_den = (T)(1.0 / (1.0 - 0.5 * s->c.r1));
     p.inv_post = (T)(1.0 / (1.0 + 0.5 * s->c.r1));
     p.has_src = s->c.r0 != 0.0 || s->c.r1 != 0.0;
+    p.err = s->err;
     return p;
 }
 
@@ -380,6 +390,7 @@ int lbm3_create(lbm3_handle *h, const lbm3_desc *desc, void *dev_workspace, size
     s->pop[1] = ws + L.pop_bytes;
     s->staging = (double *)(ws + L.off_stage);
     s->partials = (double *)(ws + L.off_part);
+    s->err = (int *)(ws + L.off_err);
     *h = s;
     return LBM_OK;
 }
@@ -417,6 +428,7 @@ int lbm3_set_phi(lbm3_handle h, const void *dev_phi, int prec, void *stream)
     if (int rc = ready3(h)) return rc;
     if (!dev_phi) return fail(LBM_EINVAL, "null phi");
     if (prec != LBM_F64 && prec != LBM_F32) return fail(LBM_EINVAL, "phi must be LBM_F64 or LBM_F32");
+    if (int rc = cuda_check(cudaMemsetAsync(h->err, 0, sizeof(int), (cudaStream_t)stream), "lbm3_set_phi")) return rc;
     if (int rc = cuda_check(launch3(h, dev_phi, prec, (cudaStream_t)stream), "lbm3_set_phi")) return rc;
     h->phi_set = 1;
     return LBM_OK;
@@ -452,6 +464,16 @@ int lbm3_reduce(lbm3_handle h, const double *dev_ref, double *dev_out, void *str
     if (int rc = cuda_check(get_phi3(h, h->staging, LBM_F64, st), "lbm3_reduce")) return rc;
     const long long n = (long long)h->d.nx * h->d.ny * h->d.nz;
     return cuda_check(launch_reduce_field(h->staging, n, dev_ref, h->partials, dev_out, st), "lbm3_reduce");
+}
+
+int lbm3_debug_flags(lbm3_handle h, int *flags, void *stream)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    if (!flags) return fail(LBM_EINVAL, "null flags pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(cudaMemcpyAsync(flags, h->err, sizeof(int), cudaMemcpyDeviceToHost, st), "lbm3_debug_flags"))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(st), "lbm3_debug_flags sync");
 }
 
 }  // extern "C"
