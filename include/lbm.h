@@ -275,6 +275,11 @@ int lbm_ensemble_set_phi(lbm_ensemble e, const void *dev_phi, int prec, void *st
    launch runs the two-step shared-memory tile routine on 30 x 30 tiles of all
    instances (two steps per sweep through HBM). Set before capturing a graph. */
 int lbm_ensemble_configure(lbm_ensemble e, int steps_per_pass);
+/* Grid of the two-step launches: persistent = 0 (default) launches one block
+   per 30 x 30 tile of the union tile list (all instances in one launch, the
+   hardware scheduler balancing the blocks); persistent = 1 launches SMs x
+   resident blocks that walk the list. Set before capturing a graph. */
+int lbm_ensemble_set_persistent(lbm_ensemble e, int persistent);
 /* nsteps time steps; mode 0: persistent launches over all tiles (two steps per
    launch when configured, an odd remainder with one); mode 1: one launch per
    instance per step (one-step arithmetic, for comparison). */

@@ -238,6 +238,15 @@ int lbm_ensemble_configure(lbm_ensemble e, int steps_per_pass)
     return LBM_OK;
 }
 
+int lbm_ensemble_set_persistent(lbm_ensemble e, int persistent)
+{
+    if (!e) return fail(LBM_EINVAL, "null ensemble");
+    if (persistent != 0 && persistent != 1) return fail(LBM_EINVAL, "persistent must be 0 or 1");
+    if (e->exec) return fail(LBM_EINVAL, "choose the grid before capturing a graph");
+    e->persistent2 = persistent;
+    return LBM_OK;
+}
+
 int lbm_ensemble_capture(lbm_ensemble e, int nsteps, void *stream)
 {
     if (!e) return fail(LBM_EINVAL, "null ensemble");

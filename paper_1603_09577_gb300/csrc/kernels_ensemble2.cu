@@ -1,7 +1,8 @@
 // kernels_ensemble2.cu -- the ensemble with two time steps per sweep through
-// HBM: one persistent launch walks a list of 30 x 30 output tiles of every
-// instance and runs the shared-memory two-step tile routine of the single-grid
-// kernel on each (FP32 storage, periodic walls, constant K per instance).
+// HBM: one launch covers the list of 30 x 30 output tiles of every instance and
+// runs the shared-memory two-step tile routine of the single-grid kernel on
+// each (FP32 storage, periodic walls, constant K per instance). By default one
+// block per tile; in persistent mode SMs x resident blocks walk the list.
 #include "kernels_step2.cuh"
 #include "lbm_ensemble.h"
 
@@ -31,13 +32,14 @@ constexpr size_t kEns2Smem = 9 * Tile2<30>::kRP * sizeof(float);
 cudaError_t ens_launch_step2(const lbm_ensemble_s *e, cudaStream_t st)
 {
     dim3 block(32, kT2Threads / 32);
+    const int grid = e->persistent2 ? e->grid2 : e->ntiles2;
     switch (e->family) {
-    case 0: k_ens_step2<0, 0><<<e->grid2, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
-    case 1: k_ens_step2<0, 1><<<e->grid2, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
-    case 2: k_ens_step2<0, 2><<<e->grid2, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
-    case 3: k_ens_step2<1, 0><<<e->grid2, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
-    case 4: k_ens_step2<1, 1><<<e->grid2, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
-    case 5: k_ens_step2<1, 2><<<e->grid2, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
+    case 0: k_ens_step2<0, 0><<<grid, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
+    case 1: k_ens_step2<0, 1><<<grid, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
+    case 2: k_ens_step2<0, 2><<<grid, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
+    case 3: k_ens_step2<1, 0><<<grid, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
+    case 4: k_ens_step2<1, 1><<<grid, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
+    case 5: k_ens_step2<1, 2><<<grid, block, kEns2Smem, st>>>(e->d_inst, e->d_tiles2, e->ntiles2, e->parity); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -44,6 +44,7 @@ struct lbm_ensemble_s {
     int count = 0, family = 0, ntiles = 0, grid = 0, parity = 0;
     int spp = 1;                    // time steps per persistent launch (1 or 2)
     int ntiles2 = 0, grid2 = 0;     // 30 x 30 tiles of the two-step kernel
+    int persistent2 = 0;            // 1: the two-step launch walks the list with grid2 blocks
     int4 *d_tiles2 = nullptr;
     lbm::EnsInst *d_inst = nullptr;
     int4 *d_tiles = nullptr;

@@ -68,6 +68,11 @@ def test_ensemble_two_steps_per_pass_matches_oracle(steps):
     e.set_phi(e.pack(phis))
     e.step(60)
     assert torch.equal(e2.phi().cpu(), e.phi().cpu())
+    # the persistent grid walking the tile list computes the same state bit for bit
+    e3 = Ensemble(inst, steps_per_pass=2, persistent=True)
+    e3.set_phi(e3.pack(phis))
+    e3.step(60)
+    assert torch.equal(e3.phi().cpu(), e.phi().cpu())
 
 
 def test_ensemble_modes_agree_bitwise():
