@@ -278,9 +278,11 @@ int lbm_ensemble_configure(lbm_ensemble e, int steps_per_pass);
 /* Grid of the two-step launches: persistent = 0 (default) launches one block
    per 30 x 30 tile of the union tile list (all instances in one launch, the
    hardware scheduler balancing the blocks); persistent = 1 launches SMs x
-   resident blocks that walk the list. Set before capturing a graph. */
+   resident blocks that walk the list. One-step launches always use the
+   persistent grid over their 32 x 8 tiles (faster for tiles that small). Set
+   before capturing a graph. */
 int lbm_ensemble_set_persistent(lbm_ensemble e, int persistent);
-/* nsteps time steps; mode 0: persistent launches over all tiles (two steps per
+/* nsteps time steps; mode 0: one launch over all tiles per step (two steps per
    launch when configured, an odd remainder with one); mode 1: one launch per
    instance per step (one-step arithmetic, for comparison). */
 int lbm_ensemble_step(lbm_ensemble e, int nsteps, int mode, void *stream);

@@ -79,12 +79,12 @@ def test_ensemble_modes_agree_bitwise():
     inst = small_instances()
     packed = None
     outs = []
-    for mode in ("persistent", "per_instance", "graph"):
-        e = Ensemble(inst)
+    for mode in ("one_launch", "per_instance", "graph", "persistent_grid"):
+        e = Ensemble(inst, persistent=mode == "persistent_grid")
         if packed is None:
             packed = e.pack([W.ensemble_phi0(d) for d in inst])
         e.set_phi(packed)
-        if mode == "persistent":
+        if mode in ("one_launch", "persistent_grid"):
             e.step(40)
         elif mode == "per_instance":
             e.step(40, mode=1)
@@ -97,7 +97,7 @@ def test_ensemble_modes_agree_bitwise():
                     e.replay()
             torch.cuda.current_stream().wait_stream(s)
         outs.append(e.phi().cpu())
-    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    assert all(torch.equal(outs[0], o) for o in outs[1:])
 
 
 @pytest.mark.parametrize("spp", [1, 2])
