@@ -93,10 +93,12 @@ typedef struct {
                                warp marches are 16 * block_rows (0: 64); for the
                                two-step tile kernel 4 selects 30 x 30 tiles,
                                other values 30 x 62                               */
-    int scheme;             /* LBM_SCHEME_B (0) or LBM_SCHEME_A. Scheme A, LBM_NEE
-                               and the flux family conv 2 run the general
-                               one-node-per-thread kernel: LBM_F64 or LBM_F32,
-                               steps_per_pass 1, kernel_variant 0 or 1            */
+    int scheme;             /* LBM_SCHEME_B (0) or LBM_SCHEME_A. Scheme A, LBM_NEE,
+                               conv 2 / 3 and diff 3 run the general kernels:
+                               one node per thread (LBM_F64 or LBM_F32,
+                               steps_per_pass 1, kernel_variant 0 or 1), or two
+                               steps per pass on 30 x 30 tiles (LBM_F32,
+                               kernel_variant 0, constant K, not conv 3 / cfree) */
 } lbm_desc;
 
 /* Coefficient families of Eq. 1 (Sec. 2.1), source and relaxation rates. */

@@ -78,7 +78,9 @@ static int check_desc(const lbm_desc *d)
         return fail(LBM_EINVAL, "extrapolation needs >= 3 nodes on its axis and a periodic or extrapolated other axis");
     if (d->scheme == LBM_SCHEME_A || d->bc_x == LBM_NEE || d->bc_y == LBM_NEE) {
         if (d->prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "Scheme A and extrapolation are built for LBM_F64 and LBM_F32");
-        if (d->steps_per_pass != 1) return fail(LBM_EUNSUPPORTED, "Scheme A and extrapolation run one step per pass");
+        if (d->steps_per_pass == 2 && (d->prec != LBM_F32 || d->kernel_variant != 0 || d->per_cell_K))
+            return fail(LBM_EUNSUPPORTED,
+                        "two steps per pass with Scheme A or extrapolation: LBM_F32, kernel_variant 0, constant K");
         if (d->kernel_variant > 1) return fail(LBM_EUNSUPPORTED, "Scheme A and extrapolation run kernel_variant 0 or 1");
     }
     for (int i = 0; i < 4; ++i)
@@ -260,18 +262,26 @@ int lbm_set_coeffs(lbm_handle h, const lbm_coeffs *c)
         if (h->d.scheme != LBM_SCHEME_A) return fail(LBM_EINVAL, "the Fisher source needs Scheme A (Eq. 35 has no closed form)");
         if (c->r0 != 0.0 || c->r1 != 0.0) return fail(LBM_EINVAL, "src_family 1 takes b; r0 and r1 must be 0");
     }
+    // the general kernels: one step per pass (kernel_variant 0 or 1), or two
+    // (FP32, kernel_variant 0, constant K, not the C-free variant)
+    const bool general2_ok = h->d.prec == LBM_F32 && h->d.kernel_variant == 0 && !h->d.per_cell_K && !c->cfree &&
+                             c->conv <= 2;
     if (c->conv >= 2) {
         if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "conv 2 and 3 are built for LBM_F64 and LBM_F32");
-        if (h->d.steps_per_pass != 1 || h->d.kernel_variant > 1)
-            return fail(LBM_EUNSUPPORTED, "conv 2 and 3 run one step per pass with kernel_variant 0 or 1");
+        if (h->d.steps_per_pass == 1 ? h->d.kernel_variant > 1 : !general2_ok)
+            return fail(LBM_EUNSUPPORTED, "conv 2 and 3: one step per pass with kernel_variant 0 or 1, or conv 2 "
+                                          "with two steps per pass (LBM_F32, kernel_variant 0, constant K)");
     }
+    if ((c->cfree || c->src_family == 1) && h->d.steps_per_pass == 2 && !general2_ok)
+        return fail(LBM_EUNSUPPORTED, "the C-free variant runs one step per pass");
     if (c->diff < 0 || c->diff > 3) return fail(LBM_EINVAL, "diff must be 0, 1, 2 or 3");
     if (c->diff == 3) {
         if (!isfinite(c->Dm[0]) || !isfinite(c->Dm[1]) || !isfinite(c->Dm[2]))
             return fail(LBM_EINVAL, "non-finite diffusion tensor Dm");
         if (h->d.prec == LBM_BF16S) return fail(LBM_EUNSUPPORTED, "diff 3 is built for LBM_F64 and LBM_F32");
-        if (h->d.steps_per_pass != 1 || h->d.kernel_variant > 1)
-            return fail(LBM_EUNSUPPORTED, "diff 3 runs one step per pass with kernel_variant 0 or 1");
+        if (h->d.steps_per_pass == 1 ? h->d.kernel_variant > 1 : !general2_ok)
+            return fail(LBM_EUNSUPPORTED, "diff 3: one step per pass with kernel_variant 0 or 1, or two steps per "
+                                          "pass with LBM_F32, kernel_variant 0 and constant K");
     }
     for (int i = 0; i < 9; ++i) {
         if (i == 3 || i == 5) continue;
@@ -344,14 +354,25 @@ int lbm_step(lbm_handle h, int nsteps, void *stream)
         const bool nee = h->d.bc_x == LBM_NEE || h->d.bc_y == LBM_NEE;
         if (nee && !h->dir_vals) return fail(LBM_EINVAL, "lbm_set_dirichlet has not been called");
         const size_t rec = 2 * ((size_t)h->d.nx + h->d.ny);
-        for (; done < nsteps; ++done) {
-            const double *bv = nullptr;
-            if (nee) {
-                long long j = h->t - h->dir_t0;
-                j = j < 0 ? 0 : (j >= h->dir_nrec ? h->dir_nrec - 1 : j);
-                bv = h->dir_vals + (size_t)j * rec;
+        // record of the step that produces time level t + 1
+        auto record = [&](long long t) -> const double * {
+            if (!nee) return nullptr;
+            long long j = t - h->dir_t0;
+            j = j < 0 ? 0 : (j >= h->dir_nrec ? h->dir_nrec - 1 : j);
+            return h->dir_vals + (size_t)j * rec;
+        };
+        if (h->d.steps_per_pass == 2) {
+            for (; done + 2 <= nsteps; done += 2) {
+                if (int rc = cuda_check(launch_step2_general(h, h->cur, record(h->t), record(h->t + 1), st),
+                                        "lbm_step (general, two steps per pass)"))
+                    return rc;
+                h->cur ^= 1;
+                h->t += 2;
             }
-            if (int rc = cuda_check(launch_general(h, h->cur, bv, nullptr, 0, st), "lbm_step (general)")) return rc;
+        }
+        for (; done < nsteps; ++done) {
+            if (int rc = cuda_check(launch_general(h, h->cur, record(h->t), nullptr, 0, st), "lbm_step (general)"))
+                return rc;
             h->cur ^= 1;
             h->t += 1;
         }

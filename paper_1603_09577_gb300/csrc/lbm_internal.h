@@ -79,6 +79,8 @@ cudaError_t launch_general_f64(const lbm_solver *s, int src, const double *bv, c
                                cudaStream_t st);
 cudaError_t launch_general_f32(const lbm_solver *s, int src, const double *bv, const void *phi0, int in_prec,
                                cudaStream_t st);
+// two general steps per pass (FP32): records of the two time levels it produces
+cudaError_t launch_step2_general(const lbm_solver *s, int src, const double *bvA, const double *bvB, cudaStream_t st);
 bool step_v4_supported(const lbm_solver *s);
 bool step_v4_preferred(const lbm_solver *s);
 cudaError_t launch_step_v4(const lbm_solver *s, int src, cudaStream_t st);

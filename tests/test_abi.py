@@ -155,7 +155,8 @@ def test_per_cell_field_required():
     (dict(bc_x=C.LBM_NEE, nx=2), C.LBM_EINVAL),                    # no inward neighbour
     (dict(scheme=2), C.LBM_EINVAL),
     (dict(scheme=C.LBM_SCHEME_A, prec=C.LBM_BF16S), C.LBM_EUNSUPPORTED),
-    (dict(bc_y=C.LBM_NEE, steps_per_pass=2), C.LBM_EUNSUPPORTED),
+    (dict(bc_y=C.LBM_NEE, steps_per_pass=2, per_cell_K=1), C.LBM_EUNSUPPORTED),
+    (dict(scheme=C.LBM_SCHEME_A, steps_per_pass=2, prec=C.LBM_BF16S), C.LBM_EUNSUPPORTED),
     (dict(scheme=C.LBM_SCHEME_A, kernel_variant=2), C.LBM_EUNSUPPORTED)])
 def test_general_path_descriptions(bad, code):
     rc, _ = ws_size(desc(**bad))
@@ -210,8 +211,16 @@ def test_tensor_diffusion_coefficients():
     assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=4))) == C.LBM_EINVAL
     assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=3, Dm=[float("inf"), 0.0, 1.0]))) == C.LBM_EINVAL
     L.lbm_destroy(h)
-    h, ws = make(desc(steps_per_pass=2))
+    h, ws = make(desc(steps_per_pass=2))                       # the general two-step kernel
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=3, Dm=[1.0, 0.0, 1.0]))) == 0
+    L.lbm_destroy(h)
+    h, ws = make(desc(steps_per_pass=2, kernel_variant=3))     # the column march has no general form
     assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(diff=3, Dm=[1.0, 0.0, 1.0]))) == C.LBM_EUNSUPPORTED
+    L.lbm_destroy(h)
+    h, ws = make(desc(steps_per_pass=2, scheme=C.LBM_SCHEME_A))
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=2, power=1, src_family=1, b=0.1))) == 0
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=3, cfree=1))) == C.LBM_EUNSUPPORTED
+    assert L.lbm_set_coeffs(h, ctypes.byref(coeffs(conv=1, cfree=1))) == C.LBM_EUNSUPPORTED
     L.lbm_destroy(h)
 
 

@@ -249,3 +249,55 @@ def test_sec36_stability_comparison(prec):
     bgk.step(g["steps"])
     r = bgk.reduce()
     assert r["nonfinite"] > 0 or r["max_abs"] > 1e3
+
+
+# ---- two steps per pass on the general path ----------------------------------------
+G2_CASES = [(67, 41, (2, 2)), (61, 31, (2, 2)), (40, 33, (2, 0)), (35, 91, (0, 2)), (64, 24, (0, 0)),
+            (52, 19, (1, 1)), (20, 17, (2, 2)), (3, 5, (2, 2)), (97, 130, (1, 0))]
+G2_COEFS = [n for n in COEFS if not COEFS[n].get("cfree", 0)]
+
+
+@pytest.mark.parametrize("scheme", ["A", "B"])
+@pytest.mark.parametrize("name", G2_COEFS)
+@pytest.mark.parametrize("case", G2_CASES, ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}" for c in G2_CASES])
+def test_general_two_steps_per_pass(scheme, name, case):
+    """The general two-step tile kernel (FP32) against the oracle, 50 and 51
+    steps (an odd count ends with one general step); grids with a one-node last
+    tile (61 = 2 x 30 + 1) exercise the shifted last tile on extrapolated axes."""
+    coef = COEFS[name]
+    if scheme == "B" and coef.get("src_family", 0) == 1:
+        pytest.skip("the Fisher source needs Scheme A")
+    nx, ny, bc = case
+    rng = np.random.default_rng(nx * 7 + ny)
+    phi0 = W.jacobi_smooth(rng.uniform(0.1, 0.9, (ny, nx)), 2)
+    for steps in (50, 51):
+        bv = records(nx, ny, steps, nx + ny) if 2 in bc else None
+        sp = O.Spec(nx=nx, ny=ny, bc_x=bc[0], bc_y=bc[1], phi_wall=(0.2, 0.6, 0.1, 0.4), s=W.s9(),
+                    scheme=1 if scheme == "A" else 0, **coef)
+        ref = oracle_run(sp, phi0, steps, bv)
+        s = Solver(nx, ny, prec="f32", bc=(BCN[bc[0]], BCN[bc[1]]), phi_wall=(0.2, 0.6, 0.1, 0.4), scheme=scheme,
+                   steps_per_pass=2)
+        s.set_coeffs(s=W.s9(), **coef)
+        if bv is not None:
+            s.set_dirichlet(torch.from_numpy(bv).cuda())
+        s.set_phi(torch.from_numpy(np.ascontiguousarray(phi0)).cuda())
+        s.step(steps)
+        got = s.phi().cpu().numpy()
+        assert rel(got, ref) <= 1e-5, (steps, rel(got, ref))
+
+
+def test_burgers_fisher_two_steps_per_pass():
+    """The Burgers-Fisher workload (301^2, 4000 steps) with two steps per pass
+    against the oracle and Eq. 47."""
+    bf = W.burgers_fisher(300, 1.0)
+    coef = dict(conv=2, power=1, u=bf["u"], diff=0, K=(bf["K"], 0.0, bf["K"]), src_family=1, b=bf["b"])
+    sp = O.Spec(nx=bf["nx"], ny=bf["ny"], bc_x=2, bc_y=2, s=W.s9(), scheme=1, **coef)
+    ref = oracle_run(sp, bf["phi0"], bf["steps"], bf["bvals"])
+    s = Solver(bf["nx"], bf["ny"], prec="f32", bc=("nee", "nee"), scheme="A", steps_per_pass=2)
+    s.set_coeffs(s=W.s9(), **coef)
+    s.set_dirichlet(torch.from_numpy(bf["bvals"]).cuda())
+    s.set_phi(torch.from_numpy(bf["phi0"]).cuda())
+    s.step(bf["steps"])
+    got = s.phi().cpu().numpy()
+    assert rel(got, ref) <= 1e-5, rel(got, ref)
+    assert gre(got, bf["exact"]) < 5e-4
