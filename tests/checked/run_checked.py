@@ -52,15 +52,17 @@ def main():
             out["max_rel"] = max(out["max_rel"], float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
                                  if prec != "bf16s" else 0.0)
     # general path: Scheme A, power-law flux, Fisher source, extrapolated walls
-    for nx, ny, bc in [(37, 29, (2, 2)), (40, 26, (2, 0)), (33, 41, (0, 2)), (3, 5, (2, 2)), (35, 22, (1, 0))]:
+    for nx, ny, bc in [(37, 29, (2, 2)), (40, 26, (2, 0)), (33, 41, (0, 2)), (3, 5, (2, 2)), (35, 22, (1, 0)),
+                       (61, 31, (2, 2))]:
         phi0 = W.phi0_aniso(nx, seed=nx * ny, ny=ny)
         rng = np.random.default_rng(nx)
         bv = rng.uniform(0.3, 0.7, (10, 2 * (nx + ny))) if 2 in bc else None
         gcoef = dict(conv=2, power=1, u=(0.06, -0.03), diff=1, K=(0.02, 0.008, 0.01), src_family=1, b=0.02)
         ref = O.run_x(O.Spec(nx=nx, ny=ny, bc_x=bc[0], bc_y=bc[1], phi_wall=(0.1, 0.2, 0.3, 0.4), s=W.s9(),
                              scheme=1, **gcoef), phi0, 10, bv)
-        for prec in ("f64", "f32"):
-            s = Solver(nx, ny, prec=prec, bc=(BCN[bc[0]], BCN[bc[1]]), phi_wall=(0.1, 0.2, 0.3, 0.4), scheme="A")
+        for prec, spp in (("f64", 1), ("f32", 1), ("f32", 2)):
+            s = Solver(nx, ny, prec=prec, bc=(BCN[bc[0]], BCN[bc[1]]), phi_wall=(0.1, 0.2, 0.3, 0.4), scheme="A",
+                       steps_per_pass=spp)
             s.set_coeffs(s=W.s9(), **gcoef)
             if bv is not None:
                 s.set_dirichlet(torch.from_numpy(bv).cuda())
