@@ -189,8 +189,10 @@ def test_general_path_argument_errors():
         Solver(20, 20, prec="f32", bc=("nee", "abb"))
     with pytest.raises(LBMError):                      # BF16S storage
         Solver(20, 20, prec="bf16s", scheme="A")
-    with pytest.raises(LBMError):                      # two steps per pass
-        Solver(20, 20, prec="f32", bc=("nee", "nee"), steps_per_pass=2)
+    with pytest.raises(LBMError):                      # two steps per pass: FP32 only
+        Solver(20, 20, prec="f64", bc=("nee", "nee"), steps_per_pass=2)
+    with pytest.raises(LBMError):                      # two steps per pass: constant K only
+        Solver(20, 20, prec="f32", bc=("nee", "nee"), steps_per_pass=2, per_cell_K=True)
     with pytest.raises(LBMError):                      # Fisher source with Scheme B
         Solver(20, 20, prec="f32").set_coeffs(conv=0, K=(0.02, 0, 0.02), src_family=1, b=0.1, power=1)
     s = Solver(20, 20, prec="f32", bc=("nee", "periodic")).set_coeffs(conv=0, K=(0.02, 0, 0.02))
