@@ -128,6 +128,33 @@ class Solver:
         C.check(self.lib.lbm_step(self.h, int(n), _stream(stream)))
         return self
 
+    # -- CUDA graphs -------------------------------------------------------------
+    def capture(self, nsteps: int):
+        """Record nsteps time steps into a CUDA graph; replay() relaunches them,
+        advancing the state by nsteps each time. The recorded launches must be
+        even in number (nsteps even with one step per pass, a multiple of 4 with
+        two), so that every replay ends on the buffer it started from. One step
+        is run first and undone (save / load) so that kernel attributes are set
+        outside the capture. Extrapolated walls replay the Dirichlet records of
+        the recorded steps."""
+        spp = int(self.desc.steps_per_pass)
+        launches = nsteps // spp + nsteps % spp
+        if nsteps < 1 or launches % 2:
+            raise ValueError("capture needs an even number of launches")
+        snap = self.save()
+        self.step(spp)
+        self.load(snap)
+        torch.cuda.current_stream().synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            C.check(self.lib.lbm_step(self.h, int(nsteps), _stream()))
+        self._graph, self._graph_steps = g, int(nsteps)
+        return self
+
+    def replay(self):
+        self._graph.replay()
+        return self
+
     # -- read-out ------------------------------------------------------------
     def phi(self, dtype=torch.float64, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         if out is None:

@@ -303,3 +303,29 @@ def test_burgers_fisher_two_steps_per_pass():
     got = s.phi().cpu().numpy()
     assert rel(got, ref) <= 1e-5, rel(got, ref)
     assert gre(got, bf["exact"]) < 5e-4
+
+
+
+@pytest.mark.parametrize("spp", [1, 2])
+def test_general_path_replays_from_a_cuda_graph(spp):
+    """Solver.capture / replay on the general path (Scheme A, extrapolated walls
+    with one constant record, Fisher source): three replays of 20 recorded steps
+    equal 60 direct steps bit for bit."""
+    nx, ny = 70, 45
+    rng = np.random.default_rng(12)
+    phi0 = torch.from_numpy(W.jacobi_smooth(rng.uniform(0.2, 0.8, (ny, nx)), 2)).cuda()
+    bv = torch.from_numpy(rng.uniform(0.3, 0.7, (1, 2 * (nx + ny)))).cuda()
+    coef = COEFS["power1-fisher"]
+    s = Solver(nx, ny, prec="f32", bc=("nee", "nee"), scheme="A", steps_per_pass=spp).set_coeffs(s=W.s9(), **coef)
+    s.set_dirichlet(bv)
+    s.set_phi(phi0)
+    s.capture(20)
+    for _ in range(3):
+        s.replay()
+    torch.cuda.synchronize()
+    replayed = s.phi().cpu()
+    d = Solver(nx, ny, prec="f32", bc=("nee", "nee"), scheme="A", steps_per_pass=spp).set_coeffs(s=W.s9(), **coef)
+    d.set_dirichlet(bv)
+    d.set_phi(phi0)
+    d.step(60)
+    assert torch.equal(replayed, d.phi().cpu())
