@@ -231,9 +231,16 @@ def run_ensemble(args):
     persistent launch per step replayed from a CUDA graph, against one launch
     per instance per step."""
     import torch
+    import torch.distributed as dist
 
-    from paper_1603_09577_gb300.ensemble import Ensemble
-    inst = W.ensemble(count=args.ens_count)
+    from paper_1603_09577_gb300.ensemble import Ensemble, shard
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    all_inst = W.ensemble(count=args.ens_count)
+    # independent instances: each rank runs its share, no exchange on the data path
+    inst = [all_inst[i] for i in shard(all_inst, rank, world)] if world > 1 else all_inst
     e = Ensemble(inst, steps_per_pass=args.ens_spp)
     packed = e.pack([W.ensemble_phi0(d) for d in inst], dtype=torch.float32)
     side = torch.cuda.Stream()
@@ -267,8 +274,10 @@ def run_ensemble(args):
 
         for _ in range(args.warmup):
             job_graph()
+        if world > 1:
+            dist.barrier()
         clk = clocks_sampler()
-        ms_graph = timed(job_graph, args.steps, side)
+        ms_graph = max_over_ranks(timed(job_graph, args.steps, side), device="cuda")
         clocks = clocks_summary(clk)
         ms_pers = timed(job_persistent, max(1, args.steps // 2), side)
         ep = Ensemble(inst, steps_per_pass=args.ens_spp, persistent=True)
@@ -283,26 +292,36 @@ def run_ensemble(args):
         ms_pgrid = timed(job_graph_persistent_grid, max(1, args.steps // 2), side)
         ms_sep = timed(job_launches, max(1, args.steps // 2), side)
         ms_g1 = timed(job_graph_one_step, max(1, args.steps // 2), side)
-    nodes = e.nodes
+    nodes = sum(d["nx"] * d["ny"] for d in all_inst)         # every rank's instances
     val = nodes * steps / (ms_graph / 1e3) / 1e6
+    if world > 1:
+        dist.destroy_process_group()
+        if rank != 0:
+            return
+        # the comparison timings below are the rank-0 share's
+        nodes_r0 = e.nodes
+    else:
+        nodes_r0 = nodes
     peak, src = measured_peak()
-    achieved = 72.0 * nodes * (steps // args.ens_spp) / (ms_graph / 1e3) / 1e9
-    out = {"metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+    achieved = 72.0 * nodes_r0 * (steps // args.ens_spp) / (ms_graph / 1e3) / 1e9
+    out = {"metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
+           "scaling": "strong" if world > 1 else "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"ensemble_256: 256 D2Q9 MRT instances, sides 64..1024 ({nodes} nodes), "
-                                  f"D(phi)=D0(1+phi), {steps} steps per job", "instances": len(inst),
-                      "tiles": e.tiles, "persistent_grid_blocks": e.grid},
+                                  f"D(phi)=D0(1+phi), {steps} steps per job", "instances": len(all_inst),
+                      "instances_rank0": len(inst), "tiles_rank0": e.tiles, "persistent_grid_blocks": e.grid,
+                      "parallelism": f"instances sharded over {world} ranks" if world > 1 else "single GPU"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak,
                         "kernel": ("k_ens_step2 (one block per tile of all instances, two steps per launch, "
                                    "graph-replayed)" if args.ens_spp == 2 else "k_ens_step (persistent, graph-replayed)"),
                         "peak_source": src},
            "steps_per_launch": args.ens_spp,
-           "one_step_graph_mlups": nodes * steps / (ms_g1 / 1e3) / 1e6,
-           "persistent_grid_graph_mlups": nodes * steps / (ms_pgrid / 1e3) / 1e6,
-           "persistent_no_graph_mlups": nodes * steps / (ms_pers / 1e3) / 1e6,
-           "one_launch_per_instance_mlups": nodes * steps / (ms_sep / 1e3) / 1e6,
+           "one_step_graph_mlups": nodes_r0 * steps / (ms_g1 / 1e3) / 1e6,
+           "persistent_grid_graph_mlups": nodes_r0 * steps / (ms_pgrid / 1e3) / 1e6,
+           "persistent_no_graph_mlups": nodes_r0 * steps / (ms_pers / 1e3) / 1e6,
+           "one_launch_per_instance_mlups": nodes_r0 * steps / (ms_sep / 1e3) / 1e6,
            "graph_speedup_vs_per_instance": ms_sep / ms_graph,
            "gpu_launches": args.steps * (1 + steps // args.ens_spp)}
     if clocks is not None:

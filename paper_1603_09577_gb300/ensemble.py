@@ -83,3 +83,22 @@ class Ensemble:
         out = torch.empty(self.nodes, dtype=dtype, device=self.device)
         C.check(self.lib.lbm_ensemble_get_phi(self.h, _ptr(out), _prec_of(out), _stream(stream)))
         return out
+
+
+def shard(instances, rank: int, world: int) -> list[int]:
+    """Indices of the instances that rank `rank` of `world` runs when an ensemble
+    is split across GPUs (instances are independent: no exchange between ranks).
+    Largest instances first, each to the rank with the fewest nodes so far, so
+    every rank gets nearly the same number of node updates per step; the result
+    is deterministic and the ranks' lists partition range(len(instances))."""
+    if not 0 <= rank < world:
+        raise ValueError("rank out of range")
+    order = sorted(range(len(instances)), key=lambda i: (-instances[i]["nx"] * instances[i]["ny"], i))
+    load = [0] * world
+    mine = []
+    for i in order:
+        r = min(range(world), key=lambda j: (load[j], j))
+        load[r] += instances[i]["nx"] * instances[i]["ny"]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
