@@ -36,7 +36,9 @@ typedef struct lbm3_solver *lbm3_handle;
 
 typedef struct {
     int nx, ny, nz;         /* nodes per axis, each >= 2                          */
-    int prec;               /* LBM_F64 or LBM_F32                                 */
+    int prec;               /* LBM_F64, LBM_F32 or LBM_BF16S (bf16 deviations
+                               g_k = fbar*_k - w_k phi plus an FP32 shift plane
+                               h = M* - sum_k g_k, float arithmetic, as in lbm.h) */
     int block_rows;         /* rows of 32-thread warps per block: 0 (= 8), 1, 2,
                                4 or 8                                             */
 } lbm3_desc;

@@ -13,6 +13,8 @@
 #include <new>
 #include <string>
 
+#include <cuda_bf16.h>
+
 #include "lbm3.h"
 #include "lbm_internal.h"
 
@@ -39,6 +41,52 @@ __host__ __device__ constexpr C w3(int k)
 {
     return k == 0 ? C(1) / C(3) : (k <= 6 ? C(1) / C(18) : C(1) / C(36));
 }
+
+// Storage of the 19 planes: FP64, FP32, or BF16 deviations g_k = f*_k - w_k phi
+// plus an FP32 shift plane h = M* - sum_k g_k (as for D2Q9: the stored node
+// sums to its post-collision mass up to FP32 rounding).
+template <int PREC> struct St3;
+template <> struct St3<LBM_F64> {
+    using T = double;
+    using C = double;
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
+    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C)
+    {
+#pragma unroll
+        for (int k = 0; k < 19; ++k) __stcs(f + k * P + i, v[k]);
+    }
+};
+template <> struct St3<LBM_F32> {
+    using T = float;
+    using C = float;
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
+    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C)
+    {
+#pragma unroll
+        for (int k = 0; k < 19; ++k) __stcs(f + k * P + i, v[k]);
+    }
+};
+template <> struct St3<LBM_BF16S> {
+    using T = __nv_bfloat16;
+    using C = float;
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *__restrict__ h, C w)
+    {
+        return fmaf(w, __ldg(h + i), __bfloat162float(f[i]));
+    }
+    __device__ static __forceinline__ void store(T *__restrict__ f, float *__restrict__ h, long long P, long long i,
+                                                 const C v[19], C phi)
+    {
+        C mass = C(0), gsum = C(0);
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+            const T g = __float2bfloat16_rn(fmaf(-w3<float>(k), phi, v[k]));
+            mass += v[k];
+            gsum += __bfloat162float(g);
+            f[k * P + i] = g;
+        }
+        h[i] = mass - gsum;
+    }
+};
 
 template <class C>
 struct Params3 {
@@ -107,10 +155,13 @@ __device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_ou
     }
 }
 
-template <class T, int CONV, int DIFF>
+template <int PREC, int CONV, int DIFF>
 __global__ void __launch_bounds__(256)
-k_step3(const Params3<T> p, const T *__restrict__ src, T *__restrict__ dst)
+k_step3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__restrict__ src,
+        const float *__restrict__ src_h, typename St3<PREC>::T *__restrict__ dst, float *__restrict__ dst_h)
 {
+    using S = St3<PREC>;
+    using T = typename S::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -132,19 +183,21 @@ k_step3(const Params3<T> p, const T *__restrict__ src, T *__restrict__ dst)
         const int xs = c3x(k) > 0 ? xm : (c3x(k) < 0 ? xp : x);
         const int ys = c3y(k) > 0 ? ym : (c3y(k) < 0 ? yp : y);
         const int zs = c3z(k) > 0 ? zm : (c3z(k) < 0 ? zp : z);
-        f[k] = __ldg(src + k * P + ((long long)zs * p.ny + ys) * p.pitch + xs);
+        f[k] = S::ld(src + k * P, ((long long)zs * p.ny + ys) * p.pitch + xs, src_h, w3<T>(k));
     }
     T phi;
     collide3<CONV, DIFF, T>(p, f, phi);
     const long long own = ((long long)z * p.ny + y) * p.pitch + x;
-#pragma unroll
-    for (int k = 0; k < 19; ++k) __stcs(dst + k * P + own, f[k]);
+    S::store(dst, dst_h, P, own, f, phi);
 }
 
-template <class T, int CONV, int DIFF>
+template <int PREC, int CONV, int DIFF>
 __global__ void __launch_bounds__(256)
-k_init3(const Params3<T> p, const void *__restrict__ phi_in, int in_prec, T *__restrict__ dst)
+k_init3(const Params3<typename St3<PREC>::C> p, const void *__restrict__ phi_in, int in_prec,
+        typename St3<PREC>::T *__restrict__ dst, float *__restrict__ dst_h)
 {
+    using S = St3<PREC>;
+    using T = typename S::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -190,15 +243,17 @@ k_init3(const Params3<T> p, const void *__restrict__ phi_in, int in_prec, T *__r
     T phi;
     collide3<CONV, DIFF, T>(p, f, phi);
     const long long own = ((long long)z * p.ny + y) * p.pitch + x;
-#pragma unroll
-    for (int k = 0; k < 19; ++k) dst[k * p.plane + own] = f[k];
+    S::store(dst, dst_h, p.plane, own, f, phi);
 }
 
 // phi(t_n) = (sum fbar* - r0/2) / (1 + r1/2) into an FP64 or FP32 field
-template <class T>
+template <int PREC>
 __global__ void __launch_bounds__(256)
-k_get_phi3(const Params3<T> p, const T *__restrict__ f, void *__restrict__ out, int out_prec)
+k_get_phi3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__restrict__ f,
+           const float *__restrict__ h, void *__restrict__ out, int out_prec)
 {
+    using S = St3<PREC>;
+    using T = typename S::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -206,7 +261,7 @@ k_get_phi3(const Params3<T> p, const T *__restrict__ f, void *__restrict__ out, 
     const long long own = ((long long)z * p.ny + y) * p.pitch + x;
     T s = T(0);
 #pragma unroll
-    for (int k = 0; k < 19; ++k) s += f[k * p.plane + own];
+    for (int k = 0; k < 19; ++k) s += S::ld(f + k * p.plane, own, h, w3<T>(k));
     const double v = (double)((s - p.half_r0) * p.inv_post);
     const long long o = ((long long)z * p.ny + y) * p.nx + x;
     if (out_prec == LBM_F64) ((double *)out)[o] = v;
@@ -222,6 +277,7 @@ struct lbm3_solver {
     long long pitch = 0, plane = 0;
     size_t esize = 0;
     void *pop[2] = {nullptr, nullptr};
+    float *hpl[2] = {nullptr, nullptr};   // BF16S shift planes
     double *staging = nullptr;
     double *partials = nullptr;
     int *err = nullptr;
@@ -239,7 +295,8 @@ int check_desc3(const lbm3_desc *d)
     if (!d) return fail(LBM_EINVAL, "null lbm3_desc");
     if (d->nx < 2 || d->ny < 2 || d->nz < 2) return fail(LBM_EINVAL, "nx, ny and nz must be >= 2");
     if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) return fail(LBM_EINVAL, "grid larger than 2^31 nodes");
-    if (d->prec != LBM_F64 && d->prec != LBM_F32) return fail(LBM_EINVAL, "D3Q19 storage is LBM_F64 or LBM_F32");
+    if (d->prec != LBM_F64 && d->prec != LBM_F32 && d->prec != LBM_BF16S)
+        return fail(LBM_EINVAL, "D3Q19 storage is LBM_F64, LBM_F32 or LBM_BF16S");
     const int b = d->block_rows;
     if (!(b == 0 || b == 1 || b == 2 || b == 4 || b == 8)) return fail(LBM_EINVAL, "block_rows must be 0, 1, 2, 4 or 8");
     if (d->ny > 65535 * 8 || d->nz > 65535) return fail(LBM_EINVAL, "ny or nz exceeds the launch grid");
@@ -248,7 +305,7 @@ int check_desc3(const lbm3_desc *d)
 
 struct Layout3 {
     long long pitch, plane;
-    size_t esize, pop_bytes, off_stage, off_part, off_err, total;
+    size_t esize, pop_bytes, h_bytes, off_stage, off_part, off_err, total;
 };
 
 Layout3 layout3(const lbm3_desc *d)
@@ -256,9 +313,10 @@ Layout3 layout3(const lbm3_desc *d)
     Layout3 L;
     L.pitch = ((long long)d->nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
     L.plane = L.pitch * d->ny * d->nz;
-    L.esize = d->prec == LBM_F64 ? 8 : 4;
+    L.esize = d->prec == LBM_F64 ? 8 : (d->prec == LBM_F32 ? 4 : 2);
     L.pop_bytes = up256(19 * (size_t)L.plane * L.esize);
-    L.off_stage = 2 * L.pop_bytes;
+    L.h_bytes = d->prec == LBM_BF16S ? up256((size_t)L.plane * 4) : 0;
+    L.off_stage = 2 * (L.pop_bytes + L.h_bytes);
     L.off_part = L.off_stage + up256((size_t)d->nx * d->ny * d->nz * 8);
     L.off_err = L.off_part + up256((size_t)kReduceBlocks * 8 * sizeof(double));
     L.total = L.off_err + 256;
@@ -309,43 +367,60 @@ dim3 grid3(const lbm3_solver *s)
     return dim3((s->d.nx + 31) / 32, (s->d.ny + b.y - 1) / b.y, s->d.nz);
 }
 
-template <class T, int CONV, int DIFF>
+template <int PREC, int CONV, int DIFF>
 cudaError_t launch3_t(const lbm3_solver *s, const void *phi0, int in_prec, cudaStream_t st)
 {
-    const Params3<T> p = params3<T>(s);
-    if (phi0) k_init3<T, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, phi0, in_prec, (T *)s->pop[s->cur]);
-    else k_step3<T, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, (const T *)s->pop[s->cur], (T *)s->pop[s->cur ^ 1]);
+    using T = typename St3<PREC>::T;
+    const auto p = params3<typename St3<PREC>::C>(s);
+    if (phi0)
+        k_init3<PREC, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, phi0, in_prec, (T *)s->pop[s->cur], s->hpl[s->cur]);
+    else
+        k_step3<PREC, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, (const T *)s->pop[s->cur], s->hpl[s->cur],
+                                                                  (T *)s->pop[s->cur ^ 1], s->hpl[s->cur ^ 1]);
     return cudaGetLastError();
 }
 
-template <class T>
+template <int PREC>
 cudaError_t launch3_p(const lbm3_solver *s, const void *phi0, int in_prec, cudaStream_t st)
 {
     switch (s->c.conv * 3 + s->c.diff) {
-    case 0: return launch3_t<T, 0, 0>(s, phi0, in_prec, st);
-    case 1: return launch3_t<T, 0, 1>(s, phi0, in_prec, st);
-    case 2: return launch3_t<T, 0, 2>(s, phi0, in_prec, st);
-    case 3: return launch3_t<T, 1, 0>(s, phi0, in_prec, st);
-    case 4: return launch3_t<T, 1, 1>(s, phi0, in_prec, st);
-    case 5: return launch3_t<T, 1, 2>(s, phi0, in_prec, st);
+    case 0: return launch3_t<PREC, 0, 0>(s, phi0, in_prec, st);
+    case 1: return launch3_t<PREC, 0, 1>(s, phi0, in_prec, st);
+    case 2: return launch3_t<PREC, 0, 2>(s, phi0, in_prec, st);
+    case 3: return launch3_t<PREC, 1, 0>(s, phi0, in_prec, st);
+    case 4: return launch3_t<PREC, 1, 1>(s, phi0, in_prec, st);
+    case 5: return launch3_t<PREC, 1, 2>(s, phi0, in_prec, st);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch3(const lbm3_solver *s, const void *phi0, int in_prec, cudaStream_t st)
 {
-    return s->d.prec == LBM_F64 ? launch3_p<double>(s, phi0, in_prec, st) : launch3_p<float>(s, phi0, in_prec, st);
+    switch (s->d.prec) {
+    case LBM_F64: return launch3_p<LBM_F64>(s, phi0, in_prec, st);
+    case LBM_F32: return launch3_p<LBM_F32>(s, phi0, in_prec, st);
+    case LBM_BF16S: return launch3_p<LBM_BF16S>(s, phi0, in_prec, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int PREC>
+cudaError_t get_phi3_p(const lbm3_solver *s, void *out, int out_prec, cudaStream_t st)
+{
+    using T = typename St3<PREC>::T;
+    k_get_phi3<PREC><<<grid3(s), block3(s), 0, st>>>(params3<typename St3<PREC>::C>(s), (const T *)s->pop[s->cur],
+                                                     s->hpl[s->cur], out, out_prec);
+    return cudaGetLastError();
 }
 
 cudaError_t get_phi3(const lbm3_solver *s, void *out, int out_prec, cudaStream_t st)
 {
-    if (s->d.prec == LBM_F64)
-        k_get_phi3<double><<<grid3(s), block3(s), 0, st>>>(params3<double>(s), (const double *)s->pop[s->cur], out,
-                                                           out_prec);
-    else
-        k_get_phi3<float><<<grid3(s), block3(s), 0, st>>>(params3<float>(s), (const float *)s->pop[s->cur], out,
-                                                         out_prec);
-    return cudaGetLastError();
+    switch (s->d.prec) {
+    case LBM_F64: return get_phi3_p<LBM_F64>(s, out, out_prec, st);
+    case LBM_F32: return get_phi3_p<LBM_F32>(s, out, out_prec, st);
+    case LBM_BF16S: return get_phi3_p<LBM_BF16S>(s, out, out_prec, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 int ready3(lbm3_handle h)
@@ -387,7 +462,11 @@ int lbm3_create(lbm3_handle *h, const lbm3_desc *desc, void *dev_workspace, size
     s->plane = L.plane;
     s->esize = L.esize;
     s->pop[0] = ws;
-    s->pop[1] = ws + L.pop_bytes;
+    s->pop[1] = ws + L.pop_bytes + L.h_bytes;
+    if (L.h_bytes) {
+        s->hpl[0] = (float *)(ws + L.pop_bytes);
+        s->hpl[1] = (float *)(ws + 2 * L.pop_bytes + L.h_bytes);
+    }
     s->staging = (double *)(ws + L.off_stage);
     s->partials = (double *)(ws + L.off_part);
     s->err = (int *)(ws + L.off_err);

@@ -237,7 +237,8 @@ def test_d3q19_descriptions_and_coefficients():
     n = ctypes.c_size_t()
     assert L.lbm3_workspace_size(ctypes.byref(d3()), ctypes.byref(n)) == 0
     assert n.value >= 2 * 19 * 10 * 8 * 64 * 4
-    for bad in (dict(nz=1), dict(prec=C.LBM_BF16S), dict(block_rows=3)):
+    assert L.lbm3_workspace_size(ctypes.byref(d3(prec=C.LBM_BF16S)), ctypes.byref(n)) == 0
+    for bad in (dict(nz=1), dict(prec=7), dict(block_rows=3)):
         assert L.lbm3_workspace_size(ctypes.byref(d3(**bad)), ctypes.byref(n)) == C.LBM_EINVAL
     d = d3()
     L.lbm3_workspace_size(ctypes.byref(d), ctypes.byref(n))
