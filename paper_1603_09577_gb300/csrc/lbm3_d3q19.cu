@@ -100,6 +100,50 @@ struct Params3 {
     int *err;                        // checked builds: index-fault word
 };
 
+// Coefficients at phi (Eq. 7 families, D = g(phi) I): B, B', the tensor
+// Q = C + c_s^2 g I - c_s^2 phi I of Eq. 3 and trQ/3, and R = r0 + r1 phi.
+template <int CONV, int DIFF, class C>
+struct Coef3 {
+    C Bx, By, Bz, bpx, bpy, bpz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, tr3, R;
+    __device__ __forceinline__ Coef3(const Params3<C> &p, C phi)
+    {
+        C cphi;
+        if (CONV == 0) {
+            Bx = p.ux * phi; By = p.uy * phi; Bz = p.uz * phi;
+            bpx = p.ux; bpy = p.uy; bpz = p.uz;
+            cphi = phi;
+        } else {
+            const C h = C(0.5) * phi * phi;
+            Bx = p.ux * h; By = p.uy * h; Bz = p.uz * h;
+            bpx = p.ux * phi; bpy = p.uy * phi; bpz = p.uz * phi;
+            cphi = phi * phi * phi * C(1.0 / 3.0);
+        }
+        C g;
+        if (DIFF == 0) g = phi;
+        else if (DIFF == 1) g = phi + C(0.5) * phi * phi;
+        else g = phi + phi * phi * phi * C(1.0 / 3.0);
+        const C diag = (g - phi) * C(1.0 / 3.0);
+        Qxx = p.ux * p.ux * cphi + diag; Qyy = p.uy * p.uy * cphi + diag; Qzz = p.uz * p.uz * cphi + diag;
+        Qxy = p.ux * p.uy * cphi; Qxz = p.ux * p.uz * cphi; Qyz = p.uy * p.uz * cphi;
+        tr3 = (Qxx + Qyy + Qzz) * C(1.0 / 3.0);
+        R = p.has_src ? p.r1 * phi + p.r0 : C(0);
+    }
+    // feq_k = w_k [phi + 3 c.B + 4.5 (c Q c - trQ/3)] (Eq. 3)
+    __device__ __forceinline__ C feq(int k, C phi) const
+    {
+        const C cx_ = C(c3x(k)), cy_ = C(c3y(k)), cz_ = C(c3z(k));
+        const C cB = cx_ * Bx + cy_ * By + cz_ * Bz;
+        const C cQc = cx_ * cx_ * Qxx + cy_ * cy_ * Qyy + cz_ * cz_ * Qzz +
+                      C(2) * (cx_ * cy_ * Qxy + cx_ * cz_ * Qxz + cy_ * cz_ * Qyz);
+        return w3<C>(k) * (phi + C(3) * cB + C(4.5) * (cQc - tr3));
+    }
+    // R_k = w_k (1 + 3 c.B') R (Eq. 9, Scheme B)
+    __device__ __forceinline__ C source(int k) const
+    {
+        return w3<C>(k) * (C(1) + C(3) * (C(c3x(k)) * bpx + C(c3y(k)) * bpy + C(c3z(k)) * bpz)) * R;
+    }
+};
+
 template <int CONV, int DIFF, class C>
 __device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_out)
 {
@@ -113,44 +157,18 @@ __device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_ou
     }
     const C phi = (rho + p.half_r0) * p.inv_den;                 // Eq. 35
     phi_out = phi;
-    // B, B' and C (Eq. 7 families), g(phi)
-    C Bx, By, Bz, bpx, bpy, bpz, cphi;
-    if (CONV == 0) {
-        Bx = p.ux * phi; By = p.uy * phi; Bz = p.uz * phi;
-        bpx = p.ux; bpy = p.uy; bpz = p.uz;
-        cphi = phi;
-    } else {
-        const C h = C(0.5) * phi * phi;
-        Bx = p.ux * h; By = p.uy * h; Bz = p.uz * h;
-        bpx = p.ux * phi; bpy = p.uy * phi; bpz = p.uz * phi;
-        cphi = phi * phi * phi * C(1.0 / 3.0);
-    }
-    C g;
-    if (DIFF == 0) g = phi;
-    else if (DIFF == 1) g = phi + C(0.5) * phi * phi;
-    else g = phi + phi * phi * phi * C(1.0 / 3.0);
-    // Q = C + c_s^2 g I - c_s^2 phi I; feq_k = w_k [phi + 3 c.B + 4.5 (c Q c - trQ/3)]
-    const C diag = (g - phi) * C(1.0 / 3.0);
-    const C Qxx = p.ux * p.ux * cphi + diag, Qyy = p.uy * p.uy * cphi + diag, Qzz = p.uz * p.uz * cphi + diag;
-    const C Qxy = p.ux * p.uy * cphi, Qxz = p.ux * p.uz * cphi, Qyz = p.uy * p.uz * cphi;
-    const C tr3 = (Qxx + Qyy + Qzz) * C(1.0 / 3.0);
-    C R = C(0);
-    if (p.has_src) R = p.r1 * phi + p.r0;
+    const Coef3<CONV, DIFF, C> q(p, phi);
     // G = (A - s_e I) [(j - B) + B' R / 2]
-    const C vx = (jx - Bx) + C(0.5) * bpx * R, vy = (jy - By) + C(0.5) * bpy * R, vz = (jz - Bz) + C(0.5) * bpz * R;
+    const C vx = (jx - q.Bx) + C(0.5) * q.bpx * q.R, vy = (jy - q.By) + C(0.5) * q.bpy * q.R;
+    const C vz = (jz - q.Bz) + C(0.5) * q.bpz * q.R;
     const C Gx = (p.G[0] * vx + p.G[1] * vy + p.G[2] * vz) * C(0.1);
     const C Gy = (p.G[1] * vx + p.G[3] * vy + p.G[4] * vz) * C(0.1);
     const C Gz = (p.G[2] * vx + p.G[4] * vy + p.G[5] * vz) * C(0.1);
 #pragma unroll
     for (int k = 0; k < 19; ++k) {
-        const C cx_ = C(c3x(k)), cy_ = C(c3y(k)), cz_ = C(c3z(k));
-        const C cB = cx_ * Bx + cy_ * By + cz_ * Bz;
-        const C cQc = cx_ * cx_ * Qxx + cy_ * cy_ * Qyy + cz_ * cz_ * Qzz +
-                      C(2) * (cx_ * cy_ * Qxy + cx_ * cz_ * Qxz + cy_ * cz_ * Qyz);
-        const C fe = w3<C>(k) * (phi + C(3) * cB + C(4.5) * (cQc - tr3));
-        const C cG = cx_ * Gx + cy_ * Gy + cz_ * Gz;
-        C v = f[k] - p.se * (f[k] - fe) - cG;
-        if (p.has_src) v += p.hse * w3<C>(k) * (C(1) + C(3) * (cx_ * bpx + cy_ * bpy + cz_ * bpz)) * R;
+        const C cG = C(c3x(k)) * Gx + C(c3y(k)) * Gy + C(c3z(k)) * Gz;
+        C v = f[k] - p.se * (f[k] - q.feq(k, phi)) - cG;
+        if (p.has_src) v += p.hse * q.source(k);
         f[k] = v;
     }
 }
@@ -204,41 +222,12 @@ k_init3(const Params3<typename St3<PREC>::C> p, const void *__restrict__ phi_in,
     if (x >= p.nx || y >= p.ny) return;
     const long long in = ((long long)z * p.ny + y) * p.nx + x;
     const T phi0 = in_prec == LBM_F64 ? T(((const double *)phi_in)[in]) : T(((const float *)phi_in)[in]);
-    // fbar = feq(phi0) - R_k/2 (Eq. 40, 33): build feq and the source populations
-    // as the collision does, with j = B - B' R / 2 so that G vanishes, then collide
+    // fbar = feq(phi0) - R_k/2 (Eq. 40, 33), then one collision
     T f[19];
     {
-        const T phi = phi0;
-        T Bx, By, Bz, bpx, bpy, bpz, cphi;
-        if (CONV == 0) {
-            Bx = p.ux * phi; By = p.uy * phi; Bz = p.uz * phi;
-            bpx = p.ux; bpy = p.uy; bpz = p.uz;
-            cphi = phi;
-        } else {
-            const T h = T(0.5) * phi * phi;
-            Bx = p.ux * h; By = p.uy * h; Bz = p.uz * h;
-            bpx = p.ux * phi; bpy = p.uy * phi; bpz = p.uz * phi;
-            cphi = phi * phi * phi * T(1.0 / 3.0);
-        }
-        T g;
-        if (DIFF == 0) g = phi;
-        else if (DIFF == 1) g = phi + T(0.5) * phi * phi;
-        else g = phi + phi * phi * phi * T(1.0 / 3.0);
-        const T diag = (g - phi) * T(1.0 / 3.0);
-        const T Qxx = p.ux * p.ux * cphi + diag, Qyy = p.uy * p.uy * cphi + diag, Qzz = p.uz * p.uz * cphi + diag;
-        const T Qxy = p.ux * p.uy * cphi, Qxz = p.ux * p.uz * cphi, Qyz = p.uy * p.uz * cphi;
-        const T tr3 = (Qxx + Qyy + Qzz) * T(1.0 / 3.0);
-        T R = T(0);
-        if (p.has_src) R = p.r1 * phi + p.r0;
+        const Coef3<CONV, DIFF, T> q(p, phi0);
 #pragma unroll
-        for (int k = 0; k < 19; ++k) {
-            const T cx_ = T(c3x(k)), cy_ = T(c3y(k)), cz_ = T(c3z(k));
-            const T cB = cx_ * Bx + cy_ * By + cz_ * Bz;
-            const T cQc = cx_ * cx_ * Qxx + cy_ * cy_ * Qyy + cz_ * cz_ * Qzz +
-                          T(2) * (cx_ * cy_ * Qxy + cx_ * cz_ * Qxz + cy_ * cz_ * Qyz);
-            const T Rk = w3<T>(k) * (T(1) + T(3) * (cx_ * bpx + cy_ * bpy + cz_ * bpz)) * R;
-            f[k] = w3<T>(k) * (phi + T(3) * cB + T(4.5) * (cQc - tr3)) - T(0.5) * Rk;
-        }
+        for (int k = 0; k < 19; ++k) f[k] = q.feq(k, phi0) - T(0.5) * q.source(k);
     }
     T phi;
     collide3<CONV, DIFF, T>(p, f, phi);
