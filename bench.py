@@ -35,6 +35,11 @@ import workloads as W  # noqa: E402
 
 WORKLOAD = "aniso_dirichlet_4096"
 BYTES_PER_UPDATE = {"f32": 72, "bf16s": 44, "f64": 144}
+# FP64 path: FP64 thread instructions per node update of k_step<F64> on this workload (ncu counts: 60 DADD +
+# 36 DFMA + 22 DMUL), and the FP64 pipe's rate on GB300 (2 thread instructions per SM per clock: 152 SMs at
+# the 2070 MHz the runs hold), the ALU roof the FP64 kernel meets before HBM
+FP64_INST_PER_UPDATE = 118
+FP64_PEAK_GINST = 2 * 152 * 2.070
 KERNEL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
               for f in ("kernels_step.cu", "kernels_step_vec.cu", "kernels_step2.cuh", "kernels_step2_f32.cu",
                         "kernels_step2_bf16.cu", "lbm_device.cuh")]
@@ -755,6 +760,14 @@ def main():
             "gpu_launches": args.steps * (1 + launches_per_job + 2),
             "mass_after_job": mass,
         }
+        if args.prec == "f64":
+            # the FP64 kernel is bound by the FP64 pipe, not HBM
+            ginst = FP64_INST_PER_UPDATE * cells * launches_per_job * args.spp / (statistics.mean(step_kernels_ms) / 1e3) / 1e9
+            out["roofline"] = {"bound": "alu", "achieved": ginst, "peak": FP64_PEAK_GINST,
+                               "unit": "G FP64 thread instructions/s", "frac": ginst / FP64_PEAK_GINST, "traffic": None,
+                               "kernel": kernel, "fp64_inst_per_update": FP64_INST_PER_UPDATE,
+                               "hbm_frac": achieved / peak, "avg_launch_ms": launch_ms,
+                               "peak_source": "FP64 pipe: 2 thread instructions per SM per clock x 152 SMs x 2070 MHz"}
         if clocks is not None:
             out["clocks"] = clocks
         if world == 1 and not args.no_cpu_baseline:
