@@ -762,7 +762,7 @@ def main():
         }
         if args.prec == "f64":
             # the FP64 kernel is bound by the FP64 pipe, not HBM
-            ginst = FP64_INST_PER_UPDATE * cells * launches_per_job * args.spp / (statistics.mean(step_kernels_ms) / 1e3) / 1e9
+            ginst = FP64_INST_PER_UPDATE * cells * lbm_steps / (statistics.mean(step_kernels_ms) / 1e3) / 1e9
             out["roofline"] = {"bound": "alu", "achieved": ginst, "peak": FP64_PEAK_GINST,
                                "unit": "G FP64 thread instructions/s", "frac": ginst / FP64_PEAK_GINST, "traffic": None,
                                "kernel": kernel, "fp64_inst_per_update": FP64_INST_PER_UPDATE,
