@@ -78,7 +78,7 @@ def main():
         c3 = dict(conv=1, u=(0.05, -0.03, 0.02), diff=1, K=(0.02, 0.004, -0.003, 0.015, 0.002, 0.012), se=1.2)
         phi3 = np.random.default_rng(nx).uniform(0.2, 0.8, (nz, ny, nx))
         ref3 = D3.run(D3.Spec3(nx=nx, ny=ny, nz=nz, **c3), phi3, 6)
-        for prec in ("f64", "f32"):
+        for prec in ("f64", "f32", "bf16s"):
             s3 = Solver3(nx, ny, nz, prec=prec).set_coeffs(**c3)
             s3.set_phi(torch.from_numpy(phi3).cuda())
             s3.step(6)
@@ -86,7 +86,8 @@ def main():
             f = ctypes.c_int()
             C.check(s3.lib.lbm3_debug_flags(s3.h, ctypes.byref(f), None))
             out["faults"].append(f.value)
-            out["max_rel"] = max(out["max_rel"], float(np.linalg.norm(got - ref3) / np.linalg.norm(ref3)))
+            if prec != "bf16s":
+                out["max_rel"] = max(out["max_rel"], float(np.linalg.norm(got - ref3) / np.linalg.norm(ref3)))
     # adjoint and ensemble
     Kf, phi0, tgt = W.adjoint_inputs(36, seed=3, ny=20)
     p0 = torch.from_numpy(phi0).cuda().requires_grad_(True)
