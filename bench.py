@@ -414,7 +414,13 @@ def run_burgers_fisher(args):
     exact = torch.from_numpy(bf["exact"]).cuda()
     bv = torch.from_numpy(bf["bvals"]).cuda()
     spp = args.bf_spp if prec == "f32" else 1
-    s = Solver(n, n, prec=prec, bc=("nee", "nee"), scheme="A", steps_per_pass=spp)
+    variant, rows = 0, 0
+    if args.tune and prec == "f32" and args.bf_spp == 2:
+        from paper_1603_09577_gb300 import tune
+        cfg = tune.tune(n, n, prec, bc=("nee", "nee"), conv=2, diff=0, scheme="A")
+        spp, variant, rows = cfg["steps_per_pass"], cfg["kernel_variant"], cfg["block_rows"]
+    s = Solver(n, n, prec=prec, bc=("nee", "nee"), scheme="A", steps_per_pass=spp, kernel_variant=variant,
+               block_rows=rows)
     s.set_coeffs(conv=2, power=1, u=bf["u"], diff=0, K=(bf["K"], 0.0, bf["K"]), s=W.s9(), src_family=1, b=bf["b"])
     red = torch.zeros(8, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()

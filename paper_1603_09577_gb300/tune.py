@@ -4,8 +4,11 @@ For a problem (grid, storage precision, walls, coefficient family) it times the
 candidate configurations on the current device -- kernel variant (one node or
 four x-adjacent nodes per thread), rows per thread block, one or two time steps
 per sweep through memory (shared-memory tiles or the register column march with
-16 to 128 rows per warp) -- on a synthetic field, and keeps the fastest in
-a JSON cache keyed by device name and problem, so later runs reuse it.
+16 to 128 rows per warp, the TMA-staged tile) -- on a synthetic field, and
+keeps the fastest in a JSON cache keyed by device name and problem, so later
+runs reuse it. Problems on the general path (Scheme A, extrapolated walls, the
+power-law flux, the tensor diffusion function) choose between the general
+one-step kernel (rows per block) and the general two-step tile kernel.
 
     cfg = tune(4096, 4096, "f32", bc=("abb", "abb"), conv=0, diff=2)
     s = Solver(4096, 4096, prec="f32", bc=("abb", "abb"), **cfg)
@@ -28,9 +31,22 @@ def cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "lbm_gb300", "tune.json"))
 
 
-def _key(nx, ny, prec, bc, conv, diff, per_cell_K):
+def _key(nx, ny, prec, bc, conv, diff, per_cell_K, scheme="B"):
     dev = torch.cuda.get_device_name()
-    return f"{dev}|{nx}x{ny}|{prec}|{bc[0]},{bc[1]}|c{conv}d{diff}|K{int(per_cell_K)}"
+    return f"{dev}|{nx}x{ny}|{prec}|{bc[0]},{bc[1]}|c{conv}d{diff}|K{int(per_cell_K)}|s{scheme}"
+
+
+def _general(bc, conv, diff, scheme) -> bool:
+    return scheme == "A" or "nee" in bc or conv >= 2 or diff == 3
+
+
+def general_candidates(prec: str, per_cell_K: bool):
+    """The general kernels: one node per thread (rows per block), and for FP32
+    with constant K the two-step tile kernel."""
+    out = [dict(kernel_variant=1, block_rows=b, steps_per_pass=1) for b in (1, 2, 4, 8)]
+    if prec == "f32" and not per_cell_K:
+        out.append(dict(kernel_variant=0, block_rows=0, steps_per_pass=2))
+    return out
 
 
 def candidates(nx: int, prec: str):
@@ -46,9 +62,11 @@ def candidates(nx: int, prec: str):
     return out
 
 
-def _time(cfg, nx, ny, prec, bc, conv, diff, per_cell_K, steps, reps):
-    s = Solver(nx, ny, prec=prec, bc=bc, per_cell_K=per_cell_K, **cfg)
-    s.set_coeffs(conv=conv, u=(0.02, 0.01), diff=diff, K=(0.02, 0.004, 0.015))
+def _time(cfg, nx, ny, prec, bc, conv, diff, per_cell_K, steps, reps, scheme="B"):
+    s = Solver(nx, ny, prec=prec, bc=bc, per_cell_K=per_cell_K, scheme=scheme, **cfg)
+    s.set_coeffs(conv=conv, u=(0.02, 0.01), diff=diff, K=(0.02, 0.004, 0.015), power=1)
+    if "nee" in bc:
+        s.set_dirichlet(torch.full((1, 2 * (nx + ny)), 0.5, dtype=torch.float64, device="cuda"))
     if per_cell_K:
         K = torch.zeros((3, ny, nx), dtype=torch.float64, device="cuda")
         K[0] = 0.02
@@ -72,9 +90,11 @@ def _time(cfg, nx, ny, prec, bc, conv, diff, per_cell_K, steps, reps):
 
 
 def tune(nx: int, ny: int, prec: str = "f32", bc=("periodic", "periodic"), conv: int = 0, diff: int = 0,
-         per_cell_K: bool = False, steps: int = 20, reps: int = 3, use_cache: bool = True) -> dict:
-    """Fastest launch configuration (kwargs for Solver) for this problem."""
-    key = _key(nx, ny, prec, bc, conv, diff, per_cell_K)
+         per_cell_K: bool = False, steps: int = 20, reps: int = 3, use_cache: bool = True, scheme: str = "B") -> dict:
+    """Fastest launch configuration (kwargs for Solver) for this problem. Problems
+    on the general path (Scheme A, extrapolated walls, conv 2, diff 3) choose
+    among the general kernels."""
+    key = _key(nx, ny, prec, bc, conv, diff, per_cell_K, scheme)
     path = cache_path()
     with _lock:
         cache = {}
@@ -87,8 +107,10 @@ def tune(nx: int, ny: int, prec: str = "f32", bc=("periodic", "periodic"), conv:
         if use_cache and key in cache:
             return dict(cache[key]["config"])
         timings = []
-        for cfg in candidates(nx, prec):
-            ms = _time(cfg, nx, ny, prec, bc, conv, diff, per_cell_K, steps, reps)
+        cands = (general_candidates(prec, per_cell_K) if _general(bc, conv, diff, scheme)
+                 else candidates(nx, prec))
+        for cfg in cands:
+            ms = _time(cfg, nx, ny, prec, bc, conv, diff, per_cell_K, steps, reps, scheme)
             timings.append((ms, cfg))
         ms, best = min(timings, key=lambda t: t[0])
         cache[key] = {"config": best, "ms_per_step": ms,
