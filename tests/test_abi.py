@@ -256,3 +256,13 @@ def test_d3q19_descriptions_and_coefficients():
     assert L.lbm3_set_coeffs(h, ctypes.byref(c)) == C.LBM_EINVAL
     assert L.lbm3_step(h, 1, None) == C.LBM_EINVAL           # no initial phi
     L.lbm3_destroy(h)
+
+
+def test_grids_beyond_the_index_range_are_rejected():
+    """Node offsets are 32-bit in places: grids above 2^31 nodes are refused on the host."""
+    assert ws_size(desc(nx=65536, ny=32769))[0] == C.LBM_EINVAL
+    assert ws_size(desc(nx=46340, ny=46340))[0] == 0            # 2.147e9 nodes: the largest square that fits
+    d = C.Desc3()
+    d.nx, d.ny, d.nz, d.prec = 2048, 1024, 1025, C.LBM_F32
+    n = ctypes.c_size_t()
+    assert C.lib().lbm3_workspace_size(ctypes.byref(d), ctypes.byref(n)) == C.LBM_EINVAL
