@@ -209,6 +209,15 @@ int lbm_check_finite(lbm_handle h, long long *nonfinite, void *stream);
 int lbm_debug_flags(lbm_handle h, int *flags, void *stream);
 int lbm_build_checked(void);
 
+/* Failure detection without a GPU fault: runs the bounded mbarrier wait that the
+   TMA-staged kernel (kernel_variant 4) uses on a barrier that expects bytes no
+   copy will deliver. The wait gives up after `polls` polls (1..2^24; 2^12 takes
+   well under a millisecond), writes 1 to *dev_status (a caller-owned device int)
+   and the call returns LBM_ETIMEOUT; the context stays usable. Synchronises
+   `stream`. The staged kernel reports the same condition by OR-ing 16 into the
+   word lbm_debug_flags reads. */
+int lbm_debug_wait_probe(unsigned polls, int *dev_status, void *stream);
+
 /* Checkpoint / resume: the state is lbm_state_bytes bytes (populations and, for
    LBM_BF16S, the phi plane). dev_dst / dev_src: device buffers of that size. */
 int lbm_state_bytes(lbm_handle h, size_t *bytes);

@@ -78,6 +78,7 @@ SIGNATURES = {
     "lbm_check_finite": [_VP, ctypes.POINTER(ctypes.c_longlong), _VP],
     "lbm_debug_flags": [_VP, ctypes.POINTER(_I), _VP],
     "lbm_build_checked": [],
+    "lbm_debug_wait_probe": [ctypes.c_uint, _VP, _VP],
     "lbm_adjoint_workspace_size": [_VP, ctypes.POINTER(_SZ)],
     "lbm_adjoint_begin": [_VP, _VP, _SZ, _VP, _I, _VP],
     "lbm_adjoint_step": [_VP, _VP, _VP],

@@ -51,11 +51,16 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
 }
 
 // bounded wait for phase `parity` of the barrier; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait_limit(unsigned long long *bar, unsigned parity, unsigned limit)
 {
-    for (unsigned i = 0; i < kWaitLimit; ++i)
+    for (unsigned i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+{
+    return mbar_wait_limit(bar, parity, kWaitLimit);
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
@@ -219,4 +224,41 @@ cudaError_t launch_step2_tma(const lbm_solver *s, int src, cudaStream_t st)
     return s->d.per_cell_K ? step2_tma_k<true>(s, src, st) : step2_tma_k<false>(s, src, st);
 }
 
+// ---- failure detection without a fault ----------------------------------------
+// The bounded mbarrier wait of the staged kernel, on a barrier that expects 16
+// bytes no copy will ever deliver: every thread gives up after `limit` polls and
+// the block reports instead of hanging. The barrier never completes, no copy is
+// in flight, so the block may leave.
+__global__ void k_wait_probe(unsigned limit, int *status)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+    __syncthreads();
+    const bool done = mbar_wait_limit(&bar, 0, limit);
+    if (__syncthreads_or(!done) && threadIdx.x == 0) *status = 1;
+    else if (threadIdx.x == 0) *status = 0;
+}
+
 }  // namespace lbm
+
+extern "C" int lbm_debug_wait_probe(unsigned polls, int *dev_status, void *stream)
+{
+    using namespace lbm;
+    if (!dev_status) return fail(LBM_EINVAL, "null status word");
+    if (polls == 0 || polls > (1u << 24)) return fail(LBM_EINVAL, "polls must be in 1..2^24");
+    cudaStream_t st = (cudaStream_t)stream;
+    k_wait_probe<<<1, 64, 0, st>>>(polls, dev_status);
+    if (int rc = cuda_check(cudaGetLastError(), "lbm_debug_wait_probe")) return rc;
+    int timed_out = 0;
+    if (int rc = cuda_check(cudaMemcpyAsync(&timed_out, dev_status, sizeof(int), cudaMemcpyDeviceToHost, st),
+                            "lbm_debug_wait_probe copy"))
+        return rc;
+    if (int rc = cuda_check(cudaStreamSynchronize(st), "lbm_debug_wait_probe sync")) return rc;
+    if (timed_out) return fail(LBM_ETIMEOUT, "the bounded wait ran out after " + std::to_string(polls) + " polls");
+    return LBM_OK;
+}

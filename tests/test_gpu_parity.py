@@ -378,3 +378,23 @@ def test_step_replays_from_a_cuda_graph(prec, spp):
     s.set_phi(phi0)
     s.step(60)
     assert torch.equal(replayed, s.phi().cpu())
+
+
+def test_bounded_wait_reports_instead_of_hanging():
+    """Failure detection without a fault: the bounded mbarrier wait of the
+    TMA-staged kernel, on a barrier no copy completes, gives up, reports
+    LBM_ETIMEOUT, and the context keeps working."""
+    import ctypes
+
+    from paper_1603_09577_gb300 import _lib as C
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = C.lib().lbm_debug_wait_probe(4096, ctypes.c_void_p(status.data_ptr()), st)
+    assert rc == C.LBM_ETIMEOUT
+    assert int(status.item()) == 1
+    assert b"bounded wait" in C.lib().lbm_last_error()
+    phi0 = np.array([[0.1, 0.4, 0.2], [0.8, 0.3, 0.5]])
+    coef = dict(conv=1, u=(0.1, 0.2), diff=2, K=(0.02, 0.005, 0.03), r1=-0.1)
+    ref = run_oracle(3, 2, phi0, 5, **coef)
+    got, _ = run_gpu("f64", 3, 2, phi0, 5, **coef)
+    assert rel(got, ref) <= 1e-12
