@@ -45,6 +45,8 @@ KERNEL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
                         "kernels_step2_bf16.cu", "lbm_device.cuh")]
 GENERAL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
                for f in ("kernels_general.cuh", "kernels_general_f32.cu", "kernels_general_f64.cu", "lbm_device.cuh")]
+STEP2G_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
+              for f in ("kernels_step2g.cu", "kernels_general.cuh", "lbm_device.cuh")]
 
 
 def src_sha(files) -> str:
@@ -482,8 +484,9 @@ def run_burgers_fisher(args):
                       "nx": n, "ny": n, "lattice": {"u": bf["u"], "K": bf["K"], "b": bf["b"]},
                       "l2": "inputs larger than L2 (two population buffers of 604 MB each, FP32)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": (traffic_per_launch(src_sha(GENERAL_SRC), "k_step_g")
-                                    if prec == "f32" and spp == 1 else None),
+                        "traffic": (None if prec != "f32" else
+                                    traffic_per_launch(src_sha(GENERAL_SRC), "k_step_g") if spp == 1 else
+                                    traffic_per_launch(src_sha(STEP2G_SRC), "k_step2g")),
                         "kernel": ("k_step2g (general two-step tile kernel, Scheme A)" if spp == 2
                                    else "k_step_g (general one-step kernel, Scheme A)"),
                         "steps_per_launch": spp,
@@ -492,7 +495,8 @@ def run_burgers_fisher(args):
            "e2e": {"value": cells * lbm_steps / (e2e_ms / 1e3) / 1e6, "unit": "MLUPS",
                    "h2d_bytes_per_step": int(host_in.numel() * esz), "d2h_bytes_per_step": int(host_out.numel() * esz)},
            "gre_vs_eq47": g[1] / g[2],
-           "gpu_launches": args.steps * (1 + launches + 2)}
+           # per job: the initialisation, the sweeps, the record-count advance, two reduction kernels
+           "gpu_launches": args.steps * (1 + launches + 1 + 2)}
     if clocks is not None:
         out["clocks"] = clocks
     if not args.no_cpu_baseline:

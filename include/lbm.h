@@ -172,11 +172,15 @@ int lbm_step(lbm_handle h, int nsteps, void *stream);
 /* Dirichlet data of the LBM_NEE axes. dev_values: device array of nrec >= 1
    records, each 2 (nx + ny) doubles laid out west[ny], east[ny], south[nx],
    north[nx] (a corner node takes its west/east value); the caller owns it and
-   keeps it alive while steps run. Record j is used by the step that produces
-   time level t0 + j + 1, t0 being the step count (since lbm_set_phi) at this
-   call; after the last record the last one is reused (nrec = 1: constant
-   values). lbm_set_phi itself takes the boundary values from phi0. A stream
-   capture of lbm_step records the record pointers of the captured steps. */
+   keeps it alive while steps run. Record j serves the (j + 1)-th step after
+   this call or after the latest lbm_set_phi, whichever came last; after the
+   last record the last one is reused (nrec = 1: constant values). lbm_set_phi
+   itself takes the boundary values from phi0. The step count lives on the
+   device and advances with the steps (one one-thread launch per lbm_step call
+   when nrec > 1), so a CUDA graph of captured steps walks through the records
+   on every replay as direct steps would. This call restarts the count on the
+   stream of the next lbm_step or lbm_save; lbm_set_phi restarts it on its own
+   stream; lbm_save stores it with the state and lbm_load restores it. */
 int lbm_set_dirichlet(lbm_handle h, const double *dev_values, int nrec);
 
 /* phi(t_n) of the current state into dev_out (nx*ny values of `prec`). */
@@ -218,8 +222,9 @@ int lbm_build_checked(void);
    word lbm_debug_flags reads. */
 int lbm_debug_wait_probe(unsigned polls, int *dev_status, void *stream);
 
-/* Checkpoint / resume: the state is lbm_state_bytes bytes (populations and, for
-   LBM_BF16S, the phi plane). dev_dst / dev_src: device buffers of that size. */
+/* Checkpoint / resume: the state is lbm_state_bytes bytes (populations; the phi
+   plane for LBM_BF16S and Scheme A; with LBM_NEE walls, a 256-byte tail holding
+   the Dirichlet record count). dev_dst / dev_src: device buffers of that size. */
 int lbm_state_bytes(lbm_handle h, size_t *bytes);
 int lbm_save(lbm_handle h, void *dev_dst, void *stream);
 int lbm_load(lbm_handle h, const void *dev_src, void *stream);

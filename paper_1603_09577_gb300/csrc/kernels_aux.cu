@@ -288,4 +288,13 @@ cudaError_t launch_reduce(const lbm_solver *s, const double *ref, double *out, c
     return cudaErrorInvalidValue;
 }
 
+// ---- Dirichlet record count -----------------------------------------------------
+__global__ void k_tick(long long *counter, int by) { *counter += by; }
+
+cudaError_t launch_tick(long long *counter, int by, cudaStream_t st)
+{
+    k_tick<<<1, 1, 0, st>>>(counter, by);
+    return cudaGetLastError();
+}
+
 }  // namespace lbm

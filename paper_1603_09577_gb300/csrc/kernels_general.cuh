@@ -15,6 +15,21 @@
 
 namespace lbm {
 
+// The Dirichlet record of a step: record min(*cnt + ahead, nrec - 1) of the
+// caller's array. *cnt counts the steps since the records were set (or since the
+// initial condition) up to the first sweep of the current lbm_step call; `ahead`
+// is the step's place within that call. A one-thread launch after the call's
+// sweeps advances *cnt, so every block of a launch reads the same value and a
+// graph replay of the steps advances the records as a direct run does.
+__device__ __forceinline__ const double *record_of(const double *base, const long long *cnt, int nrec, int rec,
+                                                   int ahead)
+{
+    if (!base) return nullptr;
+    long long j = (cnt ? *cnt : 0) + ahead;
+    if (j > nrec - 1) j = nrec - 1;
+    return base + j * (long long)rec;
+}
+
 // R(phi): affine (r0 + r1 phi) or Fisher (b phi (1 - phi^delta), Eq. 46)
 template <class C>
 __device__ __forceinline__ C source_value(const Params<C> &p, C phi)
@@ -177,7 +192,7 @@ template <int PREC, int CONV, int DIFF, bool SA>
 __global__ void __launch_bounds__(256)
 k_step_g(const Params<typename Store<PREC>::C> p, const typename Store<PREC>::T *__restrict__ src,
          const typename Store<PREC>::C *__restrict__ src_phi, typename Store<PREC>::T *__restrict__ dst,
-         typename Store<PREC>::C *__restrict__ dst_phi)
+         typename Store<PREC>::C *__restrict__ dst_phi, const long long *__restrict__ rec_cnt, int nrec, int rec_off)
 {
     using S = Store<PREC>;
     using C = typename S::C;
@@ -199,7 +214,8 @@ k_step_g(const Params<typename Store<PREC>::C> p, const typename Store<PREC>::T 
 #pragma unroll
         for (int k = 1; k < 9; ++k) sum += f[k];
         const C phif = SA ? sum : (sum + p.half_r0) * p.inv_den;
-        const double vb = ex ? p.bv[x == 0 ? y : p.ny + y] : p.bv[2 * p.ny + (y == 0 ? x : p.nx + x)];
+        const double *bv = record_of(p.bv, rec_cnt, nrec, 2 * (p.nx + p.ny), rec_off);
+        const double vb = ex ? bv[x == 0 ? y : p.ny + y] : bv[2 * p.ny + (y == 0 ? x : p.nx + x)];
         C eb[9], ef[9];
         feq_stored<C, CONV, DIFF, SA>(p, (C)vb, eb);
         feq_stored<C, CONV, DIFF, SA>(p, phif, ef);
@@ -285,7 +301,8 @@ static cudaError_t general_t(const lbm_solver *s, int src, const double *bv, con
                                                               (C *)s->phi[s->cur]);
     } else {
         k_step_g<PREC, CONV, DIFF, SA><<<grid, block, 0, st>>>(p, (const T *)s->pop[src], (const C *)s->phi[src],
-                                                              (T *)s->pop[src ^ 1], (C *)s->phi[src ^ 1]);
+                                                              (T *)s->pop[src ^ 1], (C *)s->phi[src ^ 1],
+                                                              s->dir_counter, s->dir_nrec, s->dir_off);
     }
     return cudaGetLastError();
 }

@@ -46,9 +46,20 @@ __device__ __forceinline__ int tile_origin(int b, int n, int nee)
     return (nee && n >= kTX && t0 > n - kTX) ? n - kTX : t0;
 }
 
-// Dirichlet value of an extrapolated node from a record (west, east, south, north)
-__device__ __forceinline__ float dirichlet(const Params<float> &p, const double *bv, bool ex, int x, int y)
+// The caller's Dirichlet records and the place of this sweep's first step
+// (kernel parameters; the record is looked up where a Dirichlet node needs it,
+// so no pointer stays live in registers across the sweep)
+struct Records {
+    const double *base;
+    const long long *cnt;
+    int nrec, off;
+};
+
+// Dirichlet value of an extrapolated node at the level `lvl` (0: step A,
+// 1: step B) from its record (west, east, south, north)
+__device__ __forceinline__ float dirichlet(const Params<float> &p, const Records &r, int lvl, bool ex, int x, int y)
 {
+    const double *bv = record_of(r.base, r.cnt, r.nrec, 2 * (p.nx + p.ny), r.off + lvl);
     return (float)(ex ? bv[x == 0 ? y : p.ny + y] : bv[2 * p.ny + (y == 0 ? x : p.nx + x)]);
 }
 
@@ -71,7 +82,7 @@ __device__ __forceinline__ void collide_pair_g(const Params<F2> &pw, float f[2][
 // Dirichlet node) and phi(t_n); false for a node outside the domain.
 template <int CONV, int DIFF, bool SA, bool INTERIOR>
 __device__ __forceinline__ bool node_A(const Params<float> &p, const float *__restrict__ src,
-                                       const float *__restrict__ src_phi, const double *bvA, int x, int y, float f[9],
+                                       const float *__restrict__ src_phi, const Records &rec, int x, int y, float f[9],
                                        float &prev)
 {
     if (INTERIOR) {
@@ -101,7 +112,7 @@ __device__ __forceinline__ bool node_A(const Params<float> &p, const float *__re
         for (int k = 1; k < 9; ++k) sum += f[k];
         const float phif = SA ? sum : (sum + p.half_r0) * p.inv_den;
         float eb[9], ef[9];
-        feq_stored<float, CONV, DIFF, SA>(p, dirichlet(p, bvA, ex, x, y), eb);
+        feq_stored<float, CONV, DIFF, SA>(p, dirichlet(p, rec, 0, ex, x, y), eb);
         feq_stored<float, CONV, DIFF, SA>(p, phif, ef);
 #pragma unroll
         for (int k = 0; k < 9; ++k) f[k] = eb[k] + (f[k] - ef[k]);
@@ -118,7 +129,7 @@ __device__ __forceinline__ bool node_A(const Params<float> &p, const float *__re
 template <int CONV, int DIFF, bool SA, bool INTERIOR>
 __device__ __forceinline__ void two_steps_g(const Params<float> &p, const float *__restrict__ src,
                                             const float *__restrict__ src_phi, float *__restrict__ dst,
-                                            float *__restrict__ dst_phi, const double *bvA, const double *bvB,
+                                            float *__restrict__ dst_phi, const Records &rec,
                                             float *sm, int tx0, int ty0)
 {
     constexpr int kWarps = kT2Threads / 32;
@@ -134,7 +145,7 @@ __device__ __forceinline__ void two_steps_g(const Params<float> &p, const float 
         bool ok[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
-            ok[h] = node_A<CONV, DIFF, SA, INTERIOR>(p, src, src_phi, bvA, tx0 - 1 + lane, ty0 - 1 + hy0 + h * kWarps,
+            ok[h] = node_A<CONV, DIFF, SA, INTERIOR>(p, src, src_phi, rec, tx0 - 1 + lane, ty0 - 1 + hy0 + h * kWarps,
                                                      f[h], prev[h]);
         collide_pair_g<CONV, DIFF, SA>(pw, f, prev, phi);
 #pragma unroll
@@ -183,7 +194,7 @@ __device__ __forceinline__ void two_steps_g(const Params<float> &p, const float 
                     }
                     const float phif = SA ? sum : (sum + p.half_r0) * p.inv_den;
                     float eb[9], ef[9];
-                    feq_stored<float, CONV, DIFF, SA>(p, dirichlet(p, bvB, ex, x, yy), eb);
+                    feq_stored<float, CONV, DIFF, SA>(p, dirichlet(p, rec, 1, ex, x, yy), eb);
                     feq_stored<float, CONV, DIFF, SA>(p, phif, ef);
 #pragma unroll
                     for (int k = 0; k < 9; ++k) f[h][k] = eb[k] + (f[h][k] - ef[k]);
@@ -232,35 +243,38 @@ __device__ __forceinline__ void two_steps_g(const Params<float> &p, const float 
 template <int CONV, int DIFF, bool SA>
 __global__ void __launch_bounds__(kT2Threads, 4)
 k_step2g(const Params<float> p, const float *__restrict__ src, const float *__restrict__ src_phi,
-         float *__restrict__ dst, float *__restrict__ dst_phi, const double *bvA, const double *bvB)
+         float *__restrict__ dst, float *__restrict__ dst_phi, const double *records, const long long *rec_cnt,
+         int nrec, int rec_off)
 {
     extern __shared__ float sm[];       // 9 planes (+ phi for Scheme A) of 32 x 32
+    const Records rec{records, rec_cnt, nrec, rec_off};
     const int tx0 = tile_origin(blockIdx.x, p.nx, p.nee_x), ty0 = tile_origin(blockIdx.y, p.ny, p.nee_y);
     // interior tile: no wrap, wall or Dirichlet node in the region or its sources
     const bool interior = tx0 >= 2 && tx0 + kTX + 1 <= p.nx - 1 && ty0 >= 2 && ty0 + 30 + 1 <= p.ny - 1;
-    if (interior) two_steps_g<CONV, DIFF, SA, true>(p, src, src_phi, dst, dst_phi, bvA, bvB, sm, tx0, ty0);
-    else two_steps_g<CONV, DIFF, SA, false>(p, src, src_phi, dst, dst_phi, bvA, bvB, sm, tx0, ty0);
+    if (interior) two_steps_g<CONV, DIFF, SA, true>(p, src, src_phi, dst, dst_phi, rec, sm, tx0, ty0);
+    else two_steps_g<CONV, DIFF, SA, false>(p, src, src_phi, dst, dst_phi, rec, sm, tx0, ty0);
 }
 
 namespace {
 
 template <int CONV, int DIFF, bool SA>
-cudaError_t step2g_t(const lbm_solver *s, int src, const double *bvA, const double *bvB, cudaStream_t st)
+cudaError_t step2g_t(const lbm_solver *s, int src, const double *records, cudaStream_t st)
 {
     const size_t smem = (9 + (SA ? 1 : 0)) * kRPg * sizeof(float);
     Params<float> p = make_params<float>(s);
     dim3 block(32, kT2Threads / 32);
     dim3 grid((s->d.nx + kTX - 1) / kTX, (s->d.ny + 29) / 30);
     k_step2g<CONV, DIFF, SA><<<grid, block, smem, st>>>(p, (const float *)s->pop[src], s->phi[src],
-                                                        (float *)s->pop[src ^ 1], s->phi[src ^ 1], bvA, bvB);
+                                                        (float *)s->pop[src ^ 1], s->phi[src ^ 1], records,
+                                                        s->dir_counter, s->dir_nrec, s->dir_off);
     return cudaGetLastError();
 }
 
 template <bool SA>
-cudaError_t step2g_s(const lbm_solver *s, int src, const double *bvA, const double *bvB, cudaStream_t st)
+cudaError_t step2g_s(const lbm_solver *s, int src, const double *records, cudaStream_t st)
 {
 #define LBM_G2(CV, DF) \
-    case CV * 4 + DF: return step2g_t<CV, DF, SA>(s, src, bvA, bvB, st);
+    case CV * 4 + DF: return step2g_t<CV, DF, SA>(s, src, records, st);
     switch (s->c.conv * 4 + s->c.diff) {
         LBM_G2(0, 0)
         LBM_G2(0, 1)
@@ -281,10 +295,10 @@ cudaError_t step2g_s(const lbm_solver *s, int src, const double *bvA, const doub
 
 }  // namespace
 
-cudaError_t launch_step2_general(const lbm_solver *s, int src, const double *bvA, const double *bvB, cudaStream_t st)
+cudaError_t launch_step2_general(const lbm_solver *s, int src, const double *records, cudaStream_t st)
 {
     if (s->d.prec != LBM_F32 || s->c.cfree || s->c.conv > 2 || s->d.per_cell_K) return cudaErrorInvalidValue;
-    return s->d.scheme == LBM_SCHEME_A ? step2g_s<true>(s, src, bvA, bvB, st) : step2g_s<false>(s, src, bvA, bvB, st);
+    return s->d.scheme == LBM_SCHEME_A ? step2g_s<true>(s, src, records, st) : step2g_s<false>(s, src, records, st);
 }
 
 }  // namespace lbm

@@ -61,6 +61,8 @@ int make_layout(const lbm_desc *d, Layout *L)
     off += 256;
     L->off_err = off;
     off += 256;
+    L->off_cnt = off;
+    off += 256;
     L->total = off;
     return LBM_OK;
 }
@@ -235,6 +237,7 @@ int lbm_create(lbm_handle *h, const lbm_desc *desc, void *dev_workspace, size_t 
     s->flag = (int *)(s->ws + L.off_flag);
     s->check = (double *)(s->ws + L.off_check);
     s->err = (int *)(s->ws + L.off_err);
+    s->dir_counter = (long long *)(s->ws + L.off_cnt);
     *h = s;
     return LBM_OK;
 }
@@ -317,6 +320,22 @@ int lbm_set_K_field(lbm_handle h, const double *dev_K, void *stream)
     return LBM_OK;
 }
 
+static bool is_nee(const lbm_solver *h) { return h->d.bc_x == LBM_NEE || h->d.bc_y == LBM_NEE; }
+
+// bytes of a saved state: populations, the phi plane, and for extrapolated
+// walls a 256-byte tail holding the device count of the Dirichlet records
+static size_t state_size(const lbm_solver *h) { return h->L.pop_bytes + h->L.phi_bytes + (is_nee(h) ? 256 : 0); }
+
+// a pending restart of the record count, issued on `st`
+static int flush_record_reset(lbm_solver *h, cudaStream_t st)
+{
+    if (!h->dir_reset) return LBM_OK;
+    if (int rc = cuda_check(cudaMemsetAsync(h->dir_counter, 0, sizeof(long long), st), "Dirichlet record count"))
+        return rc;
+    h->dir_reset = 0;
+    return LBM_OK;
+}
+
 int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream)
 {
     if (int rc = check_ready(h)) return rc;
@@ -326,6 +345,12 @@ int lbm_set_phi(lbm_handle h, const void *dev_phi, int prec, void *stream)
     const cudaError_t e = general_path(h) ? launch_general(h, h->cur, nullptr, dev_phi, prec, (cudaStream_t)stream)
                                           : launch_init(h, dev_phi, prec, (cudaStream_t)stream);
     if (int rc = cuda_check(e, "lbm_set_phi")) return rc;
+    if (is_nee(h)) {                     // the Dirichlet records restart with the initial condition
+        if (int rc = cuda_check(cudaMemsetAsync(h->dir_counter, 0, sizeof(long long), (cudaStream_t)stream),
+                                "lbm_set_phi (records)"))
+            return rc;
+        h->dir_reset = 0;
+    }
     h->phi_set = 1;
     h->t = 0;
     return LBM_OK;
@@ -351,19 +376,18 @@ int lbm_step(lbm_handle h, int nsteps, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     int done = 0;
     if (general_path(h)) {
-        const bool nee = h->d.bc_x == LBM_NEE || h->d.bc_y == LBM_NEE;
+        const bool nee = is_nee(h);
         if (nee && !h->dir_vals) return fail(LBM_EINVAL, "lbm_set_dirichlet has not been called");
-        const size_t rec = 2 * ((size_t)h->d.nx + h->d.ny);
-        // record of the step that produces time level t + 1
-        auto record = [&](long long t) -> const double * {
-            if (!nee) return nullptr;
-            long long j = t - h->dir_t0;
-            j = j < 0 ? 0 : (j >= h->dir_nrec ? h->dir_nrec - 1 : j);
-            return h->dir_vals + (size_t)j * rec;
-        };
+        // the kernels pick the record from the device count of steps since the
+        // records were set plus the sweep's place in this call (dir_off); one
+        // one-thread launch advances the count after the call's sweeps
+        const double *records = nee ? h->dir_vals : nullptr;
+        if (nee)
+            if (int rc = flush_record_reset(h, st)) return rc;
         if (h->d.steps_per_pass == 2) {
             for (; done + 2 <= nsteps; done += 2) {
-                if (int rc = cuda_check(launch_step2_general(h, h->cur, record(h->t), record(h->t + 1), st),
+                h->dir_off = done;
+                if (int rc = cuda_check(launch_step2_general(h, h->cur, records, st),
                                         "lbm_step (general, two steps per pass)"))
                     return rc;
                 h->cur ^= 1;
@@ -371,11 +395,15 @@ int lbm_step(lbm_handle h, int nsteps, void *stream)
             }
         }
         for (; done < nsteps; ++done) {
-            if (int rc = cuda_check(launch_general(h, h->cur, record(h->t), nullptr, 0, st), "lbm_step (general)"))
+            h->dir_off = done;
+            if (int rc = cuda_check(launch_general(h, h->cur, records, nullptr, 0, st), "lbm_step (general)"))
                 return rc;
             h->cur ^= 1;
             h->t += 1;
         }
+        h->dir_off = 0;
+        if (nee && h->dir_nrec > 1 && nsteps > 0)
+            if (int rc = cuda_check(launch_tick(h->dir_counter, nsteps, st), "lbm_step (records)")) return rc;
         return LBM_OK;
     }
     if (h->d.steps_per_pass == 2) {
@@ -404,7 +432,7 @@ int lbm_set_dirichlet(lbm_handle h, const double *dev_values, int nrec)
     if (!dev_values || nrec < 1) return fail(LBM_EINVAL, "need a device array of nrec >= 1 records");
     h->dir_vals = dev_values;
     h->dir_nrec = nrec;
-    h->dir_t0 = h->t;
+    h->dir_reset = 1;                    // record 0 serves the next step (count cleared on its stream)
     return LBM_OK;
 }
 
@@ -475,7 +503,7 @@ int lbm_state_bytes(lbm_handle h, size_t *bytes)
 {
     if (check_handle(h)) return LBM_EINVAL;
     if (!bytes) return fail(LBM_EINVAL, "null size pointer");
-    *bytes = h->L.pop_bytes + h->L.phi_bytes;
+    *bytes = state_size(h);
     return LBM_OK;
 }
 
@@ -487,8 +515,14 @@ int lbm_save(lbm_handle h, void *dev_dst, void *stream)
     if (int rc = cuda_check(cudaMemcpyAsync(dev_dst, h->pop[h->cur], h->L.pop_bytes, cudaMemcpyDeviceToDevice, st), "lbm_save"))
         return rc;
     if (h->L.phi_bytes)
-        return cuda_check(cudaMemcpyAsync((char *)dev_dst + h->L.pop_bytes, h->phi[h->cur], h->L.phi_bytes,
-                                          cudaMemcpyDeviceToDevice, st), "lbm_save phi");
+        if (int rc = cuda_check(cudaMemcpyAsync((char *)dev_dst + h->L.pop_bytes, h->phi[h->cur], h->L.phi_bytes,
+                                                cudaMemcpyDeviceToDevice, st), "lbm_save phi"))
+            return rc;
+    if (is_nee(h)) {
+        if (int rc = flush_record_reset(h, st)) return rc;
+        return cuda_check(cudaMemcpyAsync((char *)dev_dst + h->L.pop_bytes + h->L.phi_bytes, h->dir_counter,
+                                          sizeof(long long), cudaMemcpyDeviceToDevice, st), "lbm_save records");
+    }
     return LBM_OK;
 }
 
@@ -503,6 +537,12 @@ int lbm_load(lbm_handle h, const void *dev_src, void *stream)
         if (int rc = cuda_check(cudaMemcpyAsync(h->phi[h->cur], (const char *)dev_src + h->L.pop_bytes, h->L.phi_bytes,
                                                 cudaMemcpyDeviceToDevice, st), "lbm_load phi"))
             return rc;
+    if (is_nee(h)) {
+        if (int rc = cuda_check(cudaMemcpyAsync(h->dir_counter, (const char *)dev_src + h->L.pop_bytes + h->L.phi_bytes,
+                                                sizeof(long long), cudaMemcpyDeviceToDevice, st), "lbm_load records"))
+            return rc;
+        h->dir_reset = 0;
+    }
     h->phi_set = 1;
     return LBM_OK;
 }
@@ -575,7 +615,7 @@ int lbm_adjoint_segment(lbm_handle h, const void *dev_ckpt, int nsteps, void *de
     if (!h->adj_active) return fail(LBM_EINVAL, "lbm_adjoint_begin has not been called");
     if (!dev_ckpt) return fail(LBM_EINVAL, "null checkpoint");
     if (nsteps < 1) return fail(LBM_EINVAL, "segment length must be >= 1");
-    const size_t sb = h->L.pop_bytes + h->L.phi_bytes;
+    const size_t sb = state_size(h);
     if (nsteps > 1 && (!dev_states || bytes < (size_t)(nsteps - 1) * sb))
         return fail(LBM_EINVAL, "state scratch smaller than (nsteps - 1) * lbm_state_bytes");
     cudaStream_t st = (cudaStream_t)stream;

@@ -20,7 +20,7 @@ struct Layout {
     long long pitch = 0, plane = 0;
     size_t esize = 0, csize = 0;
     size_t off_pop[2] = {0, 0}, off_phi[2] = {0, 0};
-    size_t off_afield = 0, off_staging = 0, off_partials = 0, off_flag = 0, off_check = 0, off_err = 0;
+    size_t off_afield = 0, off_staging = 0, off_partials = 0, off_flag = 0, off_check = 0, off_err = 0, off_cnt = 0;
     size_t pop_bytes = 0, phi_bytes = 0, total = 0;
 };
 
@@ -48,7 +48,9 @@ struct lbm_solver {
     // Dirichlet records of the extrapolated axes (caller-owned device memory)
     const double *dir_vals = nullptr;
     int dir_nrec = 0;
-    long long dir_t0 = 0;
+    long long *dir_counter = nullptr;   // device: steps since the records' count restarted
+    int dir_reset = 0;                  // 1: clear dir_counter before the next step
+    int dir_off = 0;                    // place of the next sweep's first step within its lbm_step call
     // adjoint (caller-provided second workspace)
     char *adj = nullptr;
     void *lam[2] = {nullptr, nullptr};
@@ -79,8 +81,10 @@ cudaError_t launch_general_f64(const lbm_solver *s, int src, const double *bv, c
                                cudaStream_t st);
 cudaError_t launch_general_f32(const lbm_solver *s, int src, const double *bv, const void *phi0, int in_prec,
                                cudaStream_t st);
-// two general steps per pass (FP32): records of the two time levels it produces
-cudaError_t launch_step2_general(const lbm_solver *s, int src, const double *bvA, const double *bvB, cudaStream_t st);
+// two general steps per pass (FP32); records: the caller's Dirichlet records
+cudaError_t launch_step2_general(const lbm_solver *s, int src, const double *records, cudaStream_t st);
+// advance the device record count by `by` steps (one thread, after a call's sweeps)
+cudaError_t launch_tick(long long *counter, int by, cudaStream_t st);
 bool step_v4_supported(const lbm_solver *s);
 bool step_v4_preferred(const lbm_solver *s);
 cudaError_t launch_step_v4(const lbm_solver *s, int src, cudaStream_t st);

@@ -114,7 +114,9 @@ class Solver:
     def set_dirichlet(self, values: torch.Tensor):
         """Dirichlet records of the extrapolated axes: (nrec, 2 (nx + ny)) float64
         on the device, each record west[ny], east[ny], south[nx], north[nx];
-        record j serves the step that produces the j + 1-th time level from now."""
+        record j serves the (j + 1)-th step from now (or from the next set_phi);
+        the last one is reused after it. The step count is kept on the device,
+        so graph replays advance through the records."""
         v = values.to(device=self.device, dtype=torch.float64).contiguous()
         if v.dim() == 1:
             v = v.view(1, -1)
@@ -135,8 +137,9 @@ class Solver:
         even in number (nsteps even with one step per pass, a multiple of 4 with
         two), so that every replay ends on the buffer it started from. One step
         is run first and undone (save / load) so that kernel attributes are set
-        outside the capture. Extrapolated walls replay the Dirichlet records of
-        the recorded steps."""
+        outside the capture (the Dirichlet record count is saved and restored
+        with the state). With extrapolated walls each replay takes the next
+        records, as direct steps would."""
         spp = int(self.desc.steps_per_pass)
         launches = nsteps // spp + nsteps % spp
         if nsteps < 1 or launches % 2:

@@ -329,3 +329,58 @@ def test_general_path_replays_from_a_cuda_graph(spp):
     d.set_phi(phi0)
     d.step(60)
     assert torch.equal(replayed, d.phi().cpu())
+
+
+@pytest.mark.parametrize("spp", [1, 2])
+def test_graph_replay_walks_through_time_dependent_records(spp):
+    """With 70 time-dependent records, three replays of 20 captured steps equal
+    60 direct steps bit for bit (records 0..59), and the oracle with the same
+    records; ten more direct steps then take records 60..69."""
+    nx, ny = 52, 37
+    rng = np.random.default_rng(31)
+    phi0 = torch.from_numpy(W.jacobi_smooth(rng.uniform(0.2, 0.8, (ny, nx)), 2)).cuda()
+    bv = records(nx, ny, 70, 17)
+    coef = COEFS["power1-fisher"]
+
+    def make():
+        s = Solver(nx, ny, prec="f32", bc=("nee", "nee"), scheme="A", steps_per_pass=spp)
+        s.set_coeffs(s=W.s9(), **coef)
+        s.set_dirichlet(torch.from_numpy(bv).cuda())
+        s.set_phi(phi0)
+        return s
+
+    s = make().capture(20)
+    for _ in range(3):
+        s.replay()
+    torch.cuda.synchronize()
+    replayed = s.phi().cpu()
+    d = make().step(60)
+    assert torch.equal(replayed, d.phi().cpu())
+    sp = O.Spec(nx=nx, ny=ny, bc_x=2, bc_y=2, s=W.s9(), scheme=1, **coef)
+    ref = O.run_x(sp, phi0.cpu().numpy(), 60, bv[:60])
+    assert rel(replayed.numpy(), ref) <= TOL["f32"]
+    s.step(10)
+    ref70 = O.run_x(sp, phi0.cpu().numpy(), 70, bv)
+    assert rel(s.phi().cpu().numpy(), ref70) <= TOL["f32"]
+
+
+def test_checkpoint_restores_the_record_count():
+    """lbm_save stores the Dirichlet record count with the state: resuming from a
+    checkpoint taken at step 12 re-runs steps 13..24 with records 12..23."""
+    nx, ny = 40, 30
+    rng = np.random.default_rng(8)
+    phi0 = W.jacobi_smooth(rng.uniform(0.2, 0.8, (ny, nx)), 2)
+    bv = records(nx, ny, 30, 4)
+    coef = COEFS["power1-fisher"]
+    s = Solver(nx, ny, prec="f64", bc=("nee", "periodic"), scheme="A").set_coeffs(s=W.s9(), **coef)
+    s.set_dirichlet(torch.from_numpy(bv).cuda())
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    assert s.state_bytes() % 256 == 0
+    s.step(12)
+    ck = s.save()
+    s.step(12)
+    first = s.phi().cpu()
+    s.load(ck).step(12)
+    assert torch.equal(first, s.phi().cpu())
+    ref = O.run_x(O.Spec(nx=nx, ny=ny, bc_x=2, bc_y=0, s=W.s9(), scheme=1, **coef), phi0, 24, bv[:24])
+    assert rel(first.numpy(), ref) <= 1e-12
