@@ -179,8 +179,10 @@ int lbm_step(lbm_handle h, int nsteps, void *stream);
    device and advances with the steps (one one-thread launch per lbm_step call
    when nrec > 1), so a CUDA graph of captured steps walks through the records
    on every replay as direct steps would. This call restarts the count on the
-   stream of the next lbm_step or lbm_save; lbm_set_phi restarts it on its own
-   stream; lbm_save stores it with the state and lbm_load restores it. */
+   stream of the next lbm_step or lbm_save (a capture of that lbm_step records
+   the restart too, and every replay then starts the records over: step or
+   save once before capturing); lbm_set_phi restarts it on its own stream;
+   lbm_save stores it with the state and lbm_load restores it. */
 int lbm_set_dirichlet(lbm_handle h, const double *dev_values, int nrec);
 
 /* phi(t_n) of the current state into dev_out (nx*ny values of `prec`). */
