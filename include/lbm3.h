@@ -66,7 +66,9 @@ int lbm3_set_coeffs(lbm3_handle h, const lbm3_coeffs *c);
 /* Initial condition (Eq. 40 in the shifted variable of Eq. 33, then one
    collision). dev_phi: nx*ny*nz values of `prec` (LBM_F64 or LBM_F32). */
 int lbm3_set_phi(lbm3_handle h, const void *dev_phi, int prec, void *stream);
-/* Advance nsteps fused pull-stream / collide steps (asynchronous). */
+/* Advance nsteps fused pull-stream / collide steps (asynchronous). The kernels
+   alternate between the two population buffers and need no function
+   attributes, so a stream capture of an even nsteps replays consistently. */
 int lbm3_step(lbm3_handle h, int nsteps, void *stream);
 /* phi(t_n) into dev_out (nx*ny*nz values of `prec`). */
 int lbm3_get_phi(lbm3_handle h, void *dev_out, int prec, void *stream);

@@ -55,6 +55,23 @@ class Solver3:
         C.check(self.lib.lbm3_step(self.h, int(n), _stream(stream)))
         return self
 
+    # -- CUDA graphs -------------------------------------------------------------
+    def capture(self, nsteps: int):
+        """Record nsteps (even, so that every replay ends on the buffer it
+        started from) time steps into a CUDA graph; replay() relaunches them."""
+        if nsteps < 2 or nsteps % 2:
+            raise ValueError("capture needs an even number of steps")
+        torch.cuda.current_stream().synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            C.check(self.lib.lbm3_step(self.h, int(nsteps), _stream()))
+        self._graph, self._graph_steps = g, int(nsteps)
+        return self
+
+    def replay(self):
+        self._graph.replay()
+        return self
+
     def phi(self, dtype=torch.float64, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         if out is None:
             out = torch.empty((self.nz, self.ny, self.nx), dtype=dtype, device=self.device)

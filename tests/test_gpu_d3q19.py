@@ -66,3 +66,23 @@ def test_d3q19_gaussian_hill_96():
         got = s.phi().cpu().numpy()
         assert rel(got, ref) <= TOL[prec], (prec, rel(got, ref))
         assert np.abs(got - exact).sum() / np.abs(exact).sum() < 4e-3      # oracle: 2.25e-3
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16s"])
+def test_d3q19_replays_from_a_cuda_graph(prec):
+    """Solver3.capture / replay: four replays of 6 recorded steps equal 24 direct
+    steps bit for bit, and match the oracle."""
+    nx, ny, nz, coef = CASES[1]
+    rng = np.random.default_rng(44)
+    phi0 = rng.uniform(0.2, 0.8, (nz, ny, nx))
+    dev = torch.from_numpy(phi0).cuda()
+    s = Solver3(nx, ny, nz, prec=prec).set_coeffs(**coef).set_phi(dev).capture(6)
+    for _ in range(4):
+        s.replay()
+    torch.cuda.synchronize()
+    d = Solver3(nx, ny, nz, prec=prec).set_coeffs(**coef).set_phi(dev).step(24)
+    assert torch.equal(s.phi().cpu(), d.phi().cpu())
+    ref = D.run(D.Spec3(nx=nx, ny=ny, nz=nz, **coef), phi0, 24)
+    assert rel(s.phi().cpu().numpy(), ref) <= TOL[prec]
+    with pytest.raises(ValueError):
+        s.capture(5)
