@@ -311,6 +311,15 @@ int lbm_ensemble_capture(lbm_ensemble e, int nsteps, void *stream);
 int lbm_ensemble_replay(lbm_ensemble e, void *stream);
 /* phi(t_n) of every instance into the packed array dev_out. */
 int lbm_ensemble_get_phi(lbm_ensemble e, void *dev_out, int prec, void *stream);
+/* The statistics of lbm_reduce (Eq. 39 and norms) for every instance: dev_ref
+   is the packed FP64 reference (one value per node, lbm_ensemble_get_phi's
+   order) or NULL; dev_out receives count x 8 doubles on the device, instance
+   i's eight at dev_out[8 i], in lbm_reduce's order and meaning, phi(t_n) being
+   the FP32 value lbm_ensemble_get_phi returns. FP64, summed in a fixed order
+   (per 32 x 8 tile, then the tiles in order): bit-reproducible. Asynchronous;
+   uses a scratch area of the ensemble's workspace, so calls on different
+   streams must not overlap. */
+int lbm_ensemble_reduce(lbm_ensemble e, const double *dev_ref, double *dev_out, void *stream);
 /* Index-fault word of checked builds (see lbm_debug_flags); synchronises. */
 int lbm_ensemble_debug_flags(lbm_ensemble e, int *flags, void *stream);
 

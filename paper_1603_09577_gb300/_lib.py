@@ -104,6 +104,7 @@ SIGNATURES = {
     "lbm_ensemble_set_persistent": [_VP, _I],
     "lbm_ensemble_replay": [_VP, _VP],
     "lbm_ensemble_get_phi": [_VP, _VP, _I, _VP],
+    "lbm_ensemble_reduce": [_VP, _VP, _VP, _VP],
     "lbm_ensemble_debug_flags": [_VP, ctypes.POINTER(_I), _VP],
 }
 

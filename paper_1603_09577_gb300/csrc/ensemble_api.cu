@@ -15,7 +15,7 @@ namespace {
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct EnsLayout {
-    size_t off_inst = 0, off_tiles = 0, off_tiles2 = 0, off_err = 0, total = 0;
+    size_t off_inst = 0, off_tiles = 0, off_tiles2 = 0, off_err = 0, off_partials = 0, off_tbegin = 0, total = 0;
     int ntiles = 0, ntiles2 = 0;
     std::vector<size_t> off_pop;    // per instance: buffer A offset (B follows)
     std::vector<long long> pitch;
@@ -43,6 +43,10 @@ int ens_layout(int count, const int *nx, const int *ny, EnsLayout *L)
     off += up256(sizeof(int4) * (size_t)tiles2);
     L->off_err = off;
     off += 256;
+    L->off_partials = off;
+    off += up256(8 * sizeof(double) * (size_t)tiles);
+    L->off_tbegin = off;
+    off += up256(sizeof(int) * ((size_t)count + 1));
     L->off_pop.resize(count);
     L->pitch.resize(count);
     for (int i = 0; i < count; ++i) {
@@ -130,6 +134,10 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     e->family = c0.conv * 3 + c0.diff;
     e->ntiles = L.ntiles;
     e->tile_begin = new (std::nothrow) int[count + 1];
+    if (!e->tile_begin) {
+        delete e;
+        return fail(LBM_EINVAL, "out of host memory");
+    }
     std::vector<int4> tiles;
     tiles.reserve(L.ntiles);
     long long phi_off = 0;
@@ -152,6 +160,8 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     e->d_inst = (EnsInst *)(ws + L.off_inst);
     e->d_tiles = (int4 *)(ws + L.off_tiles);
     e->err = (int *)(ws + L.off_err);
+    e->partials = (double *)(ws + L.off_partials);
+    e->d_tile_begin = (int *)(ws + L.off_tbegin);
     int rc = cuda_check(cudaMemcpy(e->d_inst, inst.data(), sizeof(EnsInst) * count, cudaMemcpyHostToDevice),
                         "lbm_ensemble_create instance table");
     if (!rc) rc = cuda_check(cudaMemcpy(e->d_tiles2, tiles2.data(), sizeof(int4) * tiles2.size(), cudaMemcpyHostToDevice),
@@ -159,6 +169,8 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     if (!rc) rc = cuda_check(cudaMemset(e->err, 0, sizeof(int)), "lbm_ensemble_create error word");
     if (!rc) rc = cuda_check(cudaMemcpy(e->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice),
                              "lbm_ensemble_create tile table");
+    if (!rc) rc = cuda_check(cudaMemcpy(e->d_tile_begin, e->tile_begin, sizeof(int) * ((size_t)count + 1),
+                                        cudaMemcpyHostToDevice), "lbm_ensemble_create tile offsets");
     int dev = 0, sms = 0;
     if (!rc) rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
@@ -291,6 +303,12 @@ int lbm_ensemble_debug_flags(lbm_ensemble e, int *flags, void *stream)
     if (int rc = cuda_check(cudaMemcpyAsync(flags, e->err, sizeof(int), cudaMemcpyDeviceToHost, st), "lbm_ensemble_debug_flags"))
         return rc;
     return cuda_check(cudaStreamSynchronize(st), "lbm_ensemble_debug_flags sync");
+}
+
+int lbm_ensemble_reduce(lbm_ensemble e, const double *dev_ref, double *dev_out, void *stream)
+{
+    if (!e || !dev_out) return fail(LBM_EINVAL, "null ensemble or output");
+    return cuda_check(ens_launch_reduce(e, dev_ref, dev_out, (cudaStream_t)stream), "lbm_ensemble_reduce");
 }
 
 int lbm_ensemble_get_phi(lbm_ensemble e, void *dev_out, int prec, void *stream)

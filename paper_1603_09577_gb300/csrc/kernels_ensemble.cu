@@ -112,6 +112,97 @@ k_ens_get_phi(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, 
     }
 }
 
+// ---- per-instance statistics (the eight of lbm_reduce), FP64, fixed order ----
+// Pass 1: each 32 x 8 tile's statistics, a block per tile (grid-stride over the
+// list), combined by a fixed-order warp-shuffle and shared-memory tree. The
+// tiles of an instance are contiguous in the list, so pass 2 (one block per
+// instance) combines the instance's tile partials in list order. Every sum is
+// taken in the same order on every call: the results are reproducible bit for bit.
+constexpr int kEnsAcc = 8;
+
+__device__ __forceinline__ double ens_combine(int j, double a, double b) { return j == 5 ? fmax(a, b) : a + b; }
+
+// fixed-order reduction of v over the block into out (thread 0 writes)
+__device__ __forceinline__ void ens_block_reduce(double v[kEnsAcc], double *__restrict__ out)
+{
+    __shared__ double sh[kEnsThreads / 32][kEnsAcc];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int j = 0; j < kEnsAcc; ++j) v[j] = ens_combine(j, v[j], __shfl_down_sync(0xffffffffu, v[j], off));
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int j = 0; j < kEnsAcc; ++j) sh[tid >> 5][j] = v[j];
+    __syncthreads();
+    if (tid == 0)
+        for (int j = 0; j < kEnsAcc; ++j) {
+            double a = sh[0][j];
+            for (int w = 1; w < kEnsThreads / 32; ++w) a = ens_combine(j, a, sh[w][j]);
+            out[j] = a;
+        }
+    __syncthreads();                        // sh is reused by the block's next tile
+}
+
+__global__ void __launch_bounds__(kEnsThreads)
+k_ens_reduce1(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int ntiles, int parity,
+              const double *__restrict__ ref, double *__restrict__ partials)
+{
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = __ldg(tiles + t);
+        const EnsInst I = inst[tl.x];
+        const int x = tl.y + threadIdx.x, y = tl.z + threadIdx.y;
+        double v[kEnsAcc] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (x < I.nx && y < I.ny) {
+            // phi(t_n) exactly as lbm_ensemble_get_phi forms it (FP32 sum in k order)
+            const long long own = (long long)y * I.pitch + x;
+            const float *f = parity ? I.pop[1] : I.pop[0];
+            float s = f[own];
+#pragma unroll
+            for (int k = 1; k < 9; ++k) s += f[k * I.plane + own];
+            const double ph = (double)s;
+            if (!isfinite(ph)) {
+                v[6] = 1.0;
+            } else {
+                v[0] = ph;
+                v[7] = ph * ph;
+                v[5] = fabs(ph);
+                if (ref) {
+                    const double r = ref[I.phi_off + (long long)y * I.nx + x], d = ph - r;
+                    v[1] = fabs(d);
+                    v[2] = fabs(r);
+                    v[3] = d * d;
+                    v[4] = r * r;
+                }
+            }
+        }
+        ens_block_reduce(v, partials + (size_t)t * kEnsAcc);
+    }
+}
+
+__global__ void __launch_bounds__(kEnsThreads)
+k_ens_reduce2(const double *__restrict__ partials, const int *__restrict__ tile_begin, double *__restrict__ out)
+{
+    const int i = blockIdx.x;
+    const int b0 = tile_begin[i], b1 = tile_begin[i + 1];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    double v[kEnsAcc] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = b0 + tid; b < b1; b += kEnsThreads)
+#pragma unroll
+        for (int j = 0; j < kEnsAcc; ++j) v[j] = ens_combine(j, v[j], partials[(size_t)b * kEnsAcc + j]);
+    ens_block_reduce(v, out + (size_t)i * kEnsAcc);
+}
+
+cudaError_t ens_launch_reduce(const lbm_ensemble_s *e, const double *ref, double *out, cudaStream_t st)
+{
+    dim3 block(kEnsTile, kEnsRows);
+    k_ens_reduce1<<<e->grid, block, 0, st>>>(e->d_inst, e->d_tiles, e->ntiles, e->parity, ref, e->partials);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_ens_reduce2<<<e->count, block, 0, st>>>(e->partials, e->d_tile_begin, out);
+    return cudaGetLastError();
+}
+
 #define LBM_ENS_DISPATCH(KEY, CALL)                    \
     switch (KEY) {                                     \
     case 0: CALL(0, 0); break;                         \

@@ -54,6 +54,8 @@ struct lbm_ensemble_s {
     cudaGraphExec_t exec = nullptr;
     int graph_steps = 0, graph_parity = 0;
     int *err = nullptr;             // index-fault word of checked builds
+    double *partials = nullptr;     // per-tile statistics (8 doubles per 32 x 8 tile)
+    int *d_tile_begin = nullptr;    // device copy of tile_begin
 };
 
 namespace lbm {
@@ -63,5 +65,7 @@ int ens2_occupancy_blocks(int family);
 constexpr int kEns2Tile = 30;       // two-step tiles: 30 x 30 outputs
 cudaError_t ens_launch_init(const lbm_ensemble_s *e, const void *phi, int in_prec, cudaStream_t st);
 cudaError_t ens_launch_get_phi(const lbm_ensemble_s *e, void *out, int out_prec, cudaStream_t st);
+// the eight statistics of every instance into out (count x 8 doubles)
+cudaError_t ens_launch_reduce(const lbm_ensemble_s *e, const double *ref, double *out, cudaStream_t st);
 int ens_occupancy_blocks(int family);
 }  // namespace lbm

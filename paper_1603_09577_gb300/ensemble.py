@@ -7,7 +7,7 @@ import ctypes
 import torch
 
 from . import _lib as C
-from .solver import _prec_of, _ptr, _stream
+from .solver import REDUCE_KEYS, _prec_of, _ptr, _stream
 
 
 class Ensemble:
@@ -83,6 +83,26 @@ class Ensemble:
         out = torch.empty(self.nodes, dtype=dtype, device=self.device)
         C.check(self.lib.lbm_ensemble_get_phi(self.h, _ptr(out), _prec_of(out), _stream(stream)))
         return out
+
+    def reduce_async(self, ref: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+        """Per-instance statistics (sum, abs_err, abs_ref, sq_err, sq_ref, max_abs,
+        nonfinite, sum_sq) as a (count, 8) float64 tensor on the device; ref: the
+        packed reference field (FP64) or None."""
+        if out is None:
+            out = torch.empty((len(self.sizes), 8), dtype=torch.float64, device=self.device)
+        assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() == 8 * len(self.sizes)
+        if ref is not None:
+            ref = ref.to(device=self.device, dtype=torch.float64).contiguous()
+            assert ref.numel() == self.nodes
+            self._ref = ref
+        C.check(self.lib.lbm_ensemble_reduce(self.h, _ptr(ref) if ref is not None else None, _ptr(out),
+                                             _stream(stream)))
+        return out
+
+    def reduce(self, ref: torch.Tensor | None = None) -> list[dict]:
+        """reduce_async, read back: one dict per instance (keys of Solver.reduce)."""
+        return [dict(zip(REDUCE_KEYS, row)) for row in self.reduce_async(ref).cpu().tolist()]
 
 
 def shard(instances, rank: int, world: int) -> list[int]:

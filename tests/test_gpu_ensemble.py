@@ -124,3 +124,41 @@ def test_ensemble_full_workload(spp):
     for i in order:
         ref = oracle_phi(inst[i], phis[i], 1000)
         assert rel(out[i].numpy(), ref) <= 1e-5, (i, rel(out[i].numpy(), ref))
+
+
+def test_ensemble_per_instance_reductions():
+    """lbm_ensemble_reduce: every instance's eight statistics equal their
+    definitions evaluated with numpy on the returned phi (sums to 1e-12, the
+    maximum and the non-finite count exactly), the GRE against the oracle stays at
+    the parity level, repeated calls agree bit for bit, and a NaN placed in one
+    instance is counted there alone."""
+    inst = small_instances()
+    phis = [W.ensemble_phi0(d) for d in inst]
+    e = Ensemble(inst, steps_per_pass=2)
+    e.set_phi(e.pack(phis))
+    e.step(60)
+    refs = [oracle_phi(d, p0, 60) for d, p0 in zip(inst, phis)]
+    packed_ref = e.pack(refs)
+    out = e.reduce_async(packed_ref)
+    again = e.reduce_async(packed_ref, out=torch.empty_like(out))
+    assert torch.equal(out, again)
+    stats = e.reduce(packed_ref)
+    got = e.unpack(e.phi().cpu())
+    for st, g, r in zip(stats, got, refs):
+        g = g.numpy()
+        d = g - r
+        assert st["nonfinite"] == 0.0
+        assert st["max_abs"] == np.abs(g).max()
+        for key, val in (("sum", g.sum()), ("sum_sq", (g * g).sum()), ("abs_err", np.abs(d).sum()),
+                         ("abs_ref", np.abs(r).sum()), ("sq_err", (d * d).sum()), ("sq_ref", (r * r).sum())):
+            assert abs(st[key] - val) <= 1e-12 * abs(val) + 1e-300, (key, st[key], val)
+        assert st["abs_err"] / st["abs_ref"] <= 1e-5
+    plain = e.reduce()
+    for st in plain:
+        assert st["abs_err"] == st["abs_ref"] == st["sq_err"] == st["sq_ref"] == 0.0
+    # a NaN in instance 3's initial field is counted in instance 3 only
+    bad = [p.copy() for p in phis]
+    bad[3][5, 7] = np.nan
+    e.set_phi(e.pack(bad))
+    counts = [st["nonfinite"] for st in e.reduce()]
+    assert counts == [0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]
