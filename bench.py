@@ -299,6 +299,30 @@ def run_ensemble(args):
         ms_pgrid = timed(job_graph_persistent_grid, max(1, args.steps // 2), side)
         ms_sep = timed(job_launches, max(1, args.steps // 2), side)
         ms_g1 = timed(job_graph_one_step, max(1, args.steps // 2), side)
+
+        # end to end through the public API: phi0 from pinned host memory, the
+        # replayed steps, every instance's statistics back to the host
+        host_in = packed.cpu().pin_memory()
+        dev_in = torch.empty_like(packed)
+        stats = torch.empty((len(inst), 8), dtype=torch.float64, device="cuda")
+        host_stats = torch.empty((len(inst), 8), dtype=torch.float64).pin_memory()
+
+        def job_e2e():
+            dev_in.copy_(host_in, non_blocking=True)
+            e.set_phi(dev_in)
+            for _ in range(steps // 100):
+                e.replay()
+            e.reduce_async(out=stats)
+            host_stats.copy_(stats, non_blocking=True)
+            side.synchronize()
+
+        job_e2e()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            job_e2e()
+        e2e_ms = 1e3 * (time.perf_counter() - w0) / args.steps
+        mass0 = torch.tensor([float(t.double().sum()) for t in e.unpack(host_in)], dtype=torch.float64)
+        mass_drift = float(((host_stats[:, 0] - mass0).abs() / mass0.abs()).max())
     nodes = sum(d["nx"] * d["ny"] for d in all_inst)         # every rank's instances
     val = nodes * steps / (ms_graph / 1e3) / 1e6
     if world > 1:
@@ -330,6 +354,11 @@ def run_ensemble(args):
            "persistent_no_graph_mlups": nodes_r0 * steps / (ms_pers / 1e3) / 1e6,
            "one_launch_per_instance_mlups": nodes_r0 * steps / (ms_sep / 1e3) / 1e6,
            "graph_speedup_vs_per_instance": ms_sep / ms_graph,
+           "e2e": {"value": nodes_r0 * steps / (e2e_ms / 1e3) / 1e6, "unit": "MLUPS",
+                   "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
+                   "d2h_bytes_per_step": int(host_stats.numel() * host_stats.element_size()),
+                   "read_back": "per-instance FP64 statistics (lbm_ensemble_reduce)",
+                   "max_relative_mass_drift": mass_drift},
            "gpu_launches": args.steps * (1 + steps // args.ens_spp)}
     if clocks is not None:
         out["clocks"] = clocks
