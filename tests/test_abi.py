@@ -266,3 +266,50 @@ def test_grids_beyond_the_index_range_are_rejected():
     d.nx, d.ny, d.nz, d.prec = 2048, 1024, 1025, C.LBM_F32
     n = ctypes.c_size_t()
     assert C.lib().lbm3_workspace_size(ctypes.byref(d), ctypes.byref(n)) == C.LBM_EINVAL
+
+
+def ens_sizes(pairs):
+    n = len(pairs)
+    return n, (ctypes.c_int * n)(*[a for a, _ in pairs]), (ctypes.c_int * n)(*[b for _, b in pairs])
+
+
+def test_ensemble_host_validation():
+    """The ensemble's workspace size (tables, tile partials of the per-instance
+    reductions, populations) and every argument check of lbm_ensemble_create
+    that runs before device work; calls on a null ensemble are rejected."""
+    L = C.lib()
+    n = ctypes.c_size_t()
+    cnt, nx, ny = ens_sizes([(64, 40), (33, 70)])
+    assert L.lbm_ensemble_workspace_size(cnt, nx, ny, ctypes.byref(n)) == C.LBM_OK
+    pops = sum(2 * (((9 * ((a + 31) // 32 * 32) * b * 4) + 255) // 256 * 256) for a, b in [(64, 40), (33, 70)])
+    tiles = 2 * 5 + 2 * 9                           # 32 x 8 tiles of the two instances
+    assert n.value >= pops + 64 * tiles
+    for bad in ([(1, 40)], [(64, 1)]):
+        c, x, y = ens_sizes(bad)
+        assert L.lbm_ensemble_workspace_size(c, x, y, ctypes.byref(n)) == C.LBM_EINVAL
+    assert L.lbm_ensemble_workspace_size(0, nx, ny, ctypes.byref(n)) == C.LBM_EINVAL
+    assert L.lbm_ensemble_workspace_size(cnt, None, ny, ctypes.byref(n)) == C.LBM_EINVAL
+    assert L.lbm_ensemble_workspace_size(cnt, nx, ny, ctypes.byref(n)) == C.LBM_OK
+    ws = FakeWorkspace(n.value)
+    e = ctypes.c_void_p()
+
+    def create(cs, ptr=ws.ptr, size=n.value):
+        arr = (C.Coeffs * len(cs))(*cs)
+        return L.lbm_ensemble_create(ctypes.byref(e), cnt, nx, ny, arr, ctypes.c_void_p(ptr), size)
+
+    good = coeffs(diff=1)
+    assert create([good, good], ptr=ws.ptr + 8) == C.LBM_EINVAL               # misaligned workspace
+    assert create([good, good], size=n.value - 1) == C.LBM_EINVAL             # too small
+    assert create([good, coeffs(diff=2)]) == C.LBM_EINVAL                      # mixed families
+    assert create([good, coeffs(diff=1, s=[1.0, 2.0, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1])]) == C.LBM_EINVAL
+    assert create([good, coeffs(diff=1, K=[0.01, 0.02, 0.01])]) == C.LBM_EINVAL
+    assert create([good, coeffs(diff=1, r1=0.1)]) == C.LBM_EUNSUPPORTED       # no source terms
+    assert create([good, coeffs(diff=1, cfree=1)]) == C.LBM_EUNSUPPORTED
+    assert create([coeffs(conv=2), coeffs(conv=2)]) == C.LBM_EINVAL           # families 0-1 only
+    out = ctypes.c_void_p(16)
+    assert L.lbm_ensemble_step(None, 1, 0, None) == C.LBM_EINVAL
+    assert L.lbm_ensemble_reduce(None, None, out, None) == C.LBM_EINVAL
+    assert L.lbm_ensemble_get_phi(None, out, C.LBM_F64, None) == C.LBM_EINVAL
+    assert L.lbm_ensemble_set_phi(None, out, C.LBM_F64, None) == C.LBM_EINVAL
+    assert L.lbm_ensemble_replay(None, None) == C.LBM_EINVAL
+    assert L.lbm_ensemble_configure(None, 2) == C.LBM_EINVAL
