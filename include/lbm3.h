@@ -70,6 +70,13 @@ int lbm3_set_phi(lbm3_handle h, const void *dev_phi, int prec, void *stream);
    alternate between the two population buffers and need no function
    attributes, so a stream capture of an even nsteps replays consistently. */
 int lbm3_step(lbm3_handle h, int nsteps, void *stream);
+/* Checkpoint / resume: the state is lbm3_state_bytes bytes (the 19 population
+   planes and, for LBM_BF16S, the shift plane). dev_dst / dev_src: device
+   buffers of that size, owned by the caller. Asynchronous on `stream`.
+   lbm3_load also serves as the initial condition (no lbm3_set_phi needed). */
+int lbm3_state_bytes(lbm3_handle h, size_t *bytes);
+int lbm3_save(lbm3_handle h, void *dev_dst, void *stream);
+int lbm3_load(lbm3_handle h, const void *dev_src, void *stream);
 /* phi(t_n) into dev_out (nx*ny*nz values of `prec`). */
 int lbm3_get_phi(lbm3_handle h, void *dev_out, int prec, void *stream);
 /* The eight FP64 statistics of lbm_reduce over phi(t_n) (dev_ref: nx*ny*nz

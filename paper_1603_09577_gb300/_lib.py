@@ -91,6 +91,9 @@ SIGNATURES = {
     "lbm3_set_phi": [_VP, _VP, _I, _VP],
     "lbm3_step": [_VP, _I, _VP],
     "lbm3_get_phi": [_VP, _VP, _I, _VP],
+    "lbm3_state_bytes": [_VP, ctypes.POINTER(_SZ)],
+    "lbm3_save": [_VP, _VP, _VP],
+    "lbm3_load": [_VP, _VP, _VP],
     "lbm3_reduce": [_VP, _VP, _VP, _VP],
     "lbm3_debug_flags": [_VP, ctypes.POINTER(_I), _VP],
     "lbm_ensemble_workspace_size": [_I, _VP, _VP, ctypes.POINTER(_SZ)],

@@ -271,6 +271,7 @@ struct lbm3_solver {
     double *partials = nullptr;
     int *err = nullptr;
     int cur = 0;
+    size_t state_bytes = 0;               // populations, then the BF16S shift plane (contiguous)
     double G[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -459,6 +460,7 @@ int lbm3_create(lbm3_handle *h, const lbm3_desc *desc, void *dev_workspace, size
     s->staging = (double *)(ws + L.off_stage);
     s->partials = (double *)(ws + L.off_part);
     s->err = (int *)(ws + L.off_err);
+    s->state_bytes = L.pop_bytes + L.h_bytes;
     *h = s;
     return LBM_OK;
 }
@@ -511,6 +513,34 @@ int lbm3_step(lbm3_handle h, int nsteps, void *stream)
         if (int rc = cuda_check(launch3(h, nullptr, 0, (cudaStream_t)stream), "lbm3_step")) return rc;
         h->cur ^= 1;
     }
+    return LBM_OK;
+}
+
+int lbm3_state_bytes(lbm3_handle h, size_t *bytes)
+{
+    if (!h) return fail(LBM_EINVAL, "null lbm3 handle");
+    if (!bytes) return fail(LBM_EINVAL, "null size pointer");
+    *bytes = h->state_bytes;
+    return LBM_OK;
+}
+
+int lbm3_save(lbm3_handle h, void *dev_dst, void *stream)
+{
+    if (!h) return fail(LBM_EINVAL, "null lbm3 handle");
+    if (!h->phi_set) return fail(LBM_EINVAL, "lbm3_set_phi has not been called");
+    if (!dev_dst) return fail(LBM_EINVAL, "null destination");
+    return cuda_check(cudaMemcpyAsync(dev_dst, h->pop[h->cur], h->state_bytes, cudaMemcpyDeviceToDevice,
+                                      (cudaStream_t)stream), "lbm3_save");
+}
+
+int lbm3_load(lbm3_handle h, const void *dev_src, void *stream)
+{
+    if (!h) return fail(LBM_EINVAL, "null lbm3 handle");
+    if (!dev_src) return fail(LBM_EINVAL, "null source");
+    if (int rc = cuda_check(cudaMemcpyAsync(h->pop[h->cur], dev_src, h->state_bytes, cudaMemcpyDeviceToDevice,
+                                            (cudaStream_t)stream), "lbm3_load"))
+        return rc;
+    h->phi_set = 1;
     return LBM_OK;
 }
 

@@ -55,6 +55,24 @@ class Solver3:
         C.check(self.lib.lbm3_step(self.h, int(n), _stream(stream)))
         return self
 
+    # -- checkpoint / resume -------------------------------------------------------
+    def state_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        C.check(self.lib.lbm3_state_bytes(self.h, ctypes.byref(n)))
+        return n.value
+
+    def save(self, dst: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if dst is None:
+            dst = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        assert dst.is_cuda and dst.numel() * dst.element_size() >= self.state_bytes()
+        C.check(self.lib.lbm3_save(self.h, _ptr(dst), _stream(stream)))
+        return dst
+
+    def load(self, src: torch.Tensor, stream=None):
+        assert src.is_cuda and src.numel() * src.element_size() >= self.state_bytes()
+        C.check(self.lib.lbm3_load(self.h, _ptr(src), _stream(stream)))
+        return self
+
     # -- CUDA graphs -------------------------------------------------------------
     def capture(self, nsteps: int):
         """Record nsteps (even, so that every replay ends on the buffer it

@@ -255,6 +255,19 @@ def test_d3q19_descriptions_and_coefficients():
     c.se = 2.0
     assert L.lbm3_set_coeffs(h, ctypes.byref(c)) == C.LBM_EINVAL
     assert L.lbm3_step(h, 1, None) == C.LBM_EINVAL           # no initial phi
+    assert L.lbm3_save(h, ctypes.c_void_p(16), None) == C.LBM_EINVAL   # nothing to save yet
+    assert L.lbm3_load(h, None, None) == C.LBM_EINVAL
+    sb = ctypes.c_size_t()
+    assert L.lbm3_state_bytes(h, ctypes.byref(sb)) == 0
+    assert sb.value == (19 * 10 * 8 * 64 * 4 + 255) // 256 * 256       # 19 planes, x pitch 64
+    L.lbm3_destroy(h)
+    db = d3(prec=C.LBM_BF16S)
+    L.lbm3_workspace_size(ctypes.byref(db), ctypes.byref(n))
+    wb = FakeWorkspace(n.value)
+    assert L.lbm3_create(ctypes.byref(h), ctypes.byref(db), ctypes.c_void_p(wb.ptr), n.value) == 0
+    assert L.lbm3_state_bytes(h, ctypes.byref(sb)) == 0
+    plane = 10 * 8 * 64
+    assert sb.value == (19 * plane * 2 + 255) // 256 * 256 + (plane * 4 + 255) // 256 * 256   # + the shift plane
     L.lbm3_destroy(h)
 
 

@@ -86,3 +86,23 @@ def test_d3q19_replays_from_a_cuda_graph(prec):
     assert rel(s.phi().cpu().numpy(), ref) <= TOL[prec]
     with pytest.raises(ValueError):
         s.capture(5)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16s"])
+def test_d3q19_checkpoint_resume(prec):
+    """lbm3_save / lbm3_load: resuming from the state saved at step 10 repeats
+    steps 11..20 bit for bit (the BF16S shift plane travels with the state), and
+    a fresh solver loaded from the checkpoint continues identically."""
+    nx, ny, nz, coef = CASES[2]
+    rng = np.random.default_rng(9)
+    phi0 = torch.from_numpy(rng.uniform(0.2, 0.8, (nz, ny, nx))).cuda()
+    s = Solver3(nx, ny, nz, prec=prec).set_coeffs(**coef).set_phi(phi0).step(10)
+    ck = s.save()
+    s.step(10)
+    first = s.phi().cpu()
+    s.load(ck).step(10)
+    assert torch.equal(first, s.phi().cpu())
+    t = Solver3(nx, ny, nz, prec=prec).set_coeffs(**coef).load(ck).step(10)
+    assert torch.equal(first, t.phi().cpu())
+    ref = D.run(D.Spec3(nx=nx, ny=ny, nz=nz, **coef), phi0.cpu().numpy(), 20)
+    assert rel(first.numpy(), ref) <= TOL[prec]
