@@ -314,3 +314,61 @@ def test_buckley_leverett_mass_and_bounds():
     phi = O.run_x(sp, phi0, int(round(0.5 / dt)))
     assert abs(phi.sum() - phi0.sum()) < 1e-12 * phi0.sum()
     assert phi.min() > -1e-12 and phi.max() < 1.0
+
+
+def test_scheme_a_spectral_exact_with_linear_source():
+    """Scheme A on a periodic grid with B = u phi, D = phi I and R = r1 phi is a
+    shift-invariant linear map of the state (post-collision populations, stored
+    phi(t_n)), so in Fourier space every wavevector evolves by a 10 x 10 matrix:
+    f* <- [L + 3/2 r 1^T] D(q) f* - 1/2 r phi_prev and phi_prev <- 1^T D(q) f*,
+    with D(q) the pull phases, L the relaxation f - M0^-1 S M0 (f - a 1^T f),
+    and r_k = w_k (1 + c_k . Btilde / c_s^2) r1 with Btilde = (I - A/2) u
+    (Eq. 28, gamma = 0). The start is f* = (a + r) phi0 (Eq. 40, then one
+    collision with a zero time difference). M0's rows are built here from their
+    polynomial definitions (Eq. 15) in our own velocity order. Its matrix power
+    must give the oracle's phi(t_N) to rounding, with distinct rates everywhere
+    and an anisotropic K, so the bookkeeping of the previous level, the sign
+    and size of the backward difference, and Btilde are all pinned."""
+    import itertools
+
+    nx, ny, nsteps = 14, 9, 30
+    u = np.array([0.06, -0.04])
+    K3 = (0.03, 0.01, 0.02)
+    s = (1.0, 1.2, 1.3, 0.0, 0.9, 0.0, 1.1, 1.15, 1.05)
+    r1 = -0.05
+    c = np.array(list(itertools.product((-1, 0, 1), repeat=2)), dtype=np.float64)   # (9, 2), our order
+    cx, cy = c[:, 0], c[:, 1]
+    n2 = cx * cx + cy * cy
+    w = np.where(n2 == 0, 4 / 9, np.where(n2 == 1, 1 / 9, 1 / 36))
+    M = np.stack([np.ones(9), 3 * n2 - 4, 4 - 10.5 * n2 + 4.5 * n2 * n2, cx, (3 * n2 - 5) * cx,
+                  cy, (3 * n2 - 5) * cy, cx * cx - cy * cy, cx * cy])            # rho e eps jx qx jy qy pxx pxy
+    A = np.linalg.inv(3.0 * np.array([[K3[0], K3[1]], [K3[1], K3[2]]]) + 0.5 * np.eye(2))
+    S = np.diag(np.array(s, dtype=np.float64))
+    S[3, 3], S[3, 5], S[5, 3], S[5, 5] = A[0, 0], A[0, 1], A[1, 0], A[1, 1]
+    P = np.linalg.solve(M, S @ M)
+    cu = c @ u
+    a = w * (1 + 3 * cu + 4.5 * (cu * cu - (u @ u) / 3))                        # f^eq per unit phi
+    Bt = u - 0.5 * A @ u
+    r = w * (1 + 3 * (c @ Bt)) * r1
+    one = np.ones(9)
+    L = np.eye(9) - P @ (np.eye(9) - np.outer(a, one))
+
+    rng = np.random.default_rng(41)
+    phi0 = W.jacobi_smooth(rng.uniform(0.2, 0.8, (ny, nx)), 1)
+    F = np.fft.fft2(np.outer(a + r, phi0.ravel()).reshape(9, ny, nx), axes=(1, 2)).reshape(9, -1).T
+    G = np.fft.fft2(phi0).reshape(-1)
+    qy, qx = np.meshgrid(2 * np.pi * np.fft.fftfreq(ny), 2 * np.pi * np.fft.fftfreq(nx), indexing="ij")
+    shift = np.exp(-1j * (np.outer(qx.ravel(), cx) + np.outer(qy.ravel(), cy)))    # (nq, 9)
+    nq = shift.shape[0]
+    T = np.zeros((nq, 10, 10), dtype=complex)
+    T[:, :9, :9] = (L + 1.5 * np.outer(r, one))[None] * shift[:, None, :]
+    T[:, :9, 9] = -0.5 * r
+    T[:, 9, :9] = shift
+    state = np.concatenate([F, G[:, None]], axis=1)
+    out = np.einsum("qij,qj->qi", np.linalg.matrix_power(T, nsteps), state)
+    phiN = np.fft.ifft2(out[:, 9].reshape(ny, nx)).real
+
+    sp = O.Spec(nx=nx, ny=ny, conv=0, u=tuple(u), diff=0, K=K3, s=s, r1=r1, scheme=1)
+    got = O.run_x(sp, phi0, nsteps)
+    assert rel(got, phiN) <= 1e-12, rel(got, phiN)
+    assert rel(phiN, phi0) > 1e-2                       # the source and the flow changed phi substantially
