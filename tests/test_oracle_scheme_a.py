@@ -372,3 +372,21 @@ def test_scheme_a_spectral_exact_with_linear_source():
     got = O.run_x(sp, phi0, nsteps)
     assert rel(got, phiN) <= 1e-12, rel(got, phiN)
     assert rel(phiN, phi0) > 1e-2                       # the source and the flow changed phi substantially
+
+
+def test_burgers_fisher_peclet_remark_sec32():
+    """Sec. 3.2 remarks that the GREs at Pe = 600 (kappa = 0.02) lie below those
+    at Pe = 120 (kappa = 0.1) because s3 and s5 are then nearer 1. The paper does
+    not state c; with c = 12, where s3 = s5 = 1 exactly at Pe = 600, the oracle
+    reproduces the remark on the paper's 301^2 lattice at T = 1 by a factor of
+    about 7 (at the c = 40 of the other Burgers-Fisher tests both GREs are near
+    8e-5 and the order is reversed, so the remark also tells which time steps
+    the paper used)."""
+    out = {}
+    for kappa in (0.1, 0.02):
+        bf = W.burgers_fisher(300, 1.0, c=12.0, kappa=kappa)
+        sp = bf_spec(bf, 1)
+        out[kappa] = (gre(O.run_x(sp, bf["phi0"], bf["steps"], bf["bvals"]), bf["exact"]), 1 / (0.5 + 3 * bf["K"]))
+    (e120, s120), (e600, s600) = out[0.1], out[0.02]
+    assert abs(s600 - 1.0) < 1e-12 and abs(s120 - 1.0) > 0.5
+    assert e600 < e120 / 5, (e600, e120)
