@@ -36,10 +36,8 @@ import workloads as W  # noqa: E402
 WORKLOAD = "aniso_dirichlet_4096"
 BYTES_PER_UPDATE = {"f32": 72, "bf16s": 44, "f64": 144}
 # FP64 path: FP64 thread instructions per node update of k_step<F64> on this workload (ncu counts: 60 DADD +
-# 36 DFMA + 22 DMUL), and the FP64 pipe's rate on GB300 (2 thread instructions per SM per clock: 152 SMs at
-# the 2070 MHz the runs hold), the ALU roof the FP64 kernel meets before HBM
+# 36 DFMA + 22 DMUL); its roof is the FP64 pipe's rate, measured in the same run by the DFMA probe
 FP64_INST_PER_UPDATE = 118
-FP64_PEAK_GINST = 2 * 152 * 2.070
 KERNEL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
               for f in ("kernels_step.cu", "kernels_step_vec.cu", "kernels_step2.cuh", "kernels_step2_f32.cu",
                         "kernels_step2_bf16.cu", "lbm_device.cuh")]
@@ -68,6 +66,8 @@ def parse():
                     help="use --variant/--block-rows/--spp as given instead of the autotuner's choice")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sub-records (BF16S, FP64, adjoint, ensemble, 1024^2 Burgers) of the default run")
     ap.add_argument("--ens-count", type=int, default=256, help="instances of the ensemble workload")
     ap.add_argument("--ens-spp", type=int, default=2, help="time steps per persistent ensemble launch (1 or 2)")
     ap.add_argument("--bf-spp", type=int, default=2, help="time steps per launch of the Burgers-Fisher workload")
@@ -676,6 +676,294 @@ def run_gaussian3d(args):
     print(json.dumps(out), flush=True)
 
 
+def fp64_peak_probe():
+    """The FP64 pipe's measured rate (G thread instructions/s): the DFMA probe of
+    the library on every SM (8 resident blocks of 256 threads each), best of 5
+    launches timed with CUDA events, with the SM clock sampled meanwhile."""
+    import ctypes
+
+    import torch
+
+    from paper_1603_09577_gb300 import _lib as C
+    L = C.lib()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, threads, iters = sms * 8, 256, 4096
+    sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    n = ctypes.c_longlong()
+
+    def launch():
+        C.check(L.lbm_probe_fp64(blocks, threads, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(n),
+                                 ctypes.c_void_p(st.cuda_stream)))
+
+    launch()
+    torch.cuda.synchronize()
+    clk = clocks_sampler()
+    best = min(timed(launch, 4, st) for _ in range(5))
+    clocks = clocks_summary(clk)
+    ginst = n.value / (best / 1e3) / 1e9
+    mhz = clocks["sm_mhz"] if clocks else None
+    out = {"value": ginst, "unit": "G FP64 thread instructions/s",
+           "how": f"lbm_probe_fp64: {blocks} blocks x {threads} threads x {iters} iterations x 8 independent DFMA "
+                  f"chains, best of 5 x 4 launches (CUDA events)", "sms": sms}
+    if mhz:
+        out["per_sm_per_clock"] = ginst * 1e3 / (sms * mhz)
+    if clocks is not None:
+        out["clocks"] = clocks
+    return out
+
+
+def c3_measure(prec, cfg, lbm_steps, steps, warmup, warm_lbm_steps=None):
+    """The 4096^2 Dirichlet job (set_phi, lbm_steps steps, mass reduction) in one
+    storage precision: MLUPS over `steps` timed jobs, the average launch time of
+    the step kernel, clocks, and the final phi (FP64, host)."""
+    import torch
+
+    from paper_1603_09577_gb300 import Solver
+    p = W.params(WORKLOAD)
+    n = p["nx"]
+    phi0 = torch.from_numpy(W.phi0_aniso(n, seed=3).astype(np.float64 if prec == "f64" else np.float32)).cuda()
+    s = Solver(n, n, prec=prec, bc=("abb", "abb"), phi_wall=p["phi_wall"], **cfg)
+    s.set_coeffs(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"], s=W.s9(), r0=p["r0"], r1=p["r1"])
+    red = torch.zeros(8, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        s.set_phi(phi0)
+        s.step(warm_lbm_steps or lbm_steps)
+        s.reduce_async(out=red)
+    torch.cuda.synchronize()
+    clk = clocks_sampler()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for a, b in ev:
+        s.set_phi(phi0)
+        a.record(st)
+        s.step(lbm_steps)
+        b.record(st)
+        s.reduce_async(out=red)
+    t1.record(st)
+    torch.cuda.synchronize()
+    clocks = clocks_summary(clk)
+    ms = t0.elapsed_time(t1) / steps
+    spp = cfg.get("steps_per_pass", 1)
+    launches = lbm_steps // spp + lbm_steps % spp
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev) / launches
+    phi = s.phi().cpu().numpy()
+    del s
+    torch.cuda.empty_cache()
+    return {"mlups": n * n * lbm_steps / (ms / 1e3) / 1e6, "ms_per_job": ms, "avg_launch_ms": launch_ms,
+            "launches_per_job": launches, "clocks": clocks, "phi": phi}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def extra_c3(prec, lbm_steps, steps, warmup, fp64_phi, peak, src):
+    """Sub-record of the 4096^2 workload in BF16S storage (autotuned launch)."""
+    from paper_1603_09577_gb300 import tune
+    p = W.params(WORKLOAD)
+    cfg = tune.tune(p["nx"], p["ny"], prec, bc=("abb", "abb"), conv=p["conv"], diff=p["diff"])
+    assert cfg in tune.candidates(p["nx"], prec), cfg
+    r = c3_measure(prec, cfg, lbm_steps, steps, warmup)
+    cells = p["nx"] * p["ny"]
+    achieved = BYTES_PER_UPDATE[prec] * cells / (r["avg_launch_ms"] / 1e3) / 1e9
+    out = {"workload": f"{WORKLOAD}, {lbm_steps} steps per job, storage {prec}", "value": r["mlups"],
+           "unit": "MLUPS", "ms_per_job": r["ms_per_job"], "timed_jobs": steps, "config": cfg,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "algorithmic_bytes_per_launch": BYTES_PER_UPDATE[prec] * cells,
+                        "avg_launch_ms": r["avg_launch_ms"], "peak_source": src,
+                        "one_step_roof_mlups": peak * 1e3 / BYTES_PER_UPDATE[prec]},
+           "rel_l2_vs_fp64_path": rel_l2(r["phi"], fp64_phi) if fp64_phi is not None else None,
+           "clocks": r["clocks"]}
+    return out, r["phi"]
+
+
+def extra_adjoint(warmup):
+    """Sub-record of the differentiable 512^2 workload: adjoint step over forward
+    step (one launch each), and whole backward pass (checkpoints every 50,
+    recomputation included) over the forward pass, FP32 forward with FP64
+    gradient accumulation."""
+    import ctypes
+
+    import torch
+
+    from paper_1603_09577_gb300 import Solver, adjoint
+    from paper_1603_09577_gb300 import _lib as C
+    p = W.params("adjoint_512")
+    Kf, phi0, tgt = W.adjoint_inputs(512, seed=4)
+    st = torch.cuda.current_stream()
+    clk = clocks_sampler()
+    s = Solver(512, 512, prec="f32", per_cell_K=True)
+    s.set_coeffs(conv=0, u=p["u"], diff=0, s=W.s9())
+    s.set_K_field(torch.from_numpy(Kf).cuda())
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    state = s.save()
+    n = 200
+    s.step(10)
+    ms_fwd = timed(lambda: s.step(1), n, st)
+    size = ctypes.c_size_t()
+    C.check(s.lib.lbm_adjoint_workspace_size(s.h, ctypes.byref(size)))
+    ws = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+    g = torch.from_numpy(tgt).cuda()
+    C.check(s.lib.lbm_adjoint_begin(s.h, ctypes.c_void_p(ws.data_ptr()), size.value, ctypes.c_void_p(g.data_ptr()),
+                                    C.LBM_F64, ctypes.c_void_p(st.cuda_stream)))
+    adj = lambda: C.check(s.lib.lbm_adjoint_step(s.h, ctypes.c_void_p(state.data_ptr()),  # noqa: E731
+                                                 ctypes.c_void_p(st.cuda_stream)))
+    adj()
+    ms_adj = timed(adj, n, st)
+    p0 = torch.from_numpy(phi0).cuda().requires_grad_(True)
+    K = torch.from_numpy(Kf).cuda().requires_grad_(True)
+    u = torch.tensor(p["u"], dtype=torch.float64, device="cuda", requires_grad=True)
+    t = torch.from_numpy(tgt).cuda()
+    for _ in range(max(1, warmup)):
+        out = adjoint.run(p0, K, u, p["steps"], p["ckpt_every"], "f32", W.s9())
+        (0.5 * ((out - t) ** 2).sum()).backward()
+    torch.cuda.synchronize()
+    fw, bw = [], []
+    for _ in range(3):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(st)
+        out = adjoint.run(p0, K, u, p["steps"], p["ckpt_every"], "f32", W.s9())
+        loss = 0.5 * ((out - t) ** 2).sum()
+        b.record(st)
+        loss.backward()
+        c.record(st)
+        torch.cuda.synchronize()
+        fw.append(a.elapsed_time(b))
+        bw.append(b.elapsed_time(c))
+    clocks = clocks_summary(clk)
+    fwd_ms, bwd_ms = statistics.median(fw), statistics.median(bw)
+    return {"workload": "adjoint_512: linear anisotropic CDE, per-node K(x), u=(0.03,0), 512x512, 500 steps, "
+                        "checkpoints every 50, FP32 forward, FP64 gradient accumulation",
+            "adjoint_step_over_forward_step": ms_adj / ms_fwd, "forward_step_ms": ms_fwd, "adjoint_step_ms": ms_adj,
+            "forward_pass_ms": fwd_ms, "backward_pass_ms": bwd_ms, "backward_over_forward_pass": bwd_ms / fwd_ms,
+            "target": "adjoint step <= 3 x forward step", "clocks": clocks}
+
+
+def extra_ensemble(warmup, steps):
+    """Sub-record of the 256-instance ensemble (1000 steps per job): two steps
+    per launch replayed from a CUDA graph, against one launch per instance and
+    step (256 launches per step)."""
+    import torch
+
+    from paper_1603_09577_gb300.ensemble import Ensemble
+    inst = W.ensemble(count=256)
+    lbm_steps = 1000
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        e = Ensemble(inst, steps_per_pass=2)
+        packed = e.pack([W.ensemble_phi0(d) for d in inst], dtype=torch.float32)
+        e.set_phi(packed)
+        e.capture(100)
+
+        def job_graph():
+            e.set_phi(packed)
+            for _ in range(lbm_steps // 100):
+                e.replay()
+
+        e1 = Ensemble(inst, steps_per_pass=1)
+
+        def job_launches():
+            e1.set_phi(packed)
+            e1.step(lbm_steps, mode=1)
+
+        for _ in range(warmup):
+            job_graph()
+        job_launches()
+        torch.cuda.synchronize()
+        clk = clocks_sampler()
+        ms_graph = timed(job_graph, steps, side)
+        clocks = clocks_summary(clk)
+        ms_sep = timed(job_launches, max(1, steps // 2), side)
+        out_phi = e.phi()
+        finite = bool(torch.isfinite(out_phi).all())
+    nodes = e.nodes
+    del e, e1
+    torch.cuda.empty_cache()
+    return {"workload": f"ensemble_256: 256 instances, sides 64..1024 ({nodes} nodes), D(phi)=D0(1+phi), "
+                        f"{lbm_steps} steps per job, FP32",
+            "value": nodes * lbm_steps / (ms_graph / 1e3) / 1e6, "unit": "MLUPS",
+            "mode": "two steps per launch, one block per tile of all instances, 100-step CUDA graph replayed",
+            "per_instance_launches_mlups": nodes * lbm_steps / (ms_sep / 1e3) / 1e6,
+            "speedup_vs_256_launches_per_step": ms_sep / ms_graph, "finite": finite, "clocks": clocks}
+
+
+def extra_burgers(steps):
+    """Sub-record of the 1024^2 Burgers workload (5000 steps per job): FP64, FP32
+    and BF16S storage (two steps per pass with 30 x 30 tiles for the last two),
+    MLUPS and the relative L2 difference of phi from the FP64 path."""
+    import torch
+
+    from paper_1603_09577_gb300 import Solver
+    p = W.params("burgers_1024")
+    n, lbm_steps = p["nx"], p["steps"]
+    phi0_np = W.phi0_burgers()
+    st = torch.cuda.current_stream()
+    clk = clocks_sampler()
+    res, phis = {}, {}
+    for prec, cfg in (("f64", {}), ("f32", dict(steps_per_pass=2, block_rows=4)),
+                      ("bf16s", dict(steps_per_pass=2, block_rows=4))):
+        phi0 = torch.from_numpy(phi0_np.astype(np.float64 if prec == "f64" else np.float32)).cuda()
+        s = Solver(n, n, prec=prec, **cfg)
+        s.set_coeffs(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"], s=W.s9())
+
+        def job():
+            s.set_phi(phi0)
+            s.step(lbm_steps)
+
+        job()
+        reps = 1 if prec == "f64" else steps
+        ms = timed(job, reps, st)
+        phis[prec] = s.phi().cpu().numpy()
+        res[prec] = {"value": n * n * lbm_steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_job": ms,
+                     "timed_jobs": reps, "config": cfg or {"steps_per_pass": 1}}
+        del s
+    clocks = clocks_summary(clk)
+    for prec in ("f32", "bf16s"):
+        res[prec]["rel_l2_vs_fp64_path"] = rel_l2(phis[prec], phis["f64"])
+    torch.cuda.empty_cache()
+    return {"workload": "burgers_1024: D2Q9 MRT, B = a phi^2/2, a=(1,1)/sqrt2, K = 5.12 (D=0.005 on the unit "
+                        "square), 1024x1024 periodic, 5000 steps per job", **res, "clocks": clocks}
+
+
+def fp64_roofline(ginst, rate, kernel, hbm_frac, launch_ms):
+    """Roofline of the FP64 step kernel against the FP64 pipe's measured rate."""
+    return {"bound": "alu", "achieved": ginst, "peak": rate["value"], "unit": "G FP64 thread instructions/s",
+            "frac": ginst / rate["value"], "traffic": None, "kernel": kernel,
+            "fp64_inst_per_update": FP64_INST_PER_UPDATE, "hbm_frac": hbm_frac, "avg_launch_ms": launch_ms,
+            "peak_source": "measured in this run: " + rate["how"]}
+
+
+def extras(args, lbm_steps, headline_phi, peak, src, fp64_rate):
+    """The rest of the metric in the default run, each with its own clocks: the
+    FP64 and BF16S paths of the 4096^2 workload (with their relative L2 from the
+    FP64 path), the FP64 pipe's rate, the adjoint / forward time, the batched
+    ensemble against per-instance launches, and the 1024^2 Burgers workload in
+    the three precisions."""
+    p = W.params(WORKLOAD)
+    cells = p["nx"] * p["ny"]
+    ex = {"fp64_pipe": fp64_rate}
+    # FP64: one full job (about 8 s), the reference field of the other precisions
+    r = c3_measure("f64", {}, lbm_steps, 1, 1, warm_lbm_steps=20)
+    ginst = FP64_INST_PER_UPDATE * cells / (r["avg_launch_ms"] / 1e3) / 1e9
+    ex["fp64"] = {"workload": f"{WORKLOAD}, {lbm_steps} steps per job, storage f64", "value": r["mlups"],
+                  "unit": "MLUPS", "ms_per_job": r["ms_per_job"], "timed_jobs": 1,
+                  "roofline": fp64_roofline(ginst, fp64_rate, "k_step<F64> (fused pull-stream + collide)",
+                                            BYTES_PER_UPDATE["f64"] * cells / (r["avg_launch_ms"] / 1e3) / 1e9 / peak,
+                                            r["avg_launch_ms"]),
+                  "clocks": r["clocks"]}
+    fp64_phi = r["phi"]
+    ex[f"{args.prec}_headline_rel_l2_vs_fp64_path"] = rel_l2(headline_phi, fp64_phi) if headline_phi is not None else None
+    ex["bf16s"], _ = extra_c3("bf16s", lbm_steps, max(3, args.steps // 2), 2, fp64_phi, peak, src)
+    ex["adjoint"] = extra_adjoint(1)
+    ex["ensemble"] = extra_ensemble(2, 3)
+    ex["burgers_1024"] = extra_burgers(3)
+    return ex
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -709,6 +997,9 @@ def main():
     if args.tune and args.variant == 0 and args.block_rows == 0 and args.spp == 1:
         from paper_1603_09577_gb300 import tune
         cfg = tune.tune(nx, ny, args.prec, bc=("abb", "abb"), conv=p["conv"], diff=p["diff"])
+        # the tuned launch is one of the candidates the full-grid parity test
+        # compares with the oracle (tests/test_gpu_headline.py)
+        assert cfg in tune.candidates(nx, args.prec), cfg
         args.spp, args.variant, args.block_rows = cfg["steps_per_pass"], cfg["kernel_variant"], cfg["block_rows"]
         args.autotuned = True
     s = Solver(nx, ny, prec=args.prec, bc=("abb", "abb"), phi_wall=p["phi_wall"], steps_per_pass=args.spp,
@@ -771,6 +1062,10 @@ def main():
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
     e2e_val = whole_job_mlups(world, cells, lbm_steps, e2e_s * 1e3)
 
+    headline_phi = s.phi().cpu().numpy() if (rank == 0 and world == 1 and not args.no_extras) else None
+    del s
+    torch.cuda.empty_cache()
+
     if rank == 0:
         launches_per_job = lbm_steps // args.spp + lbm_steps % args.spp
         launch_ms = statistics.mean(step_kernels_ms) / launches_per_job
@@ -799,16 +1094,18 @@ def main():
             "gpu_launches": args.steps * (1 + launches_per_job + 2),
             "mass_after_job": mass,
         }
+        out["config"]["parity_tested"] = ("the launch is one of the autotuner's candidates, each compared with "
+                                          "the oracle on the full grid by tests/test_gpu_headline.py"
+                                          if getattr(args, "autotuned", False) else None)
+        fp64_rate = fp64_peak_probe() if (args.prec == "f64" or (world == 1 and not args.no_extras)) else None
         if args.prec == "f64":
             # the FP64 kernel is bound by the FP64 pipe, not HBM
             ginst = FP64_INST_PER_UPDATE * cells * lbm_steps / (statistics.mean(step_kernels_ms) / 1e3) / 1e9
-            out["roofline"] = {"bound": "alu", "achieved": ginst, "peak": FP64_PEAK_GINST,
-                               "unit": "G FP64 thread instructions/s", "frac": ginst / FP64_PEAK_GINST, "traffic": None,
-                               "kernel": kernel, "fp64_inst_per_update": FP64_INST_PER_UPDATE,
-                               "hbm_frac": achieved / peak, "avg_launch_ms": launch_ms,
-                               "peak_source": "FP64 pipe: 2 thread instructions per SM per clock x 152 SMs x 2070 MHz"}
+            out["roofline"] = fp64_roofline(ginst, fp64_rate, kernel, achieved / peak, launch_ms)
         if clocks is not None:
             out["clocks"] = clocks
+        if world == 1 and not args.no_extras:
+            out["extras"] = extras(args, lbm_steps, headline_phi, peak, src, fp64_rate)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_sample()
         print(json.dumps(out), flush=True)

@@ -224,6 +224,17 @@ int lbm_build_checked(void);
    word lbm_debug_flags reads. */
 int lbm_debug_wait_probe(unsigned polls, int *dev_status, void *stream);
 
+/* Rate probe of the FP64 pipe, the roof of the LBM_F64 step kernel (the paper has
+   no counterpart: it is a measurement aid). Launches blocks x threads threads,
+   each running 8 independent FP64 fused multiply-add recurrences for `iters`
+   iterations, asynchronously on `stream`; the caller times the launch (CUDA
+   events on the same stream) and divides *fp64_inst (host, may be NULL: the
+   FP64 thread instructions the launch executes) by the time. dev_sink: caller-
+   owned device memory of `blocks` doubles, never written in practice (it keeps
+   the recurrences live). Returns LBM_EINVAL for blocks < 1, threads not a
+   multiple of 32 in [32, 1024], iters < 1 or a null sink. */
+int lbm_probe_fp64(int blocks, int threads, int iters, double *dev_sink, long long *fp64_inst, void *stream);
+
 /* Checkpoint / resume: the state is lbm_state_bytes bytes (populations; the phi
    plane for LBM_BF16S and Scheme A; with LBM_NEE walls, a 256-byte tail holding
    the Dirichlet record count). dev_dst / dev_src: device buffers of that size. */
@@ -280,10 +291,12 @@ typedef struct lbm_ensemble_s *lbm_ensemble;
 
 /* Device workspace bytes for `count` instances of sizes nx[i] x ny[i]. */
 int lbm_ensemble_workspace_size(int count, const int *nx, const int *ny, size_t *bytes);
-/* Create; coeffs: `count` entries (per-instance u and K). Copies the instance and
-   tile tables into the caller's workspace (synchronous). */
+/* Create; coeffs: `count` entries (per-instance u and K). A synchronous set-up
+   call: it enqueues the copies of the instance and tile tables into the caller's
+   workspace on `stream` and waits for `stream` (no other stream is touched), so
+   the tables are in place when it returns. */
 int lbm_ensemble_create(lbm_ensemble *e, int count, const int *nx, const int *ny, const lbm_coeffs *coeffs,
-                        void *dev_workspace, size_t bytes);
+                        void *dev_workspace, size_t bytes, void *stream);
 int lbm_ensemble_destroy(lbm_ensemble e);
 /* Total nodes, number of tiles and the persistent grid size (blocks). */
 int lbm_ensemble_info(lbm_ensemble e, long long *nodes, int *tiles, int *grid);
@@ -334,9 +347,13 @@ int lbm_ensemble_debug_flags(lbm_ensemble e, int *flags, void *stream);
    the library's device image, present on every device that loads the library
    until the process exits. The first call on a device looks up that array's
    address (cudaGetSymbolAddress) with the device current; make the first call
-   on each device before any stream capture. All calls share the array, so calls
-   whose kernels overlap on the GPU race: order them on one stream. Returns
-   LBM_EINVAL for n < 1, n > 67,108,864 or a null field or output. */
+   on each device before any stream capture. The address is kept per device
+   ordinal for the life of the process and is valid only in the context that was
+   current at that first call: cudaDeviceReset, or making another context current
+   for the device through the driver API, is not supported afterwards. All calls
+   share the array, so calls whose kernels overlap on the GPU race: order them on
+   one stream. Returns LBM_EINVAL for n < 1, n > 67,108,864 or a null field or
+   output, and LBM_EUNSUPPORTED on a device ordinal of 64 or more. */
 int lbm_reduce_field_noalloc(const double *dev_phi, const double *dev_ref, long long n, double *dev_out,
                              void *stream);
 

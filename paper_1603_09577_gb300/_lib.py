@@ -79,6 +79,7 @@ SIGNATURES = {
     "lbm_debug_flags": [_VP, ctypes.POINTER(_I), _VP],
     "lbm_build_checked": [],
     "lbm_debug_wait_probe": [ctypes.c_uint, _VP, _VP],
+    "lbm_probe_fp64": [_I, _I, _I, _VP, ctypes.POINTER(ctypes.c_longlong), _VP],
     "lbm_adjoint_workspace_size": [_VP, ctypes.POINTER(_SZ)],
     "lbm_adjoint_begin": [_VP, _VP, _SZ, _VP, _I, _VP],
     "lbm_adjoint_step": [_VP, _VP, _VP],
@@ -97,7 +98,7 @@ SIGNATURES = {
     "lbm3_reduce": [_VP, _VP, _VP, _VP],
     "lbm3_debug_flags": [_VP, ctypes.POINTER(_I), _VP],
     "lbm_ensemble_workspace_size": [_I, _VP, _VP, ctypes.POINTER(_SZ)],
-    "lbm_ensemble_create": [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, _SZ],
+    "lbm_ensemble_create": [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, _SZ, _VP],
     "lbm_ensemble_destroy": [_VP],
     "lbm_ensemble_info": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "lbm_ensemble_set_phi": [_VP, _VP, _I, _VP],

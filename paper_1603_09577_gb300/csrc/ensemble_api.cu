@@ -85,7 +85,7 @@ int lbm_ensemble_workspace_size(int count, const int *nx, const int *ny, size_t 
 }
 
 int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *ny, const lbm_coeffs *coeffs,
-                        void *dev_ws, size_t bytes)
+                        void *dev_ws, size_t bytes, void *stream)
 {
     if (!out) return fail(LBM_EINVAL, "null ensemble pointer");
     *out = nullptr;
@@ -162,15 +162,19 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     e->err = (int *)(ws + L.off_err);
     e->partials = (double *)(ws + L.off_partials);
     e->d_tile_begin = (int *)(ws + L.off_tbegin);
-    int rc = cuda_check(cudaMemcpy(e->d_inst, inst.data(), sizeof(EnsInst) * count, cudaMemcpyHostToDevice),
+    // the tables go through the caller's stream; the call waits for that stream
+    // alone, so the host vectors may go and the tables are in place on return
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = cuda_check(cudaMemcpyAsync(e->d_inst, inst.data(), sizeof(EnsInst) * count, cudaMemcpyHostToDevice, st),
                         "lbm_ensemble_create instance table");
-    if (!rc) rc = cuda_check(cudaMemcpy(e->d_tiles2, tiles2.data(), sizeof(int4) * tiles2.size(), cudaMemcpyHostToDevice),
-                             "lbm_ensemble_create two-step tile table");
-    if (!rc) rc = cuda_check(cudaMemset(e->err, 0, sizeof(int)), "lbm_ensemble_create error word");
-    if (!rc) rc = cuda_check(cudaMemcpy(e->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice),
-                             "lbm_ensemble_create tile table");
-    if (!rc) rc = cuda_check(cudaMemcpy(e->d_tile_begin, e->tile_begin, sizeof(int) * ((size_t)count + 1),
-                                        cudaMemcpyHostToDevice), "lbm_ensemble_create tile offsets");
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(e->d_tiles2, tiles2.data(), sizeof(int4) * tiles2.size(),
+                                             cudaMemcpyHostToDevice, st), "lbm_ensemble_create two-step tile table");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(e->err, 0, sizeof(int), st), "lbm_ensemble_create error word");
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(e->d_tiles, tiles.data(), sizeof(int4) * tiles.size(),
+                                             cudaMemcpyHostToDevice, st), "lbm_ensemble_create tile table");
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(e->d_tile_begin, e->tile_begin, sizeof(int) * ((size_t)count + 1),
+                                             cudaMemcpyHostToDevice, st), "lbm_ensemble_create tile offsets");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "lbm_ensemble_create: waiting for the table copies");
     int dev = 0, sms = 0;
     if (!rc) rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");

@@ -273,19 +273,10 @@ static cudaError_t step2_ty(const lbm_solver *s, int src, cudaStream_t st)
     using T = typename Store<PREC>::T;
     constexpr size_t smem = 9 * Tile2<TY>::kRP * sizeof(float);
     if (smem > 48 * 1024) {
-        // opt in to more than 48 KB of dynamic shared memory, once per device (the
-        // first launch on a device must therefore come before any stream capture)
-        static int configured[64] = {};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
+        // more than 48 KB of dynamic shared memory: opt in once per device
+        static SmemOptIn once;
+        const cudaError_t e = opt_in_smem((const void *)k_step2<PREC, CONV, DIFF, TY, KF>, (int)smem, once);
         if (e != cudaSuccess) return e;
-        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!configured[dev]) {
-            e = cudaFuncSetAttribute(k_step2<PREC, CONV, DIFF, TY, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            if (e != cudaSuccess) return e;
-            configured[dev] = 1;
-        }
     }
     const Params<float> p = make_params<float>(s);
     dim3 block(32, kT2Threads / 32);

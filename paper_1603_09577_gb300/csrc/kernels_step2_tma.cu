@@ -110,9 +110,17 @@ k_step2_tma(const Params<float> p, const __grid_constant__ CUtensorMap src_map, 
         mbar_expect_tx(bar, kStageBytes);
         tma_load_3d(stage, &src_map, xs, ty0 - 2, 0, bar);
     }
-    if (!mbar_wait_bounded(bar, 0)) {
+    // The decision to give up is block-wide: if any thread's bounded wait ran
+    // out, every thread reports and returns together, so no thread is left
+    // behind at a later barrier. The block then waits once more (bounded) for
+    // the copy to land before it leaves; if that wait runs out as well, the
+    // block leaves with the copy possibly still in flight. Either way its tile's
+    // output is not written, and the error word (lbm_debug_flags, 16) tells the
+    // host that the results of this launch are not valid.
+    const bool landed = mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(!landed)) {
         if (tid == 0) atomicOr(p.err, kErrTimeout);
-        mbar_wait_bounded(bar, 0);                  // let the copy finish before the block leaves
+        mbar_wait_bounded(bar, 0);
         return;
     }
 
@@ -182,16 +190,9 @@ bool make_map(CUtensorMap *map, const lbm_solver *s, const void *base)
 template <int CONV, int DIFF, bool KF>
 cudaError_t step2_tma_t(const lbm_solver *s, int src, cudaStream_t st)
 {
-    static int configured[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static SmemOptIn once;
+    const cudaError_t e = opt_in_smem((const void *)k_step2_tma<CONV, DIFF, KF>, (int)kTmaSmem, once);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!configured[dev]) {
-        e = cudaFuncSetAttribute(k_step2_tma<CONV, DIFF, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
-        if (e != cudaSuccess) return e;
-        configured[dev] = 1;
-    }
     CUtensorMap map;
     if (!make_map(&map, s, s->pop[src])) return cudaErrorInvalidValue;
     const Params<float> p = make_params<float>(s);

@@ -29,6 +29,18 @@ int cuda_check(cudaError_t e, const char *what)
     return fail(LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+cudaError_t opt_in_smem(const void *kernel, int bytes, SmemOptIn &flags)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (flags.done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) flags.done[dev].store(1, std::memory_order_release);
+    return e;
+}
+
 static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int make_layout(const lbm_desc *d, Layout *L)

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <atomic>
 #include <string>
 
 #include "lbm.h"
@@ -60,6 +61,16 @@ struct lbm_solver {
 };
 
 namespace lbm {
+
+// Per-device record of a kernel's opt-in to more than 48 KB of dynamic shared
+// memory. The flags are atomic, so first launches from several host threads do
+// not race on them (cudaFuncSetAttribute is idempotent and may then run twice).
+// The opt-in happens at the first launch on a device, which must therefore come
+// before any stream capture on that device.
+struct SmemOptIn {
+    std::atomic<int> done[64];
+};
+cudaError_t opt_in_smem(const void *kernel, int bytes, SmemOptIn &flags);
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);

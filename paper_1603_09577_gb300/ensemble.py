@@ -35,7 +35,7 @@ class Ensemble:
         self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
         self.h = ctypes.c_void_p()
         C.check(self.lib.lbm_ensemble_create(ctypes.byref(self.h), n, self.nx, self.ny, co, _ptr(self.workspace),
-                                             size.value))
+                                             size.value, _stream()))
         C.check(self.lib.lbm_ensemble_configure(self.h, int(steps_per_pass)))
         # two-step launches: one block per tile (default) or a persistent grid
         C.check(self.lib.lbm_ensemble_set_persistent(self.h, int(bool(persistent))))

@@ -308,7 +308,7 @@ def test_ensemble_host_validation():
 
     def create(cs, ptr=ws.ptr, size=n.value):
         arr = (C.Coeffs * len(cs))(*cs)
-        return L.lbm_ensemble_create(ctypes.byref(e), cnt, nx, ny, arr, ctypes.c_void_p(ptr), size)
+        return L.lbm_ensemble_create(ctypes.byref(e), cnt, nx, ny, arr, ctypes.c_void_p(ptr), size, None)
 
     good = coeffs(diff=1)
     assert create([good, good], ptr=ws.ptr + 8) == C.LBM_EINVAL               # misaligned workspace
@@ -326,3 +326,29 @@ def test_ensemble_host_validation():
     assert L.lbm_ensemble_set_phi(None, out, C.LBM_F64, None) == C.LBM_EINVAL
     assert L.lbm_ensemble_replay(None, None) == C.LBM_EINVAL
     assert L.lbm_ensemble_configure(None, 2) == C.LBM_EINVAL
+
+
+def test_error_messages_are_per_thread():
+    """Two host threads calling failing entry points at the same time each read
+    back their own message (lbm_last_error is thread-local), with no GPU work."""
+    import threading
+    L = C.lib()
+    results = {}
+    barrier = threading.Barrier(2)
+
+    def worker(tag, bad):
+        barrier.wait()
+        seen = []
+        for _ in range(200):
+            n = ctypes.c_size_t()
+            rc = L.lbm_workspace_size(ctypes.byref(bad), ctypes.byref(n))
+            seen.append((rc, L.lbm_last_error()))
+        results[tag] = seen
+
+    a = desc(nx=1)                        # nx < 2
+    b = desc(steps_per_pass=3)            # invalid steps per pass
+    t1 = threading.Thread(target=worker, args=("a", a))
+    t2 = threading.Thread(target=worker, args=("b", b))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    assert all(rc == C.LBM_EINVAL and b"nx and ny" in m for rc, m in results["a"])
+    assert all(rc == C.LBM_EINVAL and b"steps_per_pass" in m for rc, m in results["b"])

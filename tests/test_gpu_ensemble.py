@@ -12,6 +12,9 @@ from paper_1603_09577_gb300.ensemble import Ensemble
 pytestmark = pytest.mark.gpu
 
 
+_ORACLE = {}
+
+
 def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
@@ -104,7 +107,8 @@ def test_ensemble_modes_agree_bitwise():
 def test_ensemble_full_workload(spp):
     """256 instances (sides 64..1024, 48.6 M nodes), 1000 steps through a
     replayed graph: finite, mass conserved per instance, and the six smallest
-    instances within the FP32 bar of the oracle."""
+    instances and the largest one (1022^2 nodes) within the FP32 bar of the
+    oracle, as relative L2 and node by node."""
     inst = W.ensemble()
     e = Ensemble(inst, steps_per_pass=spp)
     phis = [W.ensemble_phi0(d) for d in inst]
@@ -120,10 +124,18 @@ def test_ensemble_full_workload(spp):
     assert all(torch.isfinite(o).all() for o in out)
     for p0, o in zip(phis, out):
         assert abs(float(o.sum()) - p0.sum()) <= 1e-5 * p0.sum()
-    order = np.argsort([d["nx"] * d["ny"] for d in inst])[:6]
+    sizes = [d["nx"] * d["ny"] for d in inst]
+    order = list(np.argsort(sizes)[:6]) + [int(np.argmax(sizes))]
     for i in order:
-        ref = oracle_phi(inst[i], phis[i], 1000)
-        assert rel(out[i].numpy(), ref) <= 1e-5, (i, rel(out[i].numpy(), ref))
+        key = (i, 1000)
+        if key not in _ORACLE:
+            _ORACLE[key] = oracle_phi(inst[i], phis[i], 1000)
+        ref = _ORACLE[key]
+        g = out[i].numpy()
+        mx = float(np.abs(g - ref).max() / np.abs(ref).max())
+        print(f"[parity] ensemble instance {i} ({inst[i]['nx']}^2) spp {spp}: rel_l2={rel(g, ref):.3e} max_node={mx:.3e}")
+        assert rel(g, ref) <= 1e-5, (i, rel(g, ref))
+        assert mx <= 2e-5, (i, mx)
 
 
 def test_ensemble_per_instance_reductions():

@@ -254,8 +254,12 @@ def test_burgers_full_steps_reduced_grid(prec):
     got, _ = run_gpu(prec, n, n, phi0, p["steps"], **coef)
     if prec == "f64":
         # the solution decays to its mean (|phi_N| / |phi_0| ~ 5e-4): FP64 rounding
-        # of both codes accumulates at the scale of the early field, so the FP64
-        # bar is taken relative to |phi_0|
+        # of both codes accumulates at the scale of the early field. Measured
+        # relative to phi_N this is about 1.6e-12, above the 1e-12 target; the
+        # bar held is 1e-11 relative to phi_N (a 1e-10 error fails it) and
+        # 1e-12 relative to phi_0
+        print(f"[parity] burgers 256^2 x 5000 f64: rel_l2={rel(got, ref):.3e}")
+        assert rel(got, ref) <= 1e-11, rel(got, ref)
         assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(phi0)
     else:
         assert rel(got, ref) <= TOL[prec], rel(got, ref)
@@ -398,3 +402,38 @@ def test_bounded_wait_reports_instead_of_hanging():
     ref = run_oracle(3, 2, phi0, 5, **coef)
     got, _ = run_gpu("f64", 3, 2, phi0, 5, **coef)
     assert rel(got, ref) <= 1e-12
+
+
+def test_concurrent_host_threads():
+    """Two host threads, each with its own solver and stream, step at the same
+    time through the 30 x 62 tile kernel (the launcher that opts in to more than
+    48 KB of shared memory per device) and through the 30 x 30 one; each result
+    equals the same run made alone."""
+    import threading
+    nx, ny = 150, 140
+    phi0 = W.phi0_aniso(nx, seed=21, ny=ny)
+    coef = dict(conv=1, u=(0.04, -0.03), diff=2, K=(0.02, 0.006, 0.015), r1=-0.05)
+    alone = {}
+    for br in (0, 4):
+        alone[br], _ = run_gpu("bf16s", nx, ny, phi0, 40, (1, 1), (0.1, 0.2, 0.3, 0.4), spp=2, block_rows=br, **coef)
+    got = {}
+    barrier = threading.Barrier(2)
+
+    def worker(br):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            s = Solver(nx, ny, prec="bf16s", bc=("abb", "abb"), phi_wall=(0.1, 0.2, 0.3, 0.4), steps_per_pass=2,
+                       block_rows=br)
+            s.set_coeffs(s=W.s9(), **coef)
+            s.set_phi(torch.from_numpy(phi0).cuda(), stream=st)
+            barrier.wait()
+            s.step(40, stream=st)
+            got[br] = s.phi(stream=st).cpu().numpy()
+
+    ts = [threading.Thread(target=worker, args=(br,)) for br in (0, 4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for br in (0, 4):
+        assert np.array_equal(got[br], alone[br]), br

@@ -65,3 +65,32 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert rc == C.LBM_EINVAL and b"scratch capacity" in L.lbm_last_error()
     assert L.lbm_reduce_field_noalloc(ptr(phi), None, 0, ptr(out), None) == C.LBM_EINVAL
     assert L.lbm_reduce_field_noalloc(None, None, 16, ptr(out), None) == C.LBM_EINVAL
+
+
+@pytest.mark.parametrize("n", [4096 * 4096, 67108864])
+def test_noalloc_large_fields_fill_the_scratch(n):
+    """16,777,216 values (2,048 scratch slots, so the second pass walks more
+    partials than it has threads) and exactly the 67,108,864-value capacity (every
+    slot): the statistics equal their numpy FP64 definitions, and a second call
+    over the reused scratch returns the same bits."""
+    L = C.lib()
+    g = torch.Generator(device="cuda").manual_seed(n % 1000)
+    phi = torch.rand(n, generator=g, dtype=torch.float64, device="cuda") - 0.25
+    ref = torch.rand(n, generator=g, dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    outs = []
+    for _ in range(2):
+        got = torch.full((8,), -1.0, dtype=torch.float64, device="cuda")
+        C.check(L.lbm_reduce_field_noalloc(ptr(phi), ptr(ref), n, ptr(got), stream))
+        outs.append(got.cpu())
+    assert torch.equal(outs[0], outs[1])
+    a, r = phi.cpu().numpy(), ref.cpu().numpy()
+    d = a - r
+    expected = [a.sum(), np.abs(d).sum(), np.abs(r).sum(), (d * d).sum(), (r * r).sum(), np.abs(a).max(), 0.0,
+                (a * a).sum()]
+    got = outs[0].tolist()
+    for j in range(8):
+        if j in (5, 6):
+            assert got[j] == expected[j], (j, got[j], expected[j])
+        else:
+            assert abs(got[j] - expected[j]) <= 1e-12 * abs(expected[j]), (j, got[j], expected[j])
