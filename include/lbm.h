@@ -87,12 +87,16 @@ typedef struct {
                                warp walks a 30-column strip) instead of the
                                shared-memory tile kernel; 4: with steps_per_pass
                                2 and LBM_F32, the tile kernel with each interior
-                               tile's input staged by a TMA tensor copy           */
+                               tile's input staged by a TMA tensor copy; 5: with
+                               steps_per_pass 2 (LBM_F32 / LBM_BF16S), the tile
+                               kernel with two x-adjacent nodes per thread and
+                               paired (vector) loads and stores               */
     int block_rows;         /* rows of 32-thread warps per thread block: 0 (= 8),
                                1, 2, 4 or 8; for kernel_variant 3 the rows each
                                warp marches are 16 * block_rows (0: 64); for the
                                two-step tile kernel 4 selects 30 x 30 tiles,
-                               other values 30 x 62                               */
+                               other values 30 x 62; for kernel_variant 5, 4
+                               selects 62 x 14 tiles, other values 62 x 30        */
     int scheme;             /* LBM_SCHEME_B (0) or LBM_SCHEME_A. Scheme A, LBM_NEE,
                                conv 2 / 3 and diff 3 run the general kernels:
                                one node per thread (LBM_F64 or LBM_F32,

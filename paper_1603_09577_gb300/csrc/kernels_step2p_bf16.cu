@@ -1,0 +1,20 @@
+// kernels_step2p_bf16.cu -- instantiations of the two-step pair-tile kernel for
+// BF16-shifted storage (the other storage compiles in parallel in its own unit).
+#include "kernels_step2p.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step2p_bf16s(const lbm_solver *s, int src, cudaStream_t st)
+{
+    switch (s->c.conv * 3 + s->c.diff) {
+    case 0: return step2p_t<LBM_BF16S, 0, 0>(s, src, st);
+    case 1: return step2p_t<LBM_BF16S, 0, 1>(s, src, st);
+    case 2: return step2p_t<LBM_BF16S, 0, 2>(s, src, st);
+    case 3: return step2p_t<LBM_BF16S, 1, 0>(s, src, st);
+    case 4: return step2p_t<LBM_BF16S, 1, 1>(s, src, st);
+    case 5: return step2p_t<LBM_BF16S, 1, 2>(s, src, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

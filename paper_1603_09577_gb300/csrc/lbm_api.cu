@@ -102,7 +102,9 @@ static int check_desc(const lbm_desc *d)
     if (d->steps_per_pass != 1 && d->steps_per_pass != 2) return fail(LBM_EINVAL, "steps_per_pass must be 1 or 2");
     if (d->steps_per_pass == 2 && d->prec == LBM_F64)
         return fail(LBM_EUNSUPPORTED, "two steps per pass is built for LBM_F32 and LBM_BF16S");
-    if (d->kernel_variant < 0 || d->kernel_variant > 4) return fail(LBM_EINVAL, "kernel_variant must be 0 to 4");
+    if (d->kernel_variant < 0 || d->kernel_variant > 5) return fail(LBM_EINVAL, "kernel_variant must be 0 to 5");
+    if (d->kernel_variant == 5 && (d->steps_per_pass != 2 || d->prec == LBM_F64))
+        return fail(LBM_EINVAL, "kernel_variant 5 (pair tiles) needs steps_per_pass 2 and LBM_F32 or LBM_BF16S");
     if (d->kernel_variant == 3 && d->steps_per_pass != 2)
         return fail(LBM_EINVAL, "kernel_variant 3 (column march) needs steps_per_pass 2");
     if (d->kernel_variant == 4 && (d->steps_per_pass != 2 || d->prec != LBM_F32))
@@ -422,6 +424,8 @@ int lbm_step(lbm_handle h, int nsteps, void *stream)
         for (; done + 2 <= nsteps; done += 2) {
             const cudaError_t e = h->d.kernel_variant == 3   ? launch_step2m(h, h->cur, st)
                                   : h->d.kernel_variant == 4 ? launch_step2_tma(h, h->cur, st)
+                                  : h->d.kernel_variant == 5 ? (h->d.prec == LBM_F32 ? launch_step2p_f32(h, h->cur, st)
+                                                                                     : launch_step2p_bf16s(h, h->cur, st))
                                                              : launch_step2(h, h->cur, st);
             if (int rc = cuda_check(e, "lbm_step (two steps per pass)")) return rc;
             h->cur ^= 1;

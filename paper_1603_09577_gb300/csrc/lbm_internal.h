@@ -85,6 +85,9 @@ cudaError_t launch_step(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2m(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2_tma(const lbm_solver *s, int src, cudaStream_t st);
+// two steps per pass, two x-adjacent nodes per thread (kernel_variant 5)
+cudaError_t launch_step2p_f32(const lbm_solver *s, int src, cudaStream_t st);
+cudaError_t launch_step2p_bf16s(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step_ptr(const lbm_solver *s, const void *src, void *dst, cudaStream_t st);
 // general path (Scheme A, extrapolation walls, power-law flux): a step when
 // phi0 is null, else the initialisation from phi0

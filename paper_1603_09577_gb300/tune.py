@@ -3,8 +3,9 @@
 For a problem (grid, storage precision, walls, coefficient family) it times the
 candidate configurations on the current device -- kernel variant (one node or
 four x-adjacent nodes per thread), rows per thread block, one or two time steps
-per sweep through memory (shared-memory tiles or the register column march with
-16 to 128 rows per warp, the TMA-staged tile) -- on a synthetic field, and
+per sweep through memory (shared-memory tiles of one or two nodes per thread,
+the register column march with 16 to 128 rows per warp, the TMA-staged tile) --
+on a synthetic field, and
 keeps the fastest in a JSON cache keyed by device name and problem, so later
 runs reuse it. Problems on the general path (Scheme A, extrapolated walls, the
 power-law flux, the tensor diffusion function) choose between the general
@@ -56,6 +57,8 @@ def candidates(nx: int, prec: str):
     if prec != "f64":
         out.append(dict(kernel_variant=0, block_rows=0, steps_per_pass=2))
         out.append(dict(kernel_variant=0, block_rows=4, steps_per_pass=2))
+        out.append(dict(kernel_variant=5, block_rows=0, steps_per_pass=2))
+        out.append(dict(kernel_variant=5, block_rows=4, steps_per_pass=2))
         out += [dict(kernel_variant=3, block_rows=b, steps_per_pass=2) for b in (1, 2, 4, 8)]
     if prec == "f32":
         out.append(dict(kernel_variant=4, block_rows=0, steps_per_pass=2))

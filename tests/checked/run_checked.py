@@ -30,10 +30,11 @@ def flags(s):
 
 def main():
     out = {"checked": C.lib().lbm_build_checked(), "faults": [], "max_rel": 0.0}
-    cases = [(37, 29, (1, 1)), (64, 40, (0, 0)), (100, 66, (0, 1)), (132, 35, (1, 0)), (8, 5, (1, 1))]
+    cases = [(37, 29, (1, 1)), (64, 40, (0, 0)), (100, 66, (0, 1)), (132, 35, (1, 0)), (8, 5, (1, 1)),
+             (201, 90, (0, 0)), (190, 77, (1, 1))]
     configs = [("f64", 1, 1, 0), ("f32", 1, 1, 0), ("f32", 2, 1, 0), ("bf16s", 2, 1, 0),
                ("f32", 0, 2, 0), ("f32", 0, 2, 4), ("bf16s", 0, 2, 4), ("f32", 3, 2, 1),
-               ("f32", 4, 2, 0)]
+               ("f32", 4, 2, 0), ("f32", 5, 2, 0), ("f32", 5, 2, 4), ("bf16s", 5, 2, 0), ("bf16s", 5, 2, 4)]
     coef = dict(conv=1, u=(0.06, -0.03), diff=2, K=(0.02, 0.008, 0.01), r1=-0.05)
     for nx, ny, bc in cases:
         phi0 = W.phi0_aniso(nx, seed=nx + ny, ny=ny)

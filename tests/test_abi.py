@@ -63,7 +63,7 @@ def test_workspace_size_and_layout():
 
 
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(prec=7), dict(bc_x=3), dict(steps_per_pass=3),
-                                 dict(block_rows=16), dict(block_rows=3), dict(kernel_variant=5),
+                                 dict(block_rows=16), dict(block_rows=3), dict(kernel_variant=5), dict(kernel_variant=6),
                                  dict(kernel_variant=3), dict(kernel_variant=4)])
 def test_invalid_descriptions_rejected(bad):
     rc, _ = ws_size(desc(**bad))

@@ -78,7 +78,7 @@ def test_parity_families_and_walls(prec, variant, case):
     assert rel(got, ref) <= TOL[prec], rel(got, ref)
 
 
-TB = [(c, prec, n, v) for c in CASES for prec in ("f32", "bf16s") for n in (60, 61) for v in (0, 3, 4)
+TB = [(c, prec, n, v) for c in CASES for prec in ("f32", "bf16s") for n in (60, 61) for v in (0, 3, 4, 5)
       if not (v == 4 and prec != "f32")]
 
 
@@ -86,8 +86,8 @@ TB = [(c, prec, n, v) for c in CASES for prec in ("f32", "bf16s") for n in (60, 
                          ids=[f"{c[0]}x{c[1]}-bc{c[2][0]}{c[2][1]}-{p}-{n}-v{v}" for c, p, n, v in TB])
 def test_two_steps_per_pass(case, prec, steps, variant):
     """Temporal blocking (two steps per sweep; an odd count ends with one step):
-    the shared-memory tile kernel (variant 0), the register column march (3) and
-    the tile kernel with TMA-staged input (4)."""
+    the shared-memory tile kernel (variant 0), the register column march (3),
+    the tile kernel with TMA-staged input (4) and the pair-tile kernel (5)."""
     nx, ny, bc, conv, diff, u, K, r0, r1 = case
     rng = np.random.default_rng(nx * 131 + ny)
     phi0 = W.jacobi_smooth(rng.uniform(0.05, 0.95, (ny, nx)), 2)
@@ -437,3 +437,34 @@ def test_concurrent_host_threads():
         t.join()
     for br in (0, 4):
         assert np.array_equal(got[br], alone[br]), br
+
+
+PAIR_CASES = [(300, 250, (1, 1)), (257, 131, (0, 0)), (190, 64, (1, 0)), (129, 200, (0, 1)), (64, 17, (1, 1)),
+              (131, 19, (0, 0))]
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16s"])
+@pytest.mark.parametrize("block_rows", [0, 4])
+def test_pair_tiles_bit_identical_to_node_tiles(prec, block_rows):
+    """The pair-tile kernel (two x-adjacent nodes per thread, paired loads and
+    stores, 62 x 14 or 62 x 30 tiles) performs every node's arithmetic in the
+    same order as the one-node tile kernel: the two agree bit for bit, on grids
+    with interior tiles, ragged edges, both wall kinds, every coefficient
+    family, a per-node tensor field, and an odd step count; and both match the
+    oracle."""
+    for i, (nx, ny, bc) in enumerate(PAIR_CASES):
+        conv, diff = i % 2, i % 3
+        phi0 = W.phi0_aniso(nx, seed=31 + i, ny=ny)
+        walls = (0.2, 0.6, 0.1, 0.4) if bc != (0, 0) else (0, 0, 0, 0)
+        coef = dict(conv=conv, u=(0.05, -0.03), diff=diff, K=(0.02, 0.006, 0.015), r1=-0.05)
+        a, _ = run_gpu(prec, nx, ny, phi0, 21, bc, walls, spp=2, variant=0, block_rows=4, **coef)
+        b, _ = run_gpu(prec, nx, ny, phi0, 21, bc, walls, spp=2, variant=5, block_rows=block_rows, **coef)
+        assert np.array_equal(a, b), (nx, ny, bc, float(np.abs(a - b).max()))
+        ref = run_oracle(nx, ny, phi0, 21, bc, walls, **coef)
+        assert rel(b, ref) <= TOL[prec], rel(b, ref)
+    nx, ny = 260, 150
+    Kf, phi0, _ = W.adjoint_inputs(nx, seed=9, ny=ny)
+    coef = dict(conv=0, u=(0.03, 0.01), diff=0, K=(0.0, 0.0, 0.0))
+    a, _ = run_gpu(prec, nx, ny, phi0, 20, Kfield=Kf, spp=2, variant=0, block_rows=4, **coef)
+    b, _ = run_gpu(prec, nx, ny, phi0, 20, Kfield=Kf, spp=2, variant=5, block_rows=block_rows, **coef)
+    assert np.array_equal(a, b)
