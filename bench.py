@@ -66,6 +66,8 @@ def parse():
                     help="use --variant/--block-rows/--spp as given instead of the autotuner's choice")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=None,
+                    help="grid side of the headline workload (default 4096; smaller sides serve profiler captures)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-records (BF16S, FP64, adjoint, ensemble, 1024^2 Burgers) of the default run")
     ap.add_argument("--ens-count", type=int, default=256, help="instances of the ensemble workload")
@@ -100,9 +102,10 @@ def whole_job_mlups(world: int, cells: int, lbm_steps: int, ms_per_step: float) 
 
 def config(args, lbm_steps):
     p = W.params(WORKLOAD)
+    n = args.nx or p["nx"]
     return {"workload": f"{WORKLOAD}: D2Q9 MRT, D(phi)=(1+phi^2)K, K=[[0.02,0.008],[0.008,0.01]], "
-                        f"R=-0.1 phi, 4096x4096, phi=0 anti-bounce-back walls, {lbm_steps} steps per job",
-            "nx": p["nx"], "ny": p["ny"], "lbm_steps_per_bench_step": lbm_steps,
+                        f"R=-0.1 phi, {n}x{n}, phi=0 anti-bounce-back walls, {lbm_steps} steps per job",
+            "nx": n, "ny": n, "lbm_steps_per_bench_step": lbm_steps,
             "storage": args.prec, "steps_per_pass": args.spp, "kernel_variant": args.variant,
             "block_rows": args.block_rows, "autotuned": bool(getattr(args, "autotuned", False)),
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
@@ -989,10 +992,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     p = W.params(WORKLOAD)
     lbm_steps = args.lbm_steps or p["steps"]
-    nx, ny = p["nx"], p["ny"]
+    nx, ny = (args.nx, args.nx) if args.nx else (p["nx"], p["ny"])
     cells = nx * ny
 
-    phi0_np = W.phi0_aniso(4096, seed=3).astype(np.float32)
+    phi0_np = W.phi0_aniso(nx, seed=3).astype(np.float32)
     phi0 = torch.from_numpy(phi0_np).cuda()
     if args.tune and args.variant == 0 and args.block_rows == 0 and args.spp == 1:
         from paper_1603_09577_gb300 import tune

@@ -96,7 +96,8 @@ typedef struct {
                                warp marches are 16 * block_rows (0: 64); for the
                                two-step tile kernel 4 selects 30 x 30 tiles,
                                other values 30 x 62; for kernel_variant 5, 4
-                               selects 62 x 14 tiles, other values 62 x 30        */
+                               selects 62 x 14 tiles, 2 62 x 22, other values
+                               62 x 30                                            */
     int scheme;             /* LBM_SCHEME_B (0) or LBM_SCHEME_A. Scheme A, LBM_NEE,
                                conv 2 / 3 and diff 3 run the general kernels:
                                one node per thread (LBM_F64 or LBM_F32,

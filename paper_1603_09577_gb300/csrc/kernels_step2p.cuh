@@ -32,7 +32,7 @@ constexpr int kPX = 62;                          // output columns per tile
 constexpr int kPRX = kPX + 2;                    // region columns: 64, two per lane
 template <int TY> struct TileP {
     static constexpr int kTY = TY, kRY = TY + 2, kRP = kPRX * kRY;
-    static constexpr int kMinBlocks = TY > 16 ? 3 : 4;
+    static constexpr int kMinBlocks = TY > 24 ? 3 : 4;
 };
 
 __device__ __forceinline__ F2 bf2_unpack(unsigned u)
@@ -305,16 +305,20 @@ static cudaError_t step2p_ty(const lbm_solver *s, int src, cudaStream_t st)
 }
 
 // tile height from the descriptor: block_rows 4 selects 62 x 14 tiles (37 KB of
-// shared memory, 4 blocks per SM), anything else 62 x 30 (74 KB, 3 blocks)
+// shared memory, 4 blocks per SM), 2 selects 62 x 22 (55 KB, 4 blocks), anything
+// else 62 x 30 (74 KB, 3 blocks)
+template <int PREC, int CONV, int DIFF, bool KF>
+static cudaError_t step2p_k(const lbm_solver *s, int src, cudaStream_t st)
+{
+    if (s->d.block_rows == 4) return step2p_ty<PREC, CONV, DIFF, 14, KF>(s, src, st);
+    if (s->d.block_rows == 2) return step2p_ty<PREC, CONV, DIFF, 22, KF>(s, src, st);
+    return step2p_ty<PREC, CONV, DIFF, 30, KF>(s, src, st);
+}
+
 template <int PREC, int CONV, int DIFF>
 static cudaError_t step2p_t(const lbm_solver *s, int src, cudaStream_t st)
 {
-    if (s->d.per_cell_K) {
-        if (s->d.block_rows == 4) return step2p_ty<PREC, CONV, DIFF, 14, true>(s, src, st);
-        return step2p_ty<PREC, CONV, DIFF, 30, true>(s, src, st);
-    }
-    if (s->d.block_rows == 4) return step2p_ty<PREC, CONV, DIFF, 14, false>(s, src, st);
-    return step2p_ty<PREC, CONV, DIFF, 30, false>(s, src, st);
+    return s->d.per_cell_K ? step2p_k<PREC, CONV, DIFF, true>(s, src, st) : step2p_k<PREC, CONV, DIFF, false>(s, src, st);
 }
 
 }  // namespace lbm

@@ -57,8 +57,7 @@ def candidates(nx: int, prec: str):
     if prec != "f64":
         out.append(dict(kernel_variant=0, block_rows=0, steps_per_pass=2))
         out.append(dict(kernel_variant=0, block_rows=4, steps_per_pass=2))
-        out.append(dict(kernel_variant=5, block_rows=0, steps_per_pass=2))
-        out.append(dict(kernel_variant=5, block_rows=4, steps_per_pass=2))
+        out += [dict(kernel_variant=5, block_rows=b, steps_per_pass=2) for b in (0, 2, 4)]
         out += [dict(kernel_variant=3, block_rows=b, steps_per_pass=2) for b in (1, 2, 4, 8)]
     if prec == "f32":
         out.append(dict(kernel_variant=4, block_rows=0, steps_per_pass=2))

@@ -34,7 +34,8 @@ def main():
              (201, 90, (0, 0)), (190, 77, (1, 1))]
     configs = [("f64", 1, 1, 0), ("f32", 1, 1, 0), ("f32", 2, 1, 0), ("bf16s", 2, 1, 0),
                ("f32", 0, 2, 0), ("f32", 0, 2, 4), ("bf16s", 0, 2, 4), ("f32", 3, 2, 1),
-               ("f32", 4, 2, 0), ("f32", 5, 2, 0), ("f32", 5, 2, 4), ("bf16s", 5, 2, 0), ("bf16s", 5, 2, 4)]
+               ("f32", 4, 2, 0), ("f32", 5, 2, 0), ("f32", 5, 2, 4), ("bf16s", 5, 2, 0), ("bf16s", 5, 2, 4),
+               ("bf16s", 5, 2, 2)]
     coef = dict(conv=1, u=(0.06, -0.03), diff=2, K=(0.02, 0.008, 0.01), r1=-0.05)
     for nx, ny, bc in cases:
         phi0 = W.phi0_aniso(nx, seed=nx + ny, ny=ny)

@@ -444,10 +444,10 @@ PAIR_CASES = [(300, 250, (1, 1)), (257, 131, (0, 0)), (190, 64, (1, 0)), (129, 2
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16s"])
-@pytest.mark.parametrize("block_rows", [0, 4])
+@pytest.mark.parametrize("block_rows", [0, 2, 4])
 def test_pair_tiles_bit_identical_to_node_tiles(prec, block_rows):
     """The pair-tile kernel (two x-adjacent nodes per thread, paired loads and
-    stores, 62 x 14 or 62 x 30 tiles) performs every node's arithmetic in the
+    stores, 62 x 14, 62 x 22 or 62 x 30 tiles) performs every node's arithmetic in the
     same order as the one-node tile kernel: the two agree bit for bit, on grids
     with interior tiles, ragged edges, both wall kinds, every coefficient
     family, a per-node tensor field, and an odd step count; and both match the
