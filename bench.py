@@ -41,6 +41,9 @@ FP64_INST_PER_UPDATE = 118
 KERNEL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
               for f in ("kernels_step.cu", "kernels_step_vec.cu", "kernels_step2.cuh", "kernels_step2_f32.cu",
                         "kernels_step2_bf16.cu", "lbm_device.cuh")]
+PAIR_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
+            for f in ("kernels_step2p.cuh", "kernels_step2p_f32.cu", "kernels_step2p_bf16.cu", "kernels_step2.cuh",
+                      "lbm_device.cuh")]
 GENERAL_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
                for f in ("kernels_general.cuh", "kernels_general_f32.cu", "kernels_general_f64.cu", "lbm_device.cuh")]
 STEP2G_SRC = [os.path.join(ROOT, "paper_1603_09577_gb300", "csrc", f)
@@ -198,6 +201,21 @@ def traffic_per_launch(kernel_sha, key="k_step2"):
         return None
 
 
+def step_kernel(prec, spp, variant):
+    """Name of the step kernel a launch configuration runs, and its DRAM bytes per
+    launch from the committed ncu capture (None when there is none or the
+    kernel's sources changed since)."""
+    if spp == 2 and variant == 5:
+        return ("k_step2p (two fused pull-stream + collide steps per sweep, pair tiles)",
+                traffic_per_launch(src_sha(PAIR_SRC), f"k_step2p_{prec}"))
+    if spp == 2:
+        return ("k_step2 (two fused pull-stream + collide steps per sweep)",
+                traffic_per_launch(src_sha(KERNEL_SRC)) if prec == "f32" else None)
+    if variant == 2 or (variant == 0 and prec == "bf16s"):
+        return "k_step_v4 (fused pull-stream + collide, four nodes per thread)", None
+    return "k_step (fused pull-stream + collide)", None
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -251,7 +269,9 @@ def run_ensemble(args):
     all_inst = W.ensemble(count=args.ens_count)
     # independent instances: each rank runs its share, no exchange on the data path
     inst = [all_inst[i] for i in shard(all_inst, rank, world)] if world > 1 else all_inst
-    e = Ensemble(inst, steps_per_pass=args.ens_spp)
+    from paper_1603_09577_gb300 import tune
+    cfg = tune.tune_ensemble(inst, conv=0, diff=1) if args.ens_spp == 2 else {}
+    e = Ensemble(inst, steps_per_pass=args.ens_spp, **cfg)
     packed = e.pack([W.ensemble_phi0(d) for d in inst], dtype=torch.float32)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -348,10 +368,10 @@ def run_ensemble(args):
                       "parallelism": f"instances sharded over {world} ranks" if world > 1 else "single GPU"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak,
-                        "kernel": ("k_ens_step2 (one block per tile of all instances, two steps per launch, "
-                                   "graph-replayed)" if args.ens_spp == 2 else "k_ens_step (persistent, graph-replayed)"),
+                        "kernel": (f"k_ens_step2 (two steps per launch, graph-replayed, autotuned launch {cfg})"
+                                   if args.ens_spp == 2 else "k_ens_step (persistent, graph-replayed)"),
                         "peak_source": src},
-           "steps_per_launch": args.ens_spp,
+           "steps_per_launch": args.ens_spp, "tuner_timings": ensemble_tuner_timings(inst),
            "one_step_graph_mlups": nodes_r0 * steps / (ms_g1 / 1e3) / 1e6,
            "persistent_grid_graph_mlups": nodes_r0 * steps / (ms_pgrid / 1e3) / 1e6,
            "persistent_no_graph_mlups": nodes_r0 * steps / (ms_pers / 1e3) / 1e6,
@@ -772,9 +792,11 @@ def extra_c3(prec, lbm_steps, steps, warmup, fp64_phi, peak, src):
     r = c3_measure(prec, cfg, lbm_steps, steps, warmup)
     cells = p["nx"] * p["ny"]
     achieved = BYTES_PER_UPDATE[prec] * cells / (r["avg_launch_ms"] / 1e3) / 1e9
+    kernel, traffic = step_kernel(prec, cfg["steps_per_pass"], cfg["kernel_variant"])
     out = {"workload": f"{WORKLOAD}, {lbm_steps} steps per job, storage {prec}", "value": r["mlups"],
            "unit": "MLUPS", "ms_per_job": r["ms_per_job"], "timed_jobs": steps, "config": cfg,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "kernel": kernel, "traffic": traffic,
                         "algorithmic_bytes_per_launch": BYTES_PER_UPDATE[prec] * cells,
                         "avg_launch_ms": r["avg_launch_ms"], "peak_source": src,
                         "one_step_roof_mlups": peak * 1e3 / BYTES_PER_UPDATE[prec]},
@@ -851,13 +873,15 @@ def extra_ensemble(warmup, steps):
     step (256 launches per step)."""
     import torch
 
+    from paper_1603_09577_gb300 import tune
     from paper_1603_09577_gb300.ensemble import Ensemble
     inst = W.ensemble(count=256)
     lbm_steps = 1000
+    cfg = tune.tune_ensemble(inst, conv=0, diff=1)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
-        e = Ensemble(inst, steps_per_pass=2)
+        e = Ensemble(inst, steps_per_pass=2, **cfg)
         packed = e.pack([W.ensemble_phi0(d) for d in inst], dtype=torch.float32)
         e.set_phi(packed)
         e.capture(100)
@@ -889,9 +913,24 @@ def extra_ensemble(warmup, steps):
     return {"workload": f"ensemble_256: 256 instances, sides 64..1024 ({nodes} nodes), D(phi)=D0(1+phi), "
                         f"{lbm_steps} steps per job, FP32",
             "value": nodes * lbm_steps / (ms_graph / 1e3) / 1e6, "unit": "MLUPS",
-            "mode": "two steps per launch, one block per tile of all instances, 100-step CUDA graph replayed",
+            "mode": "two steps per launch over the tiles of all instances, 100-step CUDA graph replayed",
+            "autotuned_launch": cfg, "tuner_timings": ensemble_tuner_timings(inst),
             "per_instance_launches_mlups": nodes * lbm_steps / (ms_sep / 1e3) / 1e6,
             "speedup_vs_256_launches_per_step": ms_sep / ms_graph, "finite": finite, "clocks": clocks}
+
+
+def ensemble_tuner_timings(inst):
+    """The autotuner's per-candidate MLUPS for this ensemble (from its cache)."""
+    import json as _json
+
+    from paper_1603_09577_gb300 import tune
+    try:
+        with open(tune.cache_path()) as f:
+            entry = _json.load(f)[tune._ensemble_key(inst, 0, 1)]
+    except Exception:
+        return None
+    nodes = sum(d["nx"] * d["ny"] for d in inst)
+    return [{**c["config"], "mlups": nodes / (c["ms_per_step"] / 1e3) / 1e6} for c in entry["all"]]
 
 
 def extra_burgers(steps):
@@ -1077,16 +1116,13 @@ def main():
         alg_bytes = BYTES_PER_UPDATE[args.prec] * cells
         achieved = alg_bytes / (launch_ms / 1e3) / 1e9
         peak, src = measured_peak()
-        sha = src_sha(KERNEL_SRC)
-        kernel = ("k_step2 (two fused pull-stream + collide steps per sweep)" if args.spp == 2 else
-                  "k_step_v4 (fused pull-stream + collide, four nodes per thread)" if args.variant == 2 or
-                  (args.variant == 0 and args.prec == "bf16s") else "k_step (fused pull-stream + collide)")
+        kernel, traffic = step_kernel(args.prec, args.spp, args.variant)
         out = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.prec, "data": "synthetic", "config": config(args, lbm_steps),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic_per_launch(sha),
+                         "frac": achieved / peak, "traffic": traffic if nx == 4096 else None,
                          "kernel": kernel,
                          "one_step_roof_mlups": peak * 1e3 / BYTES_PER_UPDATE[args.prec],
                          "value_over_one_step_roof": value / world / (peak * 1e3 / BYTES_PER_UPDATE[args.prec]),

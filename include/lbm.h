@@ -308,16 +308,26 @@ int lbm_ensemble_info(lbm_ensemble e, long long *nodes, int *tiles, int *grid);
 /* Initial condition of every instance (Eq. 40) from the packed phi array. */
 int lbm_ensemble_set_phi(lbm_ensemble e, const void *dev_phi, int prec, void *stream);
 /* Persistent launches advance 1 (default) or 2 time steps each; with 2, every
-   launch runs the two-step shared-memory tile routine on 30 x 30 tiles of all
+   launch runs a two-step shared-memory tile routine on the tiles of all
    instances (two steps per sweep through HBM). Set before capturing a graph. */
 int lbm_ensemble_configure(lbm_ensemble e, int steps_per_pass);
 /* Grid of the two-step launches: persistent = 0 (default) launches one block
-   per 30 x 30 tile of the union tile list (all instances in one launch, the
-   hardware scheduler balancing the blocks); persistent = 1 launches SMs x
-   resident blocks that walk the list. One-step launches always use the
-   persistent grid over their 32 x 8 tiles (faster for tiles that small). Set
-   before capturing a graph. */
+   per tile of the union tile list (all instances in one launch, the hardware
+   scheduler balancing the blocks); persistent = 1 launches SMs x resident
+   blocks that walk the list with a fixed stride; persistent = 2 launches the
+   same grid, each block claiming the next tile from a counter in the workspace
+   when it finishes one (no device-side waits; the last block to leave resets
+   the counter, so launches on one stream and graph replays each start from
+   zero; launches of one ensemble must not overlap). The two-step lists hold the
+   largest instances' tiles first. One-step launches always use the persistent
+   grid over their 32 x 8 tiles (faster for tiles that small). Set before
+   capturing a graph. Results are identical bit for bit in every mode. */
 int lbm_ensemble_set_persistent(lbm_ensemble e, int persistent);
+/* Tiles of the two-step launches: pair_tiles = 0 (default) 30 x 30 output tiles
+   with one node per thread, 1 62 x 14 output tiles with two x-adjacent nodes
+   per thread (paired loads and stores; the routine of kernel_variant 5). The
+   results are identical bit for bit. Set before capturing a graph. */
+int lbm_ensemble_set_tiles(lbm_ensemble e, int pair_tiles);
 /* nsteps time steps; mode 0: one launch over all tiles per step (two steps per
    launch when configured, an odd remainder with one); mode 1: one launch per
    instance per step (one-step arithmetic, for comparison). */

@@ -106,6 +106,7 @@ SIGNATURES = {
     "lbm_ensemble_capture": [_VP, _I, _VP],
     "lbm_ensemble_configure": [_VP, _I],
     "lbm_ensemble_set_persistent": [_VP, _I],
+    "lbm_ensemble_set_tiles": [_VP, _I],
     "lbm_ensemble_replay": [_VP, _VP],
     "lbm_ensemble_get_phi": [_VP, _VP, _I, _VP],
     "lbm_ensemble_reduce": [_VP, _VP, _VP, _VP],

@@ -3,6 +3,7 @@
 // launches, and CUDA-graph capture / replay of many persistent steps.
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -15,8 +16,9 @@ namespace {
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct EnsLayout {
-    size_t off_inst = 0, off_tiles = 0, off_tiles2 = 0, off_err = 0, off_partials = 0, off_tbegin = 0, total = 0;
-    int ntiles = 0, ntiles2 = 0;
+    size_t off_inst = 0, off_tiles = 0, off_tiles2 = 0, off_tiles2p = 0, off_err = 0, off_partials = 0, off_tbegin = 0,
+           total = 0;
+    int ntiles = 0, ntiles2 = 0, ntiles2p = 0;
     std::vector<size_t> off_pop;    // per instance: buffer A offset (B follows)
     std::vector<long long> pitch;
 };
@@ -25,15 +27,17 @@ int ens_layout(int count, const int *nx, const int *ny, EnsLayout *L)
 {
     if (count < 1) return fail(LBM_EINVAL, "ensemble count must be >= 1");
     if (!nx || !ny) return fail(LBM_EINVAL, "null size arrays");
-    long long tiles = 0, tiles2 = 0;
+    long long tiles = 0, tiles2 = 0, tiles2p = 0;
     for (int i = 0; i < count; ++i) {
         if (nx[i] < 2 || ny[i] < 2) return fail(LBM_EINVAL, "instance " + std::to_string(i) + ": nx and ny must be >= 2");
         tiles += (long long)((nx[i] + kEnsTile - 1) / kEnsTile) * ((ny[i] + kEnsRows - 1) / kEnsRows);
         tiles2 += (long long)((nx[i] + kEns2Tile - 1) / kEns2Tile) * ((ny[i] + kEns2Tile - 1) / kEns2Tile);
+        tiles2p += (long long)((nx[i] + kEns2PCols - 1) / kEns2PCols) * ((ny[i] + kEns2PRows - 1) / kEns2PRows);
     }
     if (tiles > (1LL << 30)) return fail(LBM_EINVAL, "too many tiles");
     L->ntiles = (int)tiles;
     L->ntiles2 = (int)tiles2;
+    L->ntiles2p = (int)tiles2p;
     size_t off = 0;
     L->off_inst = off;
     off += up256(sizeof(EnsInst) * (size_t)count);
@@ -41,7 +45,9 @@ int ens_layout(int count, const int *nx, const int *ny, EnsLayout *L)
     off += up256(sizeof(int4) * (size_t)tiles);
     L->off_tiles2 = off;
     off += up256(sizeof(int4) * (size_t)tiles2);
-    L->off_err = off;
+    L->off_tiles2p = off;
+    off += up256(sizeof(int4) * (size_t)tiles2p);
+    L->off_err = off;                   // error word at +0, tile-claim counters at +128
     off += 256;
     L->off_partials = off;
     off += up256(8 * sizeof(double) * (size_t)tiles);
@@ -150,13 +156,28 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     }
     e->tile_begin[count] = (int)tiles.size();
     e->total_nodes = phi_off;
-    std::vector<int4> tiles2;
+    // two-step tile lists: largest instances first (the small instances' tiles,
+    // all along their wrapped edges, then fill the end of a launch), each
+    // instance's tiles row by row
+    std::vector<int> by_size(count);
+    for (int i = 0; i < count; ++i) by_size[i] = i;
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int a, int b) {
+        return (long long)nx[a] * ny[a] > (long long)nx[b] * ny[b];
+    });
+    std::vector<int4> tiles2, tiles2p;
     tiles2.reserve(L.ntiles2);
-    for (int i = 0; i < count; ++i)
+    tiles2p.reserve(L.ntiles2p);
+    for (int i : by_size) {
         for (int ty = 0; ty < ny[i]; ty += kEns2Tile)
             for (int tx = 0; tx < nx[i]; tx += kEns2Tile) tiles2.push_back(make_int4(i, tx, ty, 0));
+        for (int ty = 0; ty < ny[i]; ty += kEns2PRows)
+            for (int tx = 0; tx < nx[i]; tx += kEns2PCols) tiles2p.push_back(make_int4(i, tx, ty, 0));
+    }
     e->ntiles2 = (int)tiles2.size();
     e->d_tiles2 = (int4 *)(ws + L.off_tiles2);
+    e->ntiles2p = (int)tiles2p.size();
+    e->d_tiles2p = (int4 *)(ws + L.off_tiles2p);
+    e->d_claim = (int *)(ws + L.off_err + 128);
     e->d_inst = (EnsInst *)(ws + L.off_inst);
     e->d_tiles = (int4 *)(ws + L.off_tiles);
     e->err = (int *)(ws + L.off_err);
@@ -169,7 +190,9 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
                         "lbm_ensemble_create instance table");
     if (!rc) rc = cuda_check(cudaMemcpyAsync(e->d_tiles2, tiles2.data(), sizeof(int4) * tiles2.size(),
                                              cudaMemcpyHostToDevice, st), "lbm_ensemble_create two-step tile table");
-    if (!rc) rc = cuda_check(cudaMemsetAsync(e->err, 0, sizeof(int), st), "lbm_ensemble_create error word");
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(e->d_tiles2p, tiles2p.data(), sizeof(int4) * tiles2p.size(),
+                                             cudaMemcpyHostToDevice, st), "lbm_ensemble_create pair tile table");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(e->err, 0, 256, st), "lbm_ensemble_create error word and counters");
     if (!rc) rc = cuda_check(cudaMemcpyAsync(e->d_tiles, tiles.data(), sizeof(int4) * tiles.size(),
                                              cudaMemcpyHostToDevice, st), "lbm_ensemble_create tile table");
     if (!rc) rc = cuda_check(cudaMemcpyAsync(e->d_tile_begin, e->tile_begin, sizeof(int) * ((size_t)count + 1),
@@ -180,8 +203,10 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     const int per_sm = rc ? 0 : ens_occupancy_blocks(e->family);
     if (!rc && per_sm <= 0) rc = fail(LBM_ECUDA, "occupancy query failed");
-    const int per_sm2 = rc ? 0 : ens2_occupancy_blocks(e->family);
+    const int per_sm2 = rc ? 0 : ens2_occupancy_blocks(e->family, 0);
     if (!rc && per_sm2 <= 0) rc = fail(LBM_ECUDA, "occupancy query failed (two-step kernel)");
+    const int per_sm2p = rc ? 0 : ens2_occupancy_blocks(e->family, 1);
+    if (!rc && per_sm2p <= 0) rc = fail(LBM_ECUDA, "occupancy query failed (two-step pair kernel)");
     if (rc) {
         delete[] e->tile_begin;
         delete e;
@@ -189,6 +214,7 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
     }
     e->grid = sms * per_sm;
     e->grid2 = sms * per_sm2;
+    e->grid2p = sms * per_sm2p;
     *out = e;
     return LBM_OK;
 }
@@ -257,9 +283,18 @@ int lbm_ensemble_configure(lbm_ensemble e, int steps_per_pass)
 int lbm_ensemble_set_persistent(lbm_ensemble e, int persistent)
 {
     if (!e) return fail(LBM_EINVAL, "null ensemble");
-    if (persistent != 0 && persistent != 1) return fail(LBM_EINVAL, "persistent must be 0 or 1");
+    if (persistent < 0 || persistent > 2) return fail(LBM_EINVAL, "persistent must be 0, 1 or 2");
     if (e->exec) return fail(LBM_EINVAL, "choose the grid before capturing a graph");
     e->persistent2 = persistent;
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_tiles(lbm_ensemble e, int pair_tiles)
+{
+    if (!e) return fail(LBM_EINVAL, "null ensemble");
+    if (pair_tiles != 0 && pair_tiles != 1) return fail(LBM_EINVAL, "pair_tiles must be 0 or 1");
+    if (e->exec) return fail(LBM_EINVAL, "choose the tiles before capturing a graph");
+    e->shape2 = pair_tiles;
     return LBM_OK;
 }
 

@@ -44,8 +44,13 @@ struct lbm_ensemble_s {
     int count = 0, family = 0, ntiles = 0, grid = 0, parity = 0;
     int spp = 1;                    // time steps per persistent launch (1 or 2)
     int ntiles2 = 0, grid2 = 0;     // 30 x 30 tiles of the two-step kernel
-    int persistent2 = 0;            // 1: the two-step launch walks the list with grid2 blocks
+    int ntiles2p = 0, grid2p = 0;   // 62 x 14 pair tiles of the two-step kernel
+    int shape2 = 0;                 // two-step tiles: 0 30 x 30 (one node per thread), 1 62 x 14 (two)
+    int persistent2 = 0;            // two-step launch: 0 a block per tile, 1 persistent with a fixed
+                                    // stride, 2 persistent with tiles claimed from a counter
     int4 *d_tiles2 = nullptr;
+    int4 *d_tiles2p = nullptr;
+    int *d_claim = nullptr;         // tile counter and departed-block counter of mode 2
     lbm::EnsInst *d_inst = nullptr;
     int4 *d_tiles = nullptr;
     int *tile_begin = nullptr;      // host: first tile of each instance (count + 1)
@@ -61,8 +66,10 @@ struct lbm_ensemble_s {
 namespace lbm {
 cudaError_t ens_launch_step(const lbm_ensemble_s *e, int t_begin, int t_end, int blocks, cudaStream_t st);
 cudaError_t ens_launch_step2(const lbm_ensemble_s *e, cudaStream_t st);
-int ens2_occupancy_blocks(int family);
+int ens2_occupancy_blocks(int family, int shape);
 constexpr int kEns2Tile = 30;       // two-step tiles: 30 x 30 outputs
+constexpr int kEns2PCols = 62;      // two-step pair tiles: 62 x 14 outputs
+constexpr int kEns2PRows = 14;
 cudaError_t ens_launch_init(const lbm_ensemble_s *e, const void *phi, int in_prec, cudaStream_t st);
 cudaError_t ens_launch_get_phi(const lbm_ensemble_s *e, void *out, int out_prec, cudaStream_t st);
 // the eight statistics of every instance into out (count x 8 doubles)

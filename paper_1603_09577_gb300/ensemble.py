@@ -15,7 +15,7 @@ class Ensemble:
     rates; default `s`); the coefficient family (conv, diff) is shared."""
 
     def __init__(self, instances, conv=0, diff=1, s=(1.0, 1.2, 1.2, 0.0, 1.0, 0.0, 1.0, 1.1, 1.1), device=None,
-                 steps_per_pass: int = 1, persistent: bool = False):
+                 steps_per_pass: int = 1, persistent: int = 0, pair_tiles: bool = False):
         self.lib = C.lib()
         self.device = torch.device(device if device is not None else "cuda")
         n = len(instances)
@@ -37,8 +37,12 @@ class Ensemble:
         C.check(self.lib.lbm_ensemble_create(ctypes.byref(self.h), n, self.nx, self.ny, co, _ptr(self.workspace),
                                              size.value, _stream()))
         C.check(self.lib.lbm_ensemble_configure(self.h, int(steps_per_pass)))
-        # two-step launches: one block per tile (default) or a persistent grid
-        C.check(self.lib.lbm_ensemble_set_persistent(self.h, int(bool(persistent))))
+        # two-step launches: one block per tile (0, default), a persistent grid
+        # walking the tiles with a fixed stride (1) or claiming them (2); tiles of
+        # 30 x 30 nodes, or 62 x 14 with two nodes per thread (pair_tiles)
+        C.check(self.lib.lbm_ensemble_set_persistent(self.h, int(persistent)))
+        C.check(self.lib.lbm_ensemble_set_tiles(self.h, int(bool(pair_tiles))))
+        self.persistent, self.pair_tiles = int(persistent), bool(pair_tiles)
         self.steps_per_pass = int(steps_per_pass)
         nodes, tiles, grid = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
         C.check(self.lib.lbm_ensemble_info(self.h, ctypes.byref(nodes), ctypes.byref(tiles), ctypes.byref(grid)))

@@ -13,9 +13,18 @@ one-step kernel (rows per block) and the general two-step tile kernel.
 
     cfg = tune(4096, 4096, "f32", bc=("abb", "abb"), conv=0, diff=2)
     s = Solver(4096, 4096, prec="f32", bc=("abb", "abb"), **cfg)
+
+For a batched ensemble, tune_ensemble chooses the two-step launch: the tile
+shape (30 x 30 nodes, or 62 x 14 with two nodes per thread) and the grid (one
+block per tile, or a persistent grid walking the tiles with a fixed stride or
+claiming them from a counter), keyed by the instances' sizes and family:
+
+    cfg = tune_ensemble(instances, conv=0, diff=1)
+    e = Ensemble(instances, steps_per_pass=2, **cfg)
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 import threading
@@ -122,4 +131,75 @@ def tune(nx: int, ny: int, prec: str = "f32", bc=("periodic", "periodic"), conv:
         with open(tmp, "w") as f:
             json.dump(cache, f, indent=1)
         os.replace(tmp, path)
+        return dict(best)
+
+
+def ensemble_candidates():
+    """Two-step ensemble launches: tile shape x grid (0 one block per tile, 1
+    persistent with a fixed stride, 2 persistent claiming tiles)."""
+    return [dict(pair_tiles=pt, persistent=m) for pt in (False, True) for m in (0, 1, 2)]
+
+
+def _ensemble_key(instances, conv, diff):
+    sig = hashlib.sha256(json.dumps([[int(d["nx"]), int(d["ny"])] for d in instances]).encode()).hexdigest()[:16]
+    dev = torch.cuda.get_device_name()
+    return f"{dev}|ensemble|{len(instances)}|{sig}|c{conv}d{diff}"
+
+
+def _load(path):
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                return json.load(f)
+        except (OSError, ValueError):
+            pass
+    return {}
+
+
+def _save(path, cache):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, path)
+
+
+def tune_ensemble(instances, conv: int = 0, diff: int = 1, steps: int = 20, reps: int = 3,
+                  use_cache: bool = True) -> dict:
+    """Fastest two-step launch (kwargs pair_tiles, persistent for Ensemble) for
+    these instances; every candidate computes the same state bit for bit."""
+    from .ensemble import Ensemble
+    key = _ensemble_key(instances, conv, diff)
+    path = cache_path()
+    with _lock:
+        cache = _load(path) if use_cache else {}
+        if use_cache and key in cache:
+            return dict(cache[key]["config"])
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        timings = []
+        with torch.cuda.stream(side):
+            phi = None
+            for cfg in ensemble_candidates():
+                e = Ensemble(instances, conv=conv, diff=diff, steps_per_pass=2, **cfg)
+                if phi is None:
+                    g = torch.Generator(device="cuda").manual_seed(0)
+                    phi = 0.5 + 0.1 * torch.rand(e.nodes, generator=g, device="cuda", dtype=torch.float32)
+                e.set_phi(phi)
+                e.step(steps)                                # warm-up
+                best = float("inf")
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(side)
+                    e.step(steps)
+                    b.record(side)
+                    b.synchronize()
+                    best = min(best, a.elapsed_time(b) / steps)
+                timings.append((best, cfg))
+                del e
+        torch.cuda.current_stream().wait_stream(side)
+        ms, best = min(timings, key=lambda t: t[0])
+        cache[key] = {"config": best, "ms_per_step": ms,
+                      "all": [{"config": c, "ms_per_step": t} for t, c in timings]}
+        _save(path, cache)
         return dict(best)

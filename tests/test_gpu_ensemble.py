@@ -174,3 +174,61 @@ def test_ensemble_per_instance_reductions():
     e.set_phi(e.pack(bad))
     counts = [st["nonfinite"] for st in e.reduce()]
     assert counts == [0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]
+
+
+def mixed_instances():
+    """Small instances plus two with interior tiles of both two-step shapes."""
+    out = small_instances()
+    extra = W.ensemble(count=2, seed=23)
+    for d, (nx, ny) in zip(extra, [(260, 150), (199, 131)]):
+        out.append(dict(d, nx=nx, ny=ny, xc=nx / 3, yc=ny / 2, sigma=nx / 10))
+    return out
+
+
+@pytest.mark.parametrize("pair_tiles", [False, True])
+@pytest.mark.parametrize("persistent", [0, 1, 2])
+def test_ensemble_two_step_launches_agree_bitwise(pair_tiles, persistent):
+    """Every two-step launch of the ensemble (30 x 30 or 62 x 14 pair tiles; one
+    block per tile, a strided persistent grid, or a persistent grid claiming
+    tiles from a counter) gives the same state bit for bit, directly and when
+    replayed from a CUDA graph (the claim counter starts from zero in every
+    replay), and the state matches the oracle."""
+    inst = mixed_instances()
+    phis = [W.ensemble_phi0(d) for d in inst]
+    base = Ensemble(inst, steps_per_pass=2)
+    base.set_phi(base.pack(phis))
+    base.step(61)
+    want = base.phi().cpu()
+    e = Ensemble(inst, steps_per_pass=2, persistent=persistent, pair_tiles=pair_tiles)
+    e.set_phi(e.pack(phis))
+    e.step(61)
+    assert torch.equal(e.phi().cpu(), want)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        e.set_phi(e.pack(phis))
+        e.capture(20)
+        for _ in range(3):
+            e.replay()
+        e.step(1)
+    torch.cuda.current_stream().wait_stream(side)
+    assert torch.equal(e.phi().cpu(), want)
+    got = e.unpack(want)
+    for i in (len(inst) - 2, len(inst) - 1, 0):
+        key = (repr(sorted(inst[i].items())), 61)
+        if key not in _ORACLE:
+            _ORACLE[key] = oracle_phi(inst[i], phis[i], 61)
+        assert rel(got[i].numpy(), _ORACLE[key]) <= 1e-5
+
+
+def test_ensemble_autotuner_picks_a_candidate_and_caches(tmp_path, monkeypatch):
+    from paper_1603_09577_gb300 import tune
+    monkeypatch.setenv("LBM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    inst = mixed_instances()
+    cfg = tune.tune_ensemble(inst, conv=0, diff=1, steps=4, reps=1)
+    assert cfg in tune.ensemble_candidates()
+    import json
+    cache = json.loads((tmp_path / "tune.json").read_text())
+    (key, entry), = cache.items()
+    assert "ensemble" in key and len(entry["all"]) == len(tune.ensemble_candidates())
+    assert tune.tune_ensemble(inst, conv=0, diff=1) == cfg           # from the cache
