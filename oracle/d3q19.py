@@ -14,7 +14,12 @@ relaxes rho with s0, j with the 3 x 3 block A = (K / (d c_s^2) + I/2)^-1
 equal, the choice of the remaining 15 rows does not matter; they are completed
 here by a QR factorisation. The collision is Eq. 34 written with the matrices
 P = M^-1 S M and Q = M^-1 (I - S/2) M, and the streaming is a pull with
-periodic wrap. Arrays: populations (19, nz, ny, nx), phi (nz, ny, nx),
+periodic wrap, or, on an axis with anti-bounce-back walls, the anti-bounce-back
+rule of the 2-D model (Sec. 3.6) applied to every link whose source lies beyond
+a wall half-way between the boundary node and the missing node:
+    fbar_k(x, t+1) = -fbar*_opp(k)(x, t) + feq_k(phi_w) + feq_opp(k)(phi_w),
+phi_w the wall's value, the mean of the walls' values for a link that crosses
+two or three walls. Arrays: populations (19, nz, ny, nx), phi (nz, ny, nx),
 velocity index k in the order of Eq. 6.
 """
 from __future__ import annotations
@@ -47,6 +52,8 @@ class Spec3:
     se: float = 1.0                   # rate of every moment other than rho and j
     r0: float = 0.0
     r1: float = 0.0
+    bc: tuple = (0, 0, 0)             # per axis x, y, z: 0 periodic, 1 anti-bounce-back walls
+    phi_wall: tuple = (0.0, 0.0, 0.0, 0.0, 0.0, 0.0)   # x-, x+, y-, y+, z-, z+
 
 
 def k_matrix(K) -> np.ndarray:
@@ -136,15 +143,61 @@ def init(spec: Spec3, phi0) -> np.ndarray:
     return out.reshape(Q19, spec.nz, spec.ny, spec.nx)
 
 
+def opposite(k: int) -> int:
+    """The direction with c_opp = -c_k."""
+    return int(np.flatnonzero((CX == -CX[k]) & (CY == -CY[k]) & (CZ == -CZ[k]))[0])
+
+
+def wall_links(spec: Spec3, k: int):
+    """For direction k: a mask (nz, ny, nx) of the nodes whose source x - c_k
+    lies beyond a wall, and the wall value phi_w of each such link."""
+    shape = (spec.nz, spec.ny, spec.nx)
+    idx = np.indices(shape)                                      # z, y, x
+    coords = (idx[2], idx[1], idx[0])
+    c = (CX[k], CY[k], CZ[k])
+    n = (spec.nx, spec.ny, spec.nz)
+    total = np.zeros(shape)
+    count = np.zeros(shape)
+    for ax in range(3):
+        if not spec.bc[ax] or c[ax] == 0:
+            continue
+        src = coords[ax] - c[ax]
+        low, high = src < 0, src >= n[ax]
+        total += low * spec.phi_wall[2 * ax] + high * spec.phi_wall[2 * ax + 1]
+        count += low | high
+    mask = count > 0
+    return mask, np.where(mask, total / np.maximum(count, 1), 0.0)
+
+
+_WALLS = {}
+
+
+def _wall_terms(spec: Spec3):
+    """(k, opp(k), mask, feq at the links' wall values) for every direction with
+    links beyond a wall; computed once per problem."""
+    key = (spec.nx, spec.ny, spec.nz, tuple(spec.bc), tuple(spec.phi_wall), spec.conv, tuple(spec.u), spec.diff)
+    if key not in _WALLS:
+        out = []
+        for k in range(1, Q19):
+            mask, phiw = wall_links(spec, k)
+            if mask.any():
+                out.append((k, opposite(k), mask, feq(spec, phiw[mask])))
+        _WALLS[key] = out
+    return _WALLS[key]
+
+
 def step(spec: Spec3, F, P=None, Qm=None):
-    """Pull streaming with periodic wrap, then the collision. Returns the new
-    state and phi(t_{n+1})."""
+    """Pull streaming (periodic wrap, anti-bounce-back at walls), then the
+    collision. Returns the new state and phi(t_{n+1})."""
     if P is None:
         P, Qm = pq_matrices(spec)
     pulled = np.empty_like(F)
     for k in range(Q19):
         # f_k(x) = f*_k(x - c_k): np.roll by +c_k along each axis
         pulled[k] = np.roll(F[k], shift=(CZ[k], CY[k], CX[k]), axis=(0, 1, 2))
+    if any(spec.bc):
+        for k, ko, mask, fe in _wall_terms(spec):
+            pulled[k][mask] = -F[ko][mask] + fe[k] + fe[ko]
     out, phi = collide(spec, pulled.reshape(Q19, -1), P, Qm)
     shape = (spec.nz, spec.ny, spec.nx)
     return out.reshape((Q19,) + shape), phi.reshape(shape)

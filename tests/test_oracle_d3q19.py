@@ -164,3 +164,82 @@ def test_spectral_exact_linear_3d():
     assert np.linalg.norm(got - phiN) / np.linalg.norm(phiN) <= 1e-12
     # the hill is not trivially constant: the run changed phi by far more than the tolerance
     assert np.linalg.norm(phiN - phi0) / np.linalg.norm(phi0) > 1e-3
+
+
+# ---- anti-bounce-back walls in 3-D: the Sec. 3.6 channel embedded in D3Q19 ----
+
+def slip3(N, se, s3, axis=1, u_par=(0.0, 0.0), n_other=(2, 3), steps=None):
+    """Steady unidirectional problem of Sec. 3.6 (walls half-way outside the
+    first and last node along `axis`, phi = 0 below and 1 above, source
+    R = 2 kappa / N^2, K = kappa I) on a D3Q19 lattice periodic along the two
+    other axes, which carry the velocity u_par. Returns the profile along the
+    wall-normal axis and the largest spread across the periodic axes."""
+    kap = D.CS2 * (1.0 / s3 - 0.5)
+    n = [0, 0, 0]
+    others = [a for a in range(3) if a != axis]
+    n[axis] = N
+    n[others[0]], n[others[1]] = n_other
+    u = [0.0, 0.0, 0.0]
+    u[others[0]], u[others[1]] = u_par
+    bc = [0, 0, 0]
+    bc[axis] = 1
+    walls = [0.0] * 6
+    walls[2 * axis + 1] = 1.0
+    sp = D.Spec3(nx=n[0], ny=n[1], nz=n[2], conv=0, u=tuple(u), K=(kap, 0, 0, kap, 0, kap), se=se,
+                 r0=2 * kap / N ** 2, bc=tuple(bc), phi_wall=tuple(walls))
+    F = D.init(sp, np.zeros((n[2], n[1], n[0])))
+    P, Qm = D.pq_matrices(sp)
+    phi = None
+    for _ in range(steps or int(60 * N * N / kap) + 200):
+        F, phi = D.step(sp, F, P, Qm)
+    prof = np.moveaxis(phi, 2 - axis, 0).reshape(N, -1)
+    return prof.mean(axis=1), float(np.ptp(prof, axis=1).max())
+
+
+def eq72b(N, se, s3):
+    yb = (np.arange(N) + 0.5) / N                    # Eq. 71 node positions
+    return yb * (2 - yb) + (se * s3 - 8 * (se + s3) + 16) / (12 * N ** 2 * se * s3)
+
+
+@pytest.mark.parametrize("N,se,s3,u_par", [(4, 1.0, 0.6, (0.0, 0.0)), (6, 0.8, 0.3, (0.04, -0.03)),
+                                            (5, 1.7, 1.0, (0.1, 0.0)), (4, 0.7, 0.7, (0.0, 0.05))])
+def test_channel_exact_slip_in_3d(N, se, s3, u_par):
+    """The y-walled channel in D3Q19: the steady state equals Eq. 71 plus the
+    slip of Eq. 72b with s1 -> s_e (72a when s_e = s3) to 1e-12, with flow along
+    the periodic axes; the D3Q19 lattice projects onto the same three-velocity
+    weights along y as D2Q9."""
+    prof, spread = slip3(N, se, s3, 1, u_par)
+    assert spread < 1e-13
+    assert np.abs(prof - eq72b(N, se, s3)).max() < 1e-12
+
+
+def test_channel_walls_on_every_axis_and_zero_slip():
+    """Walls along x, y or z give the same exact profile; the rate of R14
+    (s_e = 8 (2 - s3) / (8 - s3)) removes the slip."""
+    N, s3 = 5, 0.6
+    for axis in (0, 1, 2):
+        prof, _ = slip3(N, 1.1, s3, axis, (0.02, 0.01))
+        assert np.abs(prof - eq72b(N, 1.1, s3)).max() < 1e-12, axis
+    se = 8 * (2 - s3) / (8 - s3)
+    prof, _ = slip3(N, se, s3, 2)
+    yb = (np.arange(N) + 0.5) / N
+    assert np.abs(prof - yb * (2 - yb)).max() < 1e-12
+
+
+def test_walled_box_fixed_point_and_bounds():
+    """With walls on all three axes: a uniform field at the walls' common value
+    is a fixed point (edge and corner links included), and with walls at 0 and 1
+    and no source the field stays within [0, 1] (maximum principle)."""
+    sp = D.Spec3(nx=5, ny=4, nz=6, conv=1, u=(0.08, -0.05, 0.04), diff=1, K=(0.02, 0.004, -0.003, 0.015, 0.002, 0.012),
+                 se=1.2, bc=(1, 1, 1), phi_wall=(0.6,) * 6)
+    F = D.init(sp, np.full((6, 4, 5), 0.6))
+    for _ in range(30):
+        F, phi = D.step(sp, F)
+    assert np.abs(phi - 0.6).max() < 1e-14
+    rng = np.random.default_rng(5)
+    sp = D.Spec3(nx=7, ny=6, nz=5, conv=0, u=(0.01, 0.0, -0.01), K=(0.05, 0.0, 0.0, 0.05, 0.0, 0.05), se=1.0,
+                 bc=(1, 1, 1), phi_wall=(0.0, 1.0, 0.0, 1.0, 1.0, 0.0))
+    F = D.init(sp, rng.uniform(0, 1, (5, 6, 7)))
+    for _ in range(200):
+        F, phi = D.step(sp, F)
+        assert phi.min() >= -1e-12 and phi.max() <= 1 + 1e-12
