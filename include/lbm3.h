@@ -13,7 +13,8 @@
  *     fbar*_k = fbar_k - s_e (fbar_k - feq_k) - c_k . G / 10 + (1 - s_e/2) R_k,
  *     G = (A - s_e I) [(j - B) + B' R / 2],
  * independent of how the other 15 rows are chosen. Lattice units c = 1,
- * c_s^2 = 1/3, d = 1; periodic boundaries on all axes.
+ * c_s^2 = 1/3, d = 1; periodic boundaries or anti-bounce-back Dirichlet walls
+ * per axis.
  *
  * Conventions as in lbm.h: int status (LBM_OK or an LBM_E* code, message from
  * lbm_last_error()), caller-owned device workspace (256-byte aligned) and
@@ -41,6 +42,14 @@ typedef struct {
                                h = M* - sum_k g_k, float arithmetic, as in lbm.h) */
     int block_rows;         /* rows of 32-thread warps per block: 0 (= 8), 1, 2,
                                4 or 8                                             */
+    int bc[3];              /* per axis x, y, z: LBM_PERIODIC or LBM_ABB
+                               (anti-bounce-back walls half-way beyond the first
+                               and last node, the rule of Sec. 3.6: a link whose
+                               source lies beyond a wall takes -fbar*_opp(k) of
+                               the node plus feq_k + feq_opp(k) at the wall
+                               value; a link crossing two or three walls takes
+                               their mean value)                                  */
+    double phi_wall[6];     /* wall values: x-, x+, y-, y+, z-, z+               */
 } lbm3_desc;
 
 typedef struct {

@@ -4,7 +4,8 @@
 // One thread per node, x fastest (warps of 32 along x), a grid of
 // (x tiles, y tiles, z). Every step pulls the 19 populations f_k(x) =
 // f*_k(x - c_k) with periodic wrap (19 reads and 19 writes per update: 152 B
-// in FP32), then collides in the projector form of the moment reading (see
+// in FP32), replaces the links that cross an anti-bounce-back wall at wall
+// nodes, then collides in the projector form of the moment reading (see
 // lbm3.h): feq of Eq. 3 per direction, the flux block acting on j - B, and the
 // Scheme B source.
 #include <math.h>
@@ -41,6 +42,8 @@ __host__ __device__ constexpr C w3(int k)
 {
     return k == 0 ? C(1) / C(3) : (k <= 6 ? C(1) / C(18) : C(1) / C(36));
 }
+// Eq. 6 lists every velocity next to its opposite: (1, 2), (3, 4), ..., (17, 18)
+__host__ __device__ constexpr int opp3(int k) { return k == 0 ? 0 : (k % 2 ? k + 1 : k - 1); }
 
 // Storage of the 19 planes: FP64, FP32, or BF16 deviations g_k = f*_k - w_k phi
 // plus an FP32 shift plane h = M* - sum_k g_k (as for D2Q9: the stored node
@@ -97,6 +100,9 @@ struct Params3 {
     C ux, uy, uz;
     C r0, r1, half_r0, inv_den, inv_post;
     int has_src;
+    int abb[3];                      // 1: anti-bounce-back walls on axis x, y, z
+    int any_abb;
+    C phi_wall[6];                   // x-, x+, y-, y+, z-, z+
     int *err;                        // checked builds: index-fault word
 };
 
@@ -203,9 +209,33 @@ k_step3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__r
         const int zs = c3z(k) > 0 ? zm : (c3z(k) < 0 ? zp : z);
         f[k] = S::ld(src + k * P, ((long long)zs * p.ny + ys) * p.pitch + xs, src_h, w3<T>(k));
     }
+    const long long own = ((long long)z * p.ny + y) * p.pitch + x;
+    if (p.any_abb) {
+        const bool wall = (p.abb[0] && (x == 0 || x == p.nx - 1)) || (p.abb[1] && (y == 0 || y == p.ny - 1)) ||
+                          (p.abb[2] && (z == 0 || z == p.nz - 1));
+        if (wall) {
+            // anti-bounce-back (the rule of the 2-D walls, Sec. 3.6): a link whose
+            // source lies beyond a wall takes -fbar*_opp(k) of this node plus
+            // feq_k + feq_opp(k) at the wall value (the mean value of the walls
+            // the link crosses)
+#pragma unroll
+            for (int k = 1; k < 19; ++k) {
+                const int xs = x - c3x(k), ys = y - c3y(k), zs = z - c3z(k);
+                T tot = T(0);
+                int cnt = 0;
+                if (p.abb[0] && (xs < 0 || xs >= p.nx)) { tot += xs < 0 ? p.phi_wall[0] : p.phi_wall[1]; ++cnt; }
+                if (p.abb[1] && (ys < 0 || ys >= p.ny)) { tot += ys < 0 ? p.phi_wall[2] : p.phi_wall[3]; ++cnt; }
+                if (p.abb[2] && (zs < 0 || zs >= p.nz)) { tot += zs < 0 ? p.phi_wall[4] : p.phi_wall[5]; ++cnt; }
+                if (cnt) {
+                    const T phiw = cnt == 1 ? tot : tot / T(cnt);
+                    const Coef3<CONV, DIFF, T> q(p, phiw);
+                    f[k] = q.feq(k, phiw) + q.feq(opp3(k), phiw) - S::ld(src + opp3(k) * P, own, src_h, w3<T>(opp3(k)));
+                }
+            }
+        }
+    }
     T phi;
     collide3<CONV, DIFF, T>(p, f, phi);
-    const long long own = ((long long)z * p.ny + y) * p.pitch + x;
     S::store(dst, dst_h, P, own, f, phi);
 }
 
@@ -290,6 +320,11 @@ int check_desc3(const lbm3_desc *d)
     const int b = d->block_rows;
     if (!(b == 0 || b == 1 || b == 2 || b == 4 || b == 8)) return fail(LBM_EINVAL, "block_rows must be 0, 1, 2, 4 or 8");
     if (d->ny > 65535 * 8 || d->nz > 65535) return fail(LBM_EINVAL, "ny or nz exceeds the launch grid");
+    for (int a = 0; a < 3; ++a)
+        if (d->bc[a] != LBM_PERIODIC && d->bc[a] != LBM_ABB)
+            return fail(LBM_EINVAL, "D3Q19 boundaries are LBM_PERIODIC or LBM_ABB per axis");
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(d->phi_wall[i])) return fail(LBM_EINVAL, "non-finite wall value");
     return LBM_OK;
 }
 
@@ -346,6 +381,9 @@ Params3<T> params3(const lbm3_solver *s)
     p.inv_den = (T)(1.0 / (1.0 - 0.5 * s->c.r1));
     p.inv_post = (T)(1.0 / (1.0 + 0.5 * s->c.r1));
     p.has_src = s->c.r0 != 0.0 || s->c.r1 != 0.0;
+    for (int a = 0; a < 3; ++a) p.abb[a] = s->d.bc[a] == LBM_ABB;
+    p.any_abb = p.abb[0] || p.abb[1] || p.abb[2];
+    for (int i = 0; i < 6; ++i) p.phi_wall[i] = (T)s->d.phi_wall[i];
     p.err = s->err;
     return p;
 }

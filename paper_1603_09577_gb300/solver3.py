@@ -11,14 +11,20 @@ from .solver import REDUCE_KEYS, _prec_of, _ptr, _stream
 
 
 class Solver3:
-    """One periodic D3Q19 lattice of nx x ny x nz nodes; fields are (nz, ny, nx)."""
+    """One D3Q19 lattice of nx x ny x nz nodes; fields are (nz, ny, nx).
+    bc: per axis (x, y, z) "periodic" or "abb" (anti-bounce-back walls with the
+    values phi_wall = (x-, x+, y-, y+, z-, z+))."""
 
-    def __init__(self, nx: int, ny: int, nz: int, prec: str = "f32", block_rows: int = 0, device=None):
+    def __init__(self, nx: int, ny: int, nz: int, prec: str = "f32", block_rows: int = 0, device=None,
+                 bc=("periodic", "periodic", "periodic"), phi_wall=(0.0,) * 6):
+        from .solver import BC
         self.lib = C.lib()
         self.nx, self.ny, self.nz, self.prec = int(nx), int(ny), int(nz), prec
         self.device = torch.device(device if device is not None else "cuda")
         d = C.Desc3()
         d.nx, d.ny, d.nz, d.prec, d.block_rows = self.nx, self.ny, self.nz, C.PREC[prec], int(block_rows)
+        d.bc[:] = [BC[b] for b in bc]
+        d.phi_wall[:] = [float(v) for v in phi_wall]
         size = ctypes.c_size_t()
         C.check(self.lib.lbm3_workspace_size(ctypes.byref(d), ctypes.byref(size)))
         self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)

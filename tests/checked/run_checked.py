@@ -76,12 +76,14 @@ def main():
     # D3Q19
     from oracle import d3q19 as D3
     from paper_1603_09577_gb300 import Solver3
-    for nx, ny, nz in [(21, 9, 6), (5, 33, 3), (40, 2, 4)]:
+    for nx, ny, nz, bc in [(21, 9, 6, (0, 0, 0)), (5, 33, 3, (0, 0, 0)), (40, 2, 4, (0, 0, 0)), (21, 9, 6, (1, 1, 1)),
+                           (33, 4, 5, (1, 0, 1))]:
         c3 = dict(conv=1, u=(0.05, -0.03, 0.02), diff=1, K=(0.02, 0.004, -0.003, 0.015, 0.002, 0.012), se=1.2)
+        pw = (0.1, 0.2, 0.3, 0.4, 0.5, 0.6)
         phi3 = np.random.default_rng(nx).uniform(0.2, 0.8, (nz, ny, nx))
-        ref3 = D3.run(D3.Spec3(nx=nx, ny=ny, nz=nz, **c3), phi3, 6)
+        ref3 = D3.run(D3.Spec3(nx=nx, ny=ny, nz=nz, bc=bc, phi_wall=pw, **c3), phi3, 6)
         for prec in ("f64", "f32", "bf16s"):
-            s3 = Solver3(nx, ny, nz, prec=prec).set_coeffs(**c3)
+            s3 = Solver3(nx, ny, nz, prec=prec, bc=["abb" if b else "periodic" for b in bc], phi_wall=pw).set_coeffs(**c3)
             s3.set_phi(torch.from_numpy(phi3).cuda())
             s3.step(6)
             got = s3.phi().cpu().numpy()

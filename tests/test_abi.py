@@ -240,6 +240,15 @@ def test_d3q19_descriptions_and_coefficients():
     assert L.lbm3_workspace_size(ctypes.byref(d3(prec=C.LBM_BF16S)), ctypes.byref(n)) == 0
     for bad in (dict(nz=1), dict(prec=7), dict(block_rows=3)):
         assert L.lbm3_workspace_size(ctypes.byref(d3(**bad)), ctypes.byref(n)) == C.LBM_EINVAL
+    walled = d3()
+    walled.bc[:] = [1, 0, 1]
+    walled.phi_wall[:] = [0.1, 0.2, 0.0, 0.0, 0.5, 0.6]
+    assert L.lbm3_workspace_size(ctypes.byref(walled), ctypes.byref(n)) == 0
+    walled.bc[1] = 2                                        # extrapolation is not built in 3-D
+    assert L.lbm3_workspace_size(ctypes.byref(walled), ctypes.byref(n)) == C.LBM_EINVAL
+    walled.bc[1] = 0
+    walled.phi_wall[3] = float("nan")
+    assert L.lbm3_workspace_size(ctypes.byref(walled), ctypes.byref(n)) == C.LBM_EINVAL
     d = d3()
     L.lbm3_workspace_size(ctypes.byref(d), ctypes.byref(n))
     ws = FakeWorkspace(n.value)

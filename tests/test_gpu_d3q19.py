@@ -106,3 +106,50 @@ def test_d3q19_checkpoint_resume(prec):
     assert torch.equal(first, t.phi().cpu())
     ref = D.run(D.Spec3(nx=nx, ny=ny, nz=nz, **coef), phi0.cpu().numpy(), 20)
     assert rel(first.numpy(), ref) <= TOL[prec]
+
+
+WALLS = [((1, 0, 0), (0.2, 0.7, 0, 0, 0, 0)), ((0, 1, 1), (0, 0, 0.1, 0.9, 0.5, 0.3)),
+         ((1, 1, 1), (0.3, 0.6, 0.2, 0.8, 0.4, 0.5)), ((0, 0, 1), (0, 0, 0, 0, 0.0, 1.0))]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16s"])
+@pytest.mark.parametrize("walls", WALLS, ids=["x", "yz", "xyz", "z"])
+@pytest.mark.parametrize("case", CASES[:3], ids=[f"{c[0]}x{c[1]}x{c[2]}" for c in CASES[:3]])
+def test_d3q19_walls_parity(prec, walls, case):
+    """Anti-bounce-back walls on one, two or all three axes (edge and corner
+    links included) against the oracle, on ragged grids with every flux family
+    and sources, all elements."""
+    nx, ny, nz, coef = case
+    bc, pw = walls
+    rng = np.random.default_rng(nx + 7 * ny + 31 * nz)
+    phi0 = rng.uniform(0.2, 0.8, (nz, ny, nx))
+    ref = D.run(D.Spec3(nx=nx, ny=ny, nz=nz, bc=bc, phi_wall=pw, **coef), phi0, 25)
+    names = ["abb" if b else "periodic" for b in bc]
+    s = Solver3(nx, ny, nz, prec=prec, bc=names, phi_wall=pw).set_coeffs(**coef)
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    s.step(25)
+    got = s.phi().cpu().numpy()
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+    band = np.zeros_like(got, dtype=bool)
+    for ax, b in zip((2, 1, 0), bc):
+        if b:
+            idx = [slice(None)] * 3
+            idx[ax] = [0, got.shape[ax] - 1]
+            band[tuple(idx)] = True
+    assert float(np.linalg.norm((got - ref)[band]) / np.linalg.norm(ref[band])) <= TOL[prec]
+
+
+def test_d3q19_channel_slip_on_the_gpu():
+    """The Sec. 3.6 channel embedded in 3-D (walls along y, periodic x and z,
+    flow along x): the FP64 GPU state reaches Eq. 71 with the slip of Eq. 72b
+    (s1 -> s_e) to 1e-12, as the oracle does."""
+    N, se, s3 = 6, 0.8, 0.3
+    kap = D.CS2 * (1.0 / s3 - 0.5)
+    s = Solver3(4, N, 3, prec="f64", bc=("periodic", "abb", "periodic"), phi_wall=(0, 0, 0, 1, 0, 0))
+    s.set_coeffs(conv=0, u=(0.04, 0.0, -0.03), K=(kap, 0, 0, kap, 0, kap), se=se, r0=2 * kap / N ** 2)
+    s.set_phi(torch.zeros((3, N, 4), dtype=torch.float64, device="cuda"))
+    s.step(int(60 * N * N / kap) + 200)
+    phi = s.phi().cpu().numpy()
+    yb = (np.arange(N) + 0.5) / N
+    exact = yb * (2 - yb) + (se * s3 - 8 * (se + s3) + 16) / (12 * N ** 2 * se * s3)
+    assert np.abs(phi - exact[None, :, None]).max() < 1e-12
