@@ -650,7 +650,8 @@ def run_gaussian3d(args):
 
     phi0 = hill(0.0).to(torch.float64 if prec == "f64" else torch.float32).contiguous()   # bf16s takes FP32 input
     exact = hill(float(lbm_steps)).contiguous()
-    s = Solver3(n, n, n, prec=prec).set_coeffs(conv=0, u=u, K=K, se=1.1)
+    s = Solver3(n, n, n, prec=prec, kernel_variant=args.variant, block_rows=args.block_rows).set_coeffs(
+        conv=0, u=u, K=K, se=1.1)
     red = torch.zeros(8, dtype=torch.float64, device="cuda")
     st = torch.cuda.current_stream()
 
@@ -690,7 +691,9 @@ def run_gaussian3d(args):
                                   f"{lbm_steps} steps per job", "nx": n, "ny": n, "nz": n,
                       "l2": "inputs larger than L2 (two population buffers of 0.67 to 2.5 GB each)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": None, "kernel": "k_step3 (D3Q19 fused pull-stream + collide)",
+                        "traffic": None,
+                        "kernel": ("k_step3p (D3Q19 fused pull-stream + collide, two nodes per thread)"
+                                   if args.variant == 2 else "k_step3 (D3Q19 fused pull-stream + collide)"),
                         "algorithmic_bytes_per_update": bpu, "avg_launch_ms": launch_ms,
                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src},
            "gre_vs_eq60": g[1] / g[2], "gpu_launches": args.steps * (1 + lbm_steps + 2)}
@@ -935,8 +938,8 @@ def ensemble_tuner_timings(inst):
 
 def extra_burgers(steps):
     """Sub-record of the 1024^2 Burgers workload (5000 steps per job): FP64, FP32
-    and BF16S storage (two steps per pass with 30 x 30 tiles for the last two),
-    MLUPS and the relative L2 difference of phi from the FP64 path."""
+    and BF16S storage (the autotuned launch for the last two), MLUPS and the
+    relative L2 difference of phi from the FP64 path."""
     import torch
 
     from paper_1603_09577_gb300 import Solver
@@ -946,8 +949,9 @@ def extra_burgers(steps):
     st = torch.cuda.current_stream()
     clk = clocks_sampler()
     res, phis = {}, {}
-    for prec, cfg in (("f64", {}), ("f32", dict(steps_per_pass=2, block_rows=4)),
-                      ("bf16s", dict(steps_per_pass=2, block_rows=4))):
+    from paper_1603_09577_gb300 import tune
+    tuned = {pr: tune.tune(n, n, pr, conv=p["conv"], diff=p["diff"]) for pr in ("f32", "bf16s")}
+    for prec, cfg in (("f64", {}), ("f32", tuned["f32"]), ("bf16s", tuned["bf16s"])):
         phi0 = torch.from_numpy(phi0_np.astype(np.float64 if prec == "f64" else np.float32)).cuda()
         s = Solver(n, n, prec=prec, **cfg)
         s.set_coeffs(conv=p["conv"], u=p["u"], diff=p["diff"], K=p["K"], s=W.s9())

@@ -38,26 +38,34 @@ __device__ __forceinline__ void ens_tile2(const EnsInst *__restrict__ inst, int4
 }
 
 // MODE 1: blocks walk the list with the grid's stride (launched with one block
-// per tile, each takes exactly one); 2: tiles claimed from claim[0] (claim[1]
-// counts the blocks that left)
+// per tile, each takes exactly one); 2: tiles claimed from claim[0], one tile
+// ahead (claim[1] counts the blocks that left)
 template <int CONV, int DIFF, int SHAPE, int MODE>
 __global__ void __launch_bounds__(kT2Threads, 4)
 k_ens_step2(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int ntiles, int parity, int *claim)
 {
     extern __shared__ __align__(16) float sm_e[];
-    __shared__ int next;
+    __shared__ int next[2];
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
-    int t = blockIdx.x;
-    for (;;) {
-        if (MODE == 2) {
-            if (lead) next = atomicAdd(claim, 1);
-            __syncthreads();
-            t = next;
-        }
-        if (t >= ntiles) break;
+    int t = blockIdx.x, b = 0;
+    if (MODE == 2) {
+        if (lead) next[0] = atomicAdd(claim, 1);
+        __syncthreads();
+        t = next[0];
+    }
+    while (t < ntiles) {
+        // claim the following tile while this one runs; the barrier that ends
+        // the tile publishes it (slot b ^ 1 was last read before the previous
+        // barrier)
+        if (MODE == 2 && lead) next[b ^ 1] = atomicAdd(claim, 1);
         ens_tile2<CONV, DIFF, SHAPE>(inst, __ldg(tiles + t), parity, sm_e);
-        __syncthreads();                 // the next tile overwrites shared memory (and `next`)
-        if (MODE == 1) t += gridDim.x;
+        __syncthreads();                 // the next tile overwrites shared memory
+        if (MODE == 2) {
+            b ^= 1;
+            t = next[b];
+        } else {
+            t += gridDim.x;
+        }
     }
     if (MODE == 2 && lead) {
         __threadfence();

@@ -19,165 +19,9 @@
 #include "lbm3.h"
 #include "lbm_internal.h"
 
+#include "lbm3_device.cuh"
+
 namespace lbm {
-
-// Eq. 6: D3Q19 velocities in the paper's order and weights
-__host__ __device__ constexpr int c3x(int k)
-{
-    constexpr int v[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1, 0, 0, 0, 0};
-    return v[k];
-}
-__host__ __device__ constexpr int c3y(int k)
-{
-    constexpr int v[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-    return v[k];
-}
-__host__ __device__ constexpr int c3z(int k)
-{
-    constexpr int v[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1};
-    return v[k];
-}
-template <class C>
-__host__ __device__ constexpr C w3(int k)
-{
-    return k == 0 ? C(1) / C(3) : (k <= 6 ? C(1) / C(18) : C(1) / C(36));
-}
-// Eq. 6 lists every velocity next to its opposite: (1, 2), (3, 4), ..., (17, 18)
-__host__ __device__ constexpr int opp3(int k) { return k == 0 ? 0 : (k % 2 ? k + 1 : k - 1); }
-
-// Storage of the 19 planes: FP64, FP32, or BF16 deviations g_k = f*_k - w_k phi
-// plus an FP32 shift plane h = M* - sum_k g_k (as for D2Q9: the stored node
-// sums to its post-collision mass up to FP32 rounding).
-template <int PREC> struct St3;
-template <> struct St3<LBM_F64> {
-    using T = double;
-    using C = double;
-    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
-    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C)
-    {
-#pragma unroll
-        for (int k = 0; k < 19; ++k) __stcs(f + k * P + i, v[k]);
-    }
-};
-template <> struct St3<LBM_F32> {
-    using T = float;
-    using C = float;
-    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
-    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C)
-    {
-#pragma unroll
-        for (int k = 0; k < 19; ++k) __stcs(f + k * P + i, v[k]);
-    }
-};
-template <> struct St3<LBM_BF16S> {
-    using T = __nv_bfloat16;
-    using C = float;
-    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *__restrict__ h, C w)
-    {
-        return fmaf(w, __ldg(h + i), __bfloat162float(f[i]));
-    }
-    __device__ static __forceinline__ void store(T *__restrict__ f, float *__restrict__ h, long long P, long long i,
-                                                 const C v[19], C phi)
-    {
-        C mass = C(0), gsum = C(0);
-#pragma unroll
-        for (int k = 0; k < 19; ++k) {
-            const T g = __float2bfloat16_rn(fmaf(-w3<float>(k), phi, v[k]));
-            mass += v[k];
-            gsum += __bfloat162float(g);
-            f[k * P + i] = g;
-        }
-        h[i] = mass - gsum;
-    }
-};
-
-template <class C>
-struct Params3 {
-    int nx, ny, nz;
-    long long pitch, plane;          // plane = pitch * ny * nz
-    C se, hse;                       // s_e and 1 - s_e/2
-    C G[6];                          // A - s_e I: xx, xy, xz, yy, yz, zz
-    C ux, uy, uz;
-    C r0, r1, half_r0, inv_den, inv_post;
-    int has_src;
-    int abb[3];                      // 1: anti-bounce-back walls on axis x, y, z
-    int any_abb;
-    C phi_wall[6];                   // x-, x+, y-, y+, z-, z+
-    int *err;                        // checked builds: index-fault word
-};
-
-// Coefficients at phi (Eq. 7 families, D = g(phi) I): B, B', the tensor
-// Q = C + c_s^2 g I - c_s^2 phi I of Eq. 3 and trQ/3, and R = r0 + r1 phi.
-template <int CONV, int DIFF, class C>
-struct Coef3 {
-    C Bx, By, Bz, bpx, bpy, bpz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, tr3, R;
-    __device__ __forceinline__ Coef3(const Params3<C> &p, C phi)
-    {
-        C cphi;
-        if (CONV == 0) {
-            Bx = p.ux * phi; By = p.uy * phi; Bz = p.uz * phi;
-            bpx = p.ux; bpy = p.uy; bpz = p.uz;
-            cphi = phi;
-        } else {
-            const C h = C(0.5) * phi * phi;
-            Bx = p.ux * h; By = p.uy * h; Bz = p.uz * h;
-            bpx = p.ux * phi; bpy = p.uy * phi; bpz = p.uz * phi;
-            cphi = phi * phi * phi * C(1.0 / 3.0);
-        }
-        C g;
-        if (DIFF == 0) g = phi;
-        else if (DIFF == 1) g = phi + C(0.5) * phi * phi;
-        else g = phi + phi * phi * phi * C(1.0 / 3.0);
-        const C diag = (g - phi) * C(1.0 / 3.0);
-        Qxx = p.ux * p.ux * cphi + diag; Qyy = p.uy * p.uy * cphi + diag; Qzz = p.uz * p.uz * cphi + diag;
-        Qxy = p.ux * p.uy * cphi; Qxz = p.ux * p.uz * cphi; Qyz = p.uy * p.uz * cphi;
-        tr3 = (Qxx + Qyy + Qzz) * C(1.0 / 3.0);
-        R = p.has_src ? p.r1 * phi + p.r0 : C(0);
-    }
-    // feq_k = w_k [phi + 3 c.B + 4.5 (c Q c - trQ/3)] (Eq. 3)
-    __device__ __forceinline__ C feq(int k, C phi) const
-    {
-        const C cx_ = C(c3x(k)), cy_ = C(c3y(k)), cz_ = C(c3z(k));
-        const C cB = cx_ * Bx + cy_ * By + cz_ * Bz;
-        const C cQc = cx_ * cx_ * Qxx + cy_ * cy_ * Qyy + cz_ * cz_ * Qzz +
-                      C(2) * (cx_ * cy_ * Qxy + cx_ * cz_ * Qxz + cy_ * cz_ * Qyz);
-        return w3<C>(k) * (phi + C(3) * cB + C(4.5) * (cQc - tr3));
-    }
-    // R_k = w_k (1 + 3 c.B') R (Eq. 9, Scheme B)
-    __device__ __forceinline__ C source(int k) const
-    {
-        return w3<C>(k) * (C(1) + C(3) * (C(c3x(k)) * bpx + C(c3y(k)) * bpy + C(c3z(k)) * bpz)) * R;
-    }
-};
-
-template <int CONV, int DIFF, class C>
-__device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_out)
-{
-    C rho = C(0), jx = C(0), jy = C(0), jz = C(0);
-#pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        rho += f[k];
-        if (c3x(k)) jx += C(c3x(k)) * f[k];
-        if (c3y(k)) jy += C(c3y(k)) * f[k];
-        if (c3z(k)) jz += C(c3z(k)) * f[k];
-    }
-    const C phi = (rho + p.half_r0) * p.inv_den;                 // Eq. 35
-    phi_out = phi;
-    const Coef3<CONV, DIFF, C> q(p, phi);
-    // G = (A - s_e I) [(j - B) + B' R / 2]
-    const C vx = (jx - q.Bx) + C(0.5) * q.bpx * q.R, vy = (jy - q.By) + C(0.5) * q.bpy * q.R;
-    const C vz = (jz - q.Bz) + C(0.5) * q.bpz * q.R;
-    const C Gx = (p.G[0] * vx + p.G[1] * vy + p.G[2] * vz) * C(0.1);
-    const C Gy = (p.G[1] * vx + p.G[3] * vy + p.G[4] * vz) * C(0.1);
-    const C Gz = (p.G[2] * vx + p.G[4] * vy + p.G[5] * vz) * C(0.1);
-#pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        const C cG = C(c3x(k)) * Gx + C(c3y(k)) * Gy + C(c3z(k)) * Gz;
-        C v = f[k] - p.se * (f[k] - q.feq(k, phi)) - cG;
-        if (p.has_src) v += p.hse * q.source(k);
-        f[k] = v;
-    }
-}
 
 template <int PREC, int CONV, int DIFF>
 __global__ void __launch_bounds__(256)
@@ -190,53 +34,11 @@ k_step3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__r
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
-    int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
-    int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
-    int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
-    LBM_CHK(xm, p.nx, p.err, kErrX);
-    LBM_CHK(xp, p.nx, p.err, kErrX);
-    LBM_CHK(ym, p.ny, p.err, kErrY);
-    LBM_CHK(yp, p.ny, p.err, kErrY);
-    LBM_CHK(zm, p.nz, p.err, kErrIndex);
-    LBM_CHK(zp, p.nz, p.err, kErrIndex);
-    const long long P = p.plane;
     T f[19];
-#pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        // source node x - c_k
-        const int xs = c3x(k) > 0 ? xm : (c3x(k) < 0 ? xp : x);
-        const int ys = c3y(k) > 0 ? ym : (c3y(k) < 0 ? yp : y);
-        const int zs = c3z(k) > 0 ? zm : (c3z(k) < 0 ? zp : z);
-        f[k] = S::ld(src + k * P, ((long long)zs * p.ny + ys) * p.pitch + xs, src_h, w3<T>(k));
-    }
-    const long long own = ((long long)z * p.ny + y) * p.pitch + x;
-    if (p.any_abb) {
-        const bool wall = (p.abb[0] && (x == 0 || x == p.nx - 1)) || (p.abb[1] && (y == 0 || y == p.ny - 1)) ||
-                          (p.abb[2] && (z == 0 || z == p.nz - 1));
-        if (wall) {
-            // anti-bounce-back (the rule of the 2-D walls, Sec. 3.6): a link whose
-            // source lies beyond a wall takes -fbar*_opp(k) of this node plus
-            // feq_k + feq_opp(k) at the wall value (the mean value of the walls
-            // the link crosses)
-#pragma unroll
-            for (int k = 1; k < 19; ++k) {
-                const int xs = x - c3x(k), ys = y - c3y(k), zs = z - c3z(k);
-                T tot = T(0);
-                int cnt = 0;
-                if (p.abb[0] && (xs < 0 || xs >= p.nx)) { tot += xs < 0 ? p.phi_wall[0] : p.phi_wall[1]; ++cnt; }
-                if (p.abb[1] && (ys < 0 || ys >= p.ny)) { tot += ys < 0 ? p.phi_wall[2] : p.phi_wall[3]; ++cnt; }
-                if (p.abb[2] && (zs < 0 || zs >= p.nz)) { tot += zs < 0 ? p.phi_wall[4] : p.phi_wall[5]; ++cnt; }
-                if (cnt) {
-                    const T phiw = cnt == 1 ? tot : tot / T(cnt);
-                    const Coef3<CONV, DIFF, T> q(p, phiw);
-                    f[k] = q.feq(k, phiw) + q.feq(opp3(k), phiw) - S::ld(src + opp3(k) * P, own, src_h, w3<T>(opp3(k)));
-                }
-            }
-        }
-    }
+    pull3_node<PREC, CONV, DIFF>(p, src, src_h, x, y, z, f);
     T phi;
     collide3<CONV, DIFF, T>(p, f, phi);
-    S::store(dst, dst_h, P, own, f, phi);
+    S::store(dst, dst_h, p.plane, ((long long)z * p.ny + y) * p.pitch + x, f, phi);
 }
 
 template <int PREC, int CONV, int DIFF>
@@ -325,6 +127,9 @@ int check_desc3(const lbm3_desc *d)
             return fail(LBM_EINVAL, "D3Q19 boundaries are LBM_PERIODIC or LBM_ABB per axis");
     for (int i = 0; i < 6; ++i)
         if (!isfinite(d->phi_wall[i])) return fail(LBM_EINVAL, "non-finite wall value");
+    if (d->kernel_variant < 0 || d->kernel_variant > 2) return fail(LBM_EINVAL, "kernel_variant must be 0, 1 or 2");
+    if (d->kernel_variant == 2 && d->prec == LBM_F64)
+        return fail(LBM_EUNSUPPORTED, "two nodes per thread is built for LBM_F32 and LBM_BF16S");
     return LBM_OK;
 }
 
@@ -400,6 +205,11 @@ cudaError_t launch3_t(const lbm3_solver *s, const void *phi0, int in_prec, cudaS
 {
     using T = typename St3<PREC>::T;
     const auto p = params3<typename St3<PREC>::C>(s);
+    if constexpr (PREC != LBM_F64) {
+        if (!phi0 && s->d.kernel_variant == 2)
+            return launch3_pairs(PREC, CONV * 3 + DIFF, p, s->d.block_rows, s->pop[s->cur], s->hpl[s->cur],
+                                 s->pop[s->cur ^ 1], s->hpl[s->cur ^ 1], st);
+    }
     if (phi0)
         k_init3<PREC, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, phi0, in_prec, (T *)s->pop[s->cur], s->hpl[s->cur]);
     else
