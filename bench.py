@@ -75,6 +75,10 @@ def parse():
                     help="skip the sub-records (BF16S, FP64, adjoint, ensemble, 1024^2 Burgers) of the default run")
     ap.add_argument("--ens-count", type=int, default=256, help="instances of the ensemble workload")
     ap.add_argument("--ens-spp", type=int, default=2, help="time steps per persistent ensemble launch (1 or 2)")
+    ap.add_argument("--ens-launch", default=None,
+                    help="PERSISTENT,PAIR: the two-step ensemble launch to use instead of the autotuner's (with "
+                         "--ens-only, time that launch alone, e.g. for a profiler capture)")
+    ap.add_argument("--ens-only", action="store_true", help="ensemble workload: time the chosen launch only")
     ap.add_argument("--bf-spp", type=int, default=2, help="time steps per launch of the Burgers-Fisher workload")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "ensemble_256", "adjoint_512", "burgers_fisher_4096", "stability_sweep",
@@ -270,7 +274,11 @@ def run_ensemble(args):
     # independent instances: each rank runs its share, no exchange on the data path
     inst = [all_inst[i] for i in shard(all_inst, rank, world)] if world > 1 else all_inst
     from paper_1603_09577_gb300 import tune
-    cfg = tune.tune_ensemble(inst, conv=0, diff=1) if args.ens_spp == 2 else {}
+    if args.ens_launch:
+        pers, pair = (int(v) for v in args.ens_launch.split(","))
+        cfg = dict(persistent=pers, pair_tiles=bool(pair))
+    else:
+        cfg = tune.tune_ensemble(inst, conv=0, diff=1) if args.ens_spp == 2 else {}
     e = Ensemble(inst, steps_per_pass=args.ens_spp, **cfg)
     packed = e.pack([W.ensemble_phi0(d) for d in inst], dtype=torch.float32)
     side = torch.cuda.Stream()
@@ -309,6 +317,11 @@ def run_ensemble(args):
         clk = clocks_sampler()
         ms_graph = max_over_ranks(timed(job_graph, args.steps, side), device="cuda")
         clocks = clocks_summary(clk)
+        if args.ens_only:
+            nodes = sum(d["nx"] * d["ny"] for d in inst)
+            print(json.dumps({"metric": "MLUPS", "value": nodes * steps / (ms_graph / 1e3) / 1e6, "unit": "MLUPS",
+                              "ensemble_launch": cfg, "ms_per_step": ms_graph, "clocks": clocks}), flush=True)
+            return
         ms_pers = timed(job_persistent, max(1, args.steps // 2), side)
         ep = Ensemble(inst, steps_per_pass=args.ens_spp, persistent=True)
         ep.set_phi(packed)
@@ -650,8 +663,7 @@ def run_gaussian3d(args):
 
     phi0 = hill(0.0).to(torch.float64 if prec == "f64" else torch.float32).contiguous()   # bf16s takes FP32 input
     exact = hill(float(lbm_steps)).contiguous()
-    s = Solver3(n, n, n, prec=prec, kernel_variant=args.variant, block_rows=args.block_rows).set_coeffs(
-        conv=0, u=u, K=K, se=1.1)
+    s = Solver3(n, n, n, prec=prec, block_rows=args.block_rows).set_coeffs(conv=0, u=u, K=K, se=1.1)
     red = torch.zeros(8, dtype=torch.float64, device="cuda")
     st = torch.cuda.current_stream()
 
@@ -691,9 +703,7 @@ def run_gaussian3d(args):
                                   f"{lbm_steps} steps per job", "nx": n, "ny": n, "nz": n,
                       "l2": "inputs larger than L2 (two population buffers of 0.67 to 2.5 GB each)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": None,
-                        "kernel": ("k_step3p (D3Q19 fused pull-stream + collide, two nodes per thread)"
-                                   if args.variant == 2 else "k_step3 (D3Q19 fused pull-stream + collide)"),
+                        "traffic": None, "kernel": "k_step3 (D3Q19 fused pull-stream + collide)",
                         "algorithmic_bytes_per_update": bpu, "avg_launch_ms": launch_ms,
                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src},
            "gre_vs_eq60": g[1] / g[2], "gpu_launches": args.steps * (1 + lbm_steps + 2)}

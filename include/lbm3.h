@@ -50,9 +50,6 @@ typedef struct {
                                value; a link crossing two or three walls takes
                                their mean value)                                  */
     double phi_wall[6];     /* wall values: x-, x+, y-, y+, z-, z+               */
-    int kernel_variant;     /* 0 or 1: one node per thread; 2: two x-adjacent
-                               nodes per thread with paired loads and stores and
-                               packed FP32x2 collisions (LBM_F32, LBM_BF16S)      */
 } lbm3_desc;
 
 typedef struct {

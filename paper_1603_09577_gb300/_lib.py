@@ -44,8 +44,7 @@ class Coeffs(ctypes.Structure):
 
 class Desc3(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("prec", ctypes.c_int),
-                ("block_rows", ctypes.c_int), ("bc", ctypes.c_int * 3), ("phi_wall", ctypes.c_double * 6),
-                ("kernel_variant", ctypes.c_int)]
+                ("block_rows", ctypes.c_int), ("bc", ctypes.c_int * 3), ("phi_wall", ctypes.c_double * 6)]
 
 
 class Coeffs3(ctypes.Structure):

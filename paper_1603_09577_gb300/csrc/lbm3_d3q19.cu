@@ -23,7 +23,7 @@
 
 namespace lbm {
 
-template <int PREC, int CONV, int DIFF>
+template <int PREC, int CONV, int DIFF, bool WALLS>
 __global__ void __launch_bounds__(256)
 k_step3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__restrict__ src,
         const float *__restrict__ src_h, typename St3<PREC>::T *__restrict__ dst, float *__restrict__ dst_h)
@@ -35,7 +35,7 @@ k_step3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__r
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     T f[19];
-    pull3_node<PREC, CONV, DIFF>(p, src, src_h, x, y, z, f);
+    pull3_node<PREC, CONV, DIFF, WALLS>(p, src, src_h, x, y, z, f);
     T phi;
     collide3<CONV, DIFF, T>(p, f, phi);
     S::store(dst, dst_h, p.plane, ((long long)z * p.ny + y) * p.pitch + x, f, phi);
@@ -127,9 +127,6 @@ int check_desc3(const lbm3_desc *d)
             return fail(LBM_EINVAL, "D3Q19 boundaries are LBM_PERIODIC or LBM_ABB per axis");
     for (int i = 0; i < 6; ++i)
         if (!isfinite(d->phi_wall[i])) return fail(LBM_EINVAL, "non-finite wall value");
-    if (d->kernel_variant < 0 || d->kernel_variant > 2) return fail(LBM_EINVAL, "kernel_variant must be 0, 1 or 2");
-    if (d->kernel_variant == 2 && d->prec == LBM_F64)
-        return fail(LBM_EUNSUPPORTED, "two nodes per thread is built for LBM_F32 and LBM_BF16S");
     return LBM_OK;
 }
 
@@ -205,16 +202,14 @@ cudaError_t launch3_t(const lbm3_solver *s, const void *phi0, int in_prec, cudaS
 {
     using T = typename St3<PREC>::T;
     const auto p = params3<typename St3<PREC>::C>(s);
-    if constexpr (PREC != LBM_F64) {
-        if (!phi0 && s->d.kernel_variant == 2)
-            return launch3_pairs(PREC, CONV * 3 + DIFF, p, s->d.block_rows, s->pop[s->cur], s->hpl[s->cur],
-                                 s->pop[s->cur ^ 1], s->hpl[s->cur ^ 1], st);
-    }
     if (phi0)
         k_init3<PREC, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, phi0, in_prec, (T *)s->pop[s->cur], s->hpl[s->cur]);
+    else if (p.any_abb)
+        k_step3<PREC, CONV, DIFF, true><<<grid3(s), block3(s), 0, st>>>(p, (const T *)s->pop[s->cur], s->hpl[s->cur],
+                                                                        (T *)s->pop[s->cur ^ 1], s->hpl[s->cur ^ 1]);
     else
-        k_step3<PREC, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, (const T *)s->pop[s->cur], s->hpl[s->cur],
-                                                                  (T *)s->pop[s->cur ^ 1], s->hpl[s->cur ^ 1]);
+        k_step3<PREC, CONV, DIFF, false><<<grid3(s), block3(s), 0, st>>>(p, (const T *)s->pop[s->cur], s->hpl[s->cur],
+                                                                         (T *)s->pop[s->cur ^ 1], s->hpl[s->cur ^ 1]);
     return cudaGetLastError();
 }
 

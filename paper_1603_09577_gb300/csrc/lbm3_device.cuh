@@ -170,9 +170,10 @@ __device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_ou
     }
 }
 
-// Pull the 19 populations of node (x, y, z) with periodic wrap, then replace
-// the links that cross an anti-bounce-back wall (at wall nodes only).
-template <int PREC, int CONV, int DIFF>
+// Pull the 19 populations of node (x, y, z) with periodic wrap; WALLS: then
+// replace the links that cross an anti-bounce-back wall (at wall nodes only).
+// A lattice without walls compiles without the wall code.
+template <int PREC, int CONV, int DIFF, bool WALLS>
 __device__ __forceinline__ void pull3_node(const Params3<typename St3<PREC>::C> &p,
                                            const typename St3<PREC>::T *__restrict__ src,
                                            const float *__restrict__ src_h, int x, int y, int z,
@@ -198,8 +199,8 @@ __device__ __forceinline__ void pull3_node(const Params3<typename St3<PREC>::C> 
         const int zs = c3z(k) > 0 ? zm : (c3z(k) < 0 ? zp : z);
         f[k] = S::ld(src + k * P, ((long long)zs * p.ny + ys) * p.pitch + xs, src_h, w3<T>(k));
     }
-    const long long own = ((long long)z * p.ny + y) * p.pitch + x;
-    if (p.any_abb) {
+    if constexpr (WALLS) {
+        const long long own = ((long long)z * p.ny + y) * p.pitch + x;
         const bool wall = (p.abb[0] && (x == 0 || x == p.nx - 1)) || (p.abb[1] && (y == 0 || y == p.ny - 1)) ||
                           (p.abb[2] && (z == 0 || z == p.nz - 1));
         if (wall) {
@@ -224,9 +225,5 @@ __device__ __forceinline__ void pull3_node(const Params3<typename St3<PREC>::C> 
         }
     }
 }
-
-// the step with two x-adjacent nodes per thread (lbm3_pairs.cu)
-cudaError_t launch3_pairs(int prec, int family, const Params3<float> &p, int block_rows, const void *src,
-                          const float *src_h, void *dst, float *dst_h, cudaStream_t st);
 
 }  // namespace lbm

@@ -16,7 +16,7 @@ class Solver3:
     values phi_wall = (x-, x+, y-, y+, z-, z+))."""
 
     def __init__(self, nx: int, ny: int, nz: int, prec: str = "f32", block_rows: int = 0, device=None,
-                 bc=("periodic", "periodic", "periodic"), phi_wall=(0.0,) * 6, kernel_variant: int = 0):
+                 bc=("periodic", "periodic", "periodic"), phi_wall=(0.0,) * 6):
         from .solver import BC
         self.lib = C.lib()
         self.nx, self.ny, self.nz, self.prec = int(nx), int(ny), int(nz), prec
@@ -25,7 +25,6 @@ class Solver3:
         d.nx, d.ny, d.nz, d.prec, d.block_rows = self.nx, self.ny, self.nz, C.PREC[prec], int(block_rows)
         d.bc[:] = [BC[b] for b in bc]
         d.phi_wall[:] = [float(v) for v in phi_wall]
-        d.kernel_variant = int(kernel_variant)
         size = ctypes.c_size_t()
         C.check(self.lib.lbm3_workspace_size(ctypes.byref(d), ctypes.byref(size)))
         self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)

@@ -154,21 +154,3 @@ def test_d3q19_channel_slip_on_the_gpu():
     exact = yb * (2 - yb) + (se * s3 - 8 * (se + s3) + 16) / (12 * N ** 2 * se * s3)
     assert np.abs(phi - exact[None, :, None]).max() < 1e-12
 
-
-@pytest.mark.parametrize("prec", ["f32", "bf16s"])
-@pytest.mark.parametrize("walls", [((0, 0, 0), (0,) * 6)] + WALLS[1:3], ids=["periodic", "yz", "xyz"])
-@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}" for c in CASES])
-def test_d3q19_pair_kernel_parity(prec, walls, case):
-    """The step with two x-adjacent nodes per thread (kernel_variant 2, odd and
-    even nx, interior and edge pairs) against the oracle, all elements."""
-    nx, ny, nz, coef = case
-    bc, pw = walls
-    rng = np.random.default_rng(3 * nx + ny + nz)
-    phi0 = rng.uniform(0.2, 0.8, (nz, ny, nx))
-    ref = D.run(D.Spec3(nx=nx, ny=ny, nz=nz, bc=bc, phi_wall=pw, **coef), phi0, 25)
-    names = ["abb" if b else "periodic" for b in bc]
-    s = Solver3(nx, ny, nz, prec=prec, bc=names, phi_wall=pw, kernel_variant=2).set_coeffs(**coef)
-    s.set_phi(torch.from_numpy(phi0).cuda())
-    s.step(25)
-    got = s.phi().cpu().numpy()
-    assert rel(got, ref) <= TOL[prec], rel(got, ref)
