@@ -17,7 +17,7 @@
 
 namespace lbm {
 
-template <int CONV, int DIFF, int SHAPE, bool PRE_SYNC>
+template <int CONV, int DIFF, int SHAPE>
 __device__ __forceinline__ void ens_tile2(const EnsInst *__restrict__ inst, int4 tl, int parity, float *sm)
 {
     const EnsInst I = inst[tl.x];
@@ -27,23 +27,19 @@ __device__ __forceinline__ void ens_tile2(const EnsInst *__restrict__ inst, int4
     const int tx0 = tl.y, ty0 = tl.z;
     if (SHAPE == 0) {
         const bool interior = tx0 >= 2 && tx0 + kTX + 1 <= p.nx - 1 && ty0 >= 2 && ty0 + 30 + 1 <= p.ny - 1;
-        if (interior) two_steps<LBM_F32, CONV, DIFF, true, 30, false, PRE_SYNC>(p, src, nullptr, dst, nullptr, sm, tx0, ty0);
-        else two_steps<LBM_F32, CONV, DIFF, false, 30, false, PRE_SYNC>(p, src, nullptr, dst, nullptr, sm, tx0, ty0);
+        if (interior) two_steps<LBM_F32, CONV, DIFF, true, 30, false>(p, src, nullptr, dst, nullptr, sm, tx0, ty0);
+        else two_steps<LBM_F32, CONV, DIFF, false, 30, false>(p, src, nullptr, dst, nullptr, sm, tx0, ty0);
     } else {
         constexpr int TY = kEns2PRows;
         const bool interior = tx0 >= 2 && tx0 + kPRX <= p.nx - 1 && ty0 >= 2 && ty0 + TY + 1 <= p.ny - 1;
-        if (interior)
-            two_steps_pair<LBM_F32, CONV, DIFF, true, TY, false, PRE_SYNC>(p, src, nullptr, dst, nullptr, sm, tx0, ty0);
-        else two_steps_pair_edge<LBM_F32, CONV, DIFF, TY, false, PRE_SYNC>(p, src, nullptr, dst, nullptr, sm, tx0, ty0);
+        if (interior) two_steps_pair<LBM_F32, CONV, DIFF, true, TY, false>(p, src, nullptr, dst, nullptr, sm, tx0, ty0);
+        else two_steps_pair_edge<LBM_F32, CONV, DIFF, TY, false>(p, src, nullptr, dst, nullptr, sm, tx0, ty0);
     }
 }
 
 // MODE 0: one block per tile; 1: a persistent grid walking the list with the
 // grid's stride; 2: a persistent grid claiming tiles from claim[0], one tile
-// ahead (claim[1] counts the blocks that left). In the persistent modes the
-// barrier that keeps a tile's step A from overwriting the region the previous
-// tile's step B still reads sits inside step A, after the first row's loads
-// (PRE_SYNC), instead of ending every tile.
+// ahead (claim[1] counts the blocks that left).
 template <int CONV, int DIFF, int SHAPE, int MODE>
 __global__ void __launch_bounds__(kT2Threads, 4)
 k_ens_step2(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int ntiles, int parity, int *claim)
@@ -51,7 +47,7 @@ k_ens_step2(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, in
     extern __shared__ __align__(16) float sm_e[];
     __shared__ int next[2];
     if (MODE == 0) {
-        ens_tile2<CONV, DIFF, SHAPE, false>(inst, __ldg(tiles + blockIdx.x), parity, sm_e);
+        ens_tile2<CONV, DIFF, SHAPE>(inst, __ldg(tiles + blockIdx.x), parity, sm_e);
         return;
     }
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
@@ -62,11 +58,12 @@ k_ens_step2(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, in
         t = next[0];
     }
     while (t < ntiles) {
-        // claim the following tile while this one runs: this tile's barriers
-        // publish it, and slot b ^ 1 was last read before the previous tile's
-        // barriers
+        // claim the following tile while this one runs; the barrier that ends
+        // the tile publishes it (slot b ^ 1 was last read before the previous
+        // barrier)
         if (MODE == 2 && lead) next[b ^ 1] = atomicAdd(claim, 1);
-        ens_tile2<CONV, DIFF, SHAPE, true>(inst, __ldg(tiles + t), parity, sm_e);
+        ens_tile2<CONV, DIFF, SHAPE>(inst, __ldg(tiles + t), parity, sm_e);
+        __syncthreads();                 // the next tile overwrites shared memory
         if (MODE == 2) {
             b ^= 1;
             t = next[b];

@@ -186,11 +186,7 @@ __device__ __forceinline__ void step2_B(const Params<float> &p, const Params<F2>
     }
 }
 
-// PRE_SYNC: the block ran another tile just before (a persistent walk), so its
-// step B may still be reading shared memory: the first write of step A waits at
-// a barrier, placed after the first row pair's loads and collision so that the
-// wait overlaps them.
-template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY, bool KF, bool PRE_SYNC = false>
+template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY, bool KF>
 __device__ __forceinline__ void two_steps(const Params<float> &p, const typename Store<PREC>::T *__restrict__ src,
                                           const float *__restrict__ src_h, typename Store<PREC>::T *__restrict__ dst,
                                           float *__restrict__ dst_h, float *sm, int tx0, int ty0)
@@ -243,7 +239,6 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
             }
         }
         collide_pair<CONV, DIFF>(pw, f, A3, A35, A5, phi);
-        if (PRE_SYNC && hy0 == warp) __syncthreads();
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (INTERIOR || ok[h]) {

@@ -125,9 +125,7 @@ __device__ __forceinline__ void store_pair(const Params<float> &p, typename Stor
     }
 }
 
-// PRE_SYNC: as for two_steps, a barrier before the first shared-memory write
-// (after the first row's loads and collision) when the block ran a tile before.
-template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY, bool KF, bool PRE_SYNC = false>
+template <int PREC, int CONV, int DIFF, bool INTERIOR, int TY, bool KF>
 __device__ __forceinline__ void two_steps_pair(const Params<float> &p, const typename Store<PREC>::T *__restrict__ src,
                                                const float *__restrict__ src_h, typename Store<PREC>::T *__restrict__ dst,
                                                float *__restrict__ dst_h, float *sm, int X0, int Y0)
@@ -192,7 +190,6 @@ __device__ __forceinline__ void two_steps_pair(const Params<float> &p, const typ
             A5 = F2(__ldg(p.Afield + 2 * P + o0), __ldg(p.Afield + 2 * P + o1));
         }
         collide<F2, CONV, DIFF>(pw, g, A3, A35, A5, ph);
-        if (PRE_SYNC && hy == warp) __syncthreads();
         const int c = hy * kPRX + 2 * lane;
         if (INTERIOR || (ok[0] && ok[1])) {
 #pragma unroll
@@ -266,13 +263,13 @@ __device__ __forceinline__ void two_steps_pair(const Params<float> &p, const typ
 // The per-node path of the tiles along the domain's edges, kept out of line so
 // that its register needs (the wrap, the wall terms) do not raise those of the
 // interior tiles, which are all but a few per cent of a large grid.
-template <int PREC, int CONV, int DIFF, int TY, bool KF, bool PRE_SYNC = false>
+template <int PREC, int CONV, int DIFF, int TY, bool KF>
 __device__ __noinline__ void two_steps_pair_edge(const Params<float> &p, const typename Store<PREC>::T *__restrict__ src,
                                                  const float *__restrict__ src_h,
                                                  typename Store<PREC>::T *__restrict__ dst, float *__restrict__ dst_h,
                                                  float *sm, int X0, int Y0)
 {
-    two_steps_pair<PREC, CONV, DIFF, false, TY, KF, PRE_SYNC>(p, src, src_h, dst, dst_h, sm, X0, Y0);
+    two_steps_pair<PREC, CONV, DIFF, false, TY, KF>(p, src, src_h, dst, dst_h, sm, X0, Y0);
 }
 
 template <int PREC, int CONV, int DIFF, int TY, bool KF>

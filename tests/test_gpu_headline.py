@@ -1,11 +1,12 @@
 """Parity of the exact launches the benchmark times, at the benchmark's sizes.
 
 Every launch configuration the autotuner may choose for the 4096^2 Dirichlet
-workload (FP32 and BF16S) is compared with the FP64 oracle on the full grid,
-and the two-step tile kernels (both tile heights, the 30 x 30 tile being the
-tuned FP32 and BF16S choice) also over all 2000 steps on 512^2. The 1024^2
-Burgers workload is compared with the oracle at its full 5000 steps in every
-precision. Besides the relative L2 norm over the whole field, each comparison
+workload (FP32 and BF16S) is compared with the FP64 oracle on the full grid;
+the two-step tile kernels (node tiles of both heights and the 62 x 14 pair
+tiles the autotuner picks) also over all 2000 steps on 512^2, and the tuned
+launch over the full 4096^2 x 2000-step job on the corner block the oracle can
+compute exactly. The 1024^2 Burgers workload is compared with the oracle at its
+full 5000 steps in every precision. Besides the relative L2 norm over the whole field, each comparison
 checks the relative L2 norm over the two-node band along the walls (0.1 % of
 the nodes at 4096^2, where an error confined to the walls would vanish in the
 whole-field norm) and the largest error of any single node.
@@ -87,13 +88,13 @@ def test_every_tuner_candidate_on_the_full_grid(prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16s"])
-@pytest.mark.parametrize("block_rows", [4, 0])
-def test_two_step_tiles_all_steps(prec, block_rows):
-    """The two-step tile kernel with 30 x 30 (block_rows 4, the tuned launch) and
-    30 x 62 tiles over the workload's 2000 steps on 512^2."""
+@pytest.mark.parametrize("variant,block_rows", [(5, 4), (0, 4), (0, 0)])
+def test_two_step_tiles_all_steps(prec, variant, block_rows):
+    """The two-step tile kernels over the workload's 2000 steps on 512^2: 62 x 14
+    pair tiles (the tuned launch), 30 x 30 and 30 x 62 node tiles."""
     ref = oracle_aniso(512, 2000)
-    got = gpu_aniso(512, 2000, prec, dict(kernel_variant=0, block_rows=block_rows, steps_per_pass=2))
-    compare(got, ref, prec, f"512^2 x 2000 tile rows {block_rows}")
+    got = gpu_aniso(512, 2000, prec, dict(kernel_variant=variant, block_rows=block_rows, steps_per_pass=2))
+    compare(got, ref, prec, f"512^2 x 2000 v{variant} tile rows {block_rows}")
 
 
 def test_tuned_launch_is_a_tested_candidate():
@@ -139,3 +140,28 @@ def test_burgers_full_size_against_the_oracle(prec, spp, rows):
     else:
         assert full <= TOL[prec], full
         assert mx <= MAXTOL[prec], mx
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16s"])
+def test_full_run_corner_block_against_the_oracle(prec):
+    """The benchmark's exact job (4096^2, all 2000 steps, the autotuned launch)
+    compared with the oracle node by node on the 48 x 48 block at the corner
+    (0, 0). After N steps a node depends only on nodes within N of it, so the
+    oracle run on the 2048^2 corner sub-grid (its own walls at 2047.5 are at least
+    2001 steps away from the block) computes the block exactly as the full grid
+    does."""
+    p, coef, phi0 = aniso(4096)
+    steps, sub, m = p["steps"], 2048, 48
+    key = ("corner", sub, steps)
+    if key not in _CACHE:
+        sp = O.Spec(nx=sub, ny=sub, bc_x=1, bc_y=1, phi_wall=p["phi_wall"], s=W.s9(), **coef)
+        _CACHE[key] = O.run(sp, np.ascontiguousarray(phi0[:sub, :sub]), steps)[:m, :m]
+    ref = _CACHE[key]
+    cfg = tune.tune(4096, 4096, prec, bc=("abb", "abb"), conv=0, diff=2)
+    got = gpu_aniso(4096, steps, prec, cfg)[:m, :m]
+    d = got - ref
+    full = float(np.linalg.norm(d) / np.linalg.norm(ref))
+    mx = float(np.abs(d).max() / np.abs(ref).max())
+    print(f"[parity] 4096^2 x {steps} corner {m}x{m} {cfg_id(cfg)} {prec}: rel_l2={full:.3e} max_node={mx:.3e}")
+    assert full <= TOL[prec], full
+    assert mx <= MAXTOL[prec], mx
