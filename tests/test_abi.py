@@ -361,3 +361,16 @@ def test_error_messages_are_per_thread():
     t1.start(); t2.start(); t1.join(); t2.join()
     assert all(rc == C.LBM_EINVAL and b"nx and ny" in m for rc, m in results["a"])
     assert all(rc == C.LBM_EINVAL and b"steps_per_pass" in m for rc, m in results["b"])
+
+
+def test_probe_and_ensemble_tile_arguments_checked_on_the_host():
+    """Argument checks of lbm_probe_fp64 and lbm_ensemble_set_tiles /
+    lbm_ensemble_set_persistent run before any device work."""
+    L = C.lib()
+    n = ctypes.c_longlong(-1)
+    sink = ctypes.c_void_p(16)
+    for bad in ((0, 256, 10, sink), (8, 100, 10, sink), (8, 2048, 10, sink), (8, 256, 0, sink), (8, 256, 10, None)):
+        assert L.lbm_probe_fp64(*bad, ctypes.byref(n), None) == C.LBM_EINVAL, bad
+    assert n.value == -1
+    assert L.lbm_ensemble_set_tiles(None, 1) == C.LBM_EINVAL
+    assert L.lbm_ensemble_set_persistent(None, 2) == C.LBM_EINVAL

@@ -468,3 +468,33 @@ def test_pair_tiles_bit_identical_to_node_tiles(prec, block_rows):
     a, _ = run_gpu(prec, nx, ny, phi0, 20, Kfield=Kf, spp=2, variant=0, block_rows=4, **coef)
     b, _ = run_gpu(prec, nx, ny, phi0, 20, Kfield=Kf, spp=2, variant=5, block_rows=block_rows, **coef)
     assert np.array_equal(a, b)
+
+
+def test_fp64_probe_counts_and_rate():
+    """The FP64-pipe probe executes blocks x threads x iters x 8 FP64 thread
+    instructions, and its measured rate lies between a tenth of and twice the
+    rate of two FP64 instructions per SM per clock at the SM's maximum clock."""
+    import ctypes
+
+    from paper_1603_09577_gb300 import _lib as C
+    L = C.lib()
+    props = torch.cuda.get_device_properties(0)
+    blocks, threads, iters = props.multi_processor_count * 8, 256, 2048
+    sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    n = ctypes.c_longlong()
+    st = torch.cuda.current_stream()
+    run = lambda: C.check(L.lbm_probe_fp64(blocks, threads, iters, ctypes.c_void_p(sink.data_ptr()),  # noqa: E731
+                                           ctypes.byref(n), ctypes.c_void_p(st.cuda_stream)))
+    run()
+    torch.cuda.synchronize()
+    assert n.value == blocks * threads * iters * 8
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    run()
+    b.record(st)
+    torch.cuda.synchronize()
+    rate = n.value / (a.elapsed_time(b) / 1e3)
+    mhz = 2070.0
+    nominal = 2 * props.multi_processor_count * mhz * 1e6
+    assert 0.1 * nominal < rate < 2 * nominal, rate
+    assert float(sink.abs().sum()) == 0.0
