@@ -126,6 +126,13 @@ int lbm_ensemble_create(lbm_ensemble *out, int count, const int *nx, const int *
         I.nx = nx[i];
         I.ny = ny[i];
         I.A3 = (float)A3; I.A35 = (float)A35; I.A5 = (float)A5;
+        {
+            Params<float> sc;
+            set_scaled_rates<float>(c.s, A3, A35, A5, &sc);
+            I.se1 = sc.se1; I.se2 = sc.se2; I.sq4 = sc.sq4; I.sq6 = sc.sq6; I.sp7 = sc.sp7; I.sp8 = sc.sp8;
+            I.he1 = sc.he1; I.he2 = sc.he2; I.hq4 = sc.hq4; I.hq6 = sc.hq6;
+            I.a3s = sc.a3s; I.a35s = sc.a35s; I.a5s = sc.a5s; I.c3s = sc.c3s; I.c35s = sc.c35s; I.c5s = sc.c5s;
+        }
         I.ux = (float)c.u[0]; I.uy = (float)c.u[1];
         I.uxx = (float)(c.u[0] * c.u[0]); I.uxy = (float)(c.u[0] * c.u[1]); I.uyy = (float)(c.u[1] * c.u[1]);
         I.s1 = (float)c.s[1]; I.s2 = (float)c.s[2]; I.s4 = (float)c.s[4];

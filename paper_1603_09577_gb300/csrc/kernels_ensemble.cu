@@ -42,7 +42,7 @@ __device__ __forceinline__ void ens_tile(const EnsInst &I, int tx0, int ty0, int
         f[7] = __ldg(src + 7 * P + rp + xp);
         f[8] = __ldg(src + 8 * P + rp + xm);
         float phi;
-        collide<float, CONV, DIFF>(p, f, p.A3, p.A35, p.A5, phi);
+        collide<float, CONV, DIFF, false>(p, f, p.A3, p.A35, p.A5, phi);
 #pragma unroll
         for (int k = 0; k < 9; ++k) __stcs(dst + k * P + own, f[k]);
     }
@@ -80,7 +80,7 @@ k_ens_init(const EnsInst *__restrict__ inst, const int4 *__restrict__ tiles, int
             const float ph = in_prec == LBM_F64 ? (float)((const double *)phi)[i] : ((const float *)phi)[i];
             float f[9], phi_c;
             equilibrium<float, CONV, DIFF>(p, ph, f);
-            collide<float, CONV, DIFF>(p, f, p.A3, p.A35, p.A5, phi_c);
+            collide<float, CONV, DIFF, false>(p, f, p.A3, p.A35, p.A5, phi_c);
             const long long own = (long long)y * I.pitch + x;
 #pragma unroll
             for (int k = 0; k < 9; ++k) (parity ? I.pop[1] : I.pop[0])[k * I.plane + own] = f[k];

@@ -63,14 +63,12 @@ k_step(const Params<typename Store<PREC>::C> p, const typename Store<PREC>::T *_
         }
     }
 
-    C A3 = p.A3, A35 = p.A35, A5 = p.A5;
-    if (p.Afield) {
-        A3 = __ldg(p.Afield + own);
-        A35 = __ldg(p.Afield + P + own);
-        A5 = __ldg(p.Afield + 2 * P + own);
-    }
     C phi;
-    collide<C, CONV, DIFF>(p, f, A3, A35, A5, phi);
+    if (p.Afield)
+        collide<C, CONV, DIFF, true>(p, f, __ldg(p.Afield + own), __ldg(p.Afield + P + own), __ldg(p.Afield + 2 * P + own),
+                                     phi);
+    else
+        collide<C, CONV, DIFF, false>(p, f, p.A3, p.A35, p.A5, phi);
     S::store_cell(dst, dst_phi, P, own, f, phi);
 }
 

@@ -91,6 +91,9 @@ __device__ __forceinline__ Params<F2> widen(const Params<float> &p)
     w.s1 = p.s1; w.s2 = p.s2; w.s4 = p.s4; w.s6 = p.s6; w.s7 = p.s7; w.s8 = p.s8;
     w.h1 = p.h1; w.h2 = p.h2; w.h4 = p.h4; w.h6 = p.h6;
     w.A3 = p.A3; w.A35 = p.A35; w.A5 = p.A5;
+    w.se1 = p.se1; w.se2 = p.se2; w.sq4 = p.sq4; w.sq6 = p.sq6; w.sp7 = p.sp7; w.sp8 = p.sp8;
+    w.he1 = p.he1; w.he2 = p.he2; w.hq4 = p.hq4; w.hq6 = p.hq6;
+    w.a3s = p.a3s; w.a35s = p.a35s; w.a5s = p.a5s; w.c3s = p.c3s; w.c35s = p.c35s; w.c5s = p.c5s;
     w.ux = p.ux; w.uy = p.uy; w.uxx = p.uxx; w.uxy = p.uxy; w.uyy = p.uyy;
     w.r0 = p.r0; w.r1 = p.r1; w.half_r0 = p.half_r0; w.inv_den = p.inv_den; w.inv_post = p.inv_post;
     w.has_src = p.has_src;
@@ -98,8 +101,9 @@ __device__ __forceinline__ Params<F2> widen(const Params<float> &p)
     return w;
 }
 
-// collide two nodes with one packed instruction stream
-template <int CONV, int DIFF>
+// collide two nodes with one packed instruction stream; NODE_K: A3, A35, A5
+// are the nodes' blocks (per-node tensor field), else the constant block of pw
+template <int CONV, int DIFF, bool NODE_K>
 __device__ __forceinline__ void collide_pair(const Params<F2> &pw, float f[2][9], const float A3[2], const float A35[2],
                                              const float A5[2], float phi[2])
 {
@@ -107,7 +111,7 @@ __device__ __forceinline__ void collide_pair(const Params<F2> &pw, float f[2][9]
 #pragma unroll
     for (int k = 0; k < 9; ++k) g[k] = F2(f[0][k], f[1][k]);
     F2 ph;
-    collide<F2, CONV, DIFF>(pw, g, F2(A3[0], A3[1]), F2(A35[0], A35[1]), F2(A5[0], A5[1]), ph);
+    collide<F2, CONV, DIFF, NODE_K>(pw, g, F2(A3[0], A3[1]), F2(A35[0], A35[1]), F2(A5[0], A5[1]), ph);
 #pragma unroll
     for (int k = 0; k < 9; ++k) { f[0][k] = g[k].v.x; f[1][k] = g[k].v.y; }
     phi[0] = ph.v.x;
@@ -178,7 +182,7 @@ __device__ __forceinline__ void step2_B(const Params<float> &p, const Params<F2>
                 A5[h] = __ldg(p.Afield + 2 * P + own[h]);
             }
         }
-        collide_pair<CONV, DIFF>(pw, f, A3, A35, A5, phi);
+        collide_pair<CONV, DIFF, KF>(pw, f, A3, A35, A5, phi);
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             if (ok[h]) S::store_cell(dst, dst_h, P, own[h], f[h], phi[h]);
@@ -238,7 +242,7 @@ __device__ __forceinline__ void two_steps(const Params<float> &p, const typename
                 A5[h] = __ldg(p.Afield + 2 * P + own);
             }
         }
-        collide_pair<CONV, DIFF>(pw, f, A3, A35, A5, phi);
+        collide_pair<CONV, DIFF, KF>(pw, f, A3, A35, A5, phi);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (INTERIOR || ok[h]) {

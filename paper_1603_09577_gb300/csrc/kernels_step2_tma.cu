@@ -144,7 +144,7 @@ k_step2_tma(const Params<float> p, const __grid_constant__ CUtensorMap src_map, 
                 A5[h] = __ldg(p.Afield + 2 * P + own);
             }
         }
-        collide_pair<CONV, DIFF>(pw, f, A3, A35, A5, phi);
+        collide_pair<CONV, DIFF, KF>(pw, f, A3, A35, A5, phi);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = (hy0 + h * kWarps) * kRX + lane;

@@ -71,7 +71,7 @@ __device__ __forceinline__ void collide_pair_g(const Params<F2> &pw, float f[2][
     for (int k = 0; k < 9; ++k) g[k] = F2(f[0][k], f[1][k]);
     F2 ph;
     if (SA) collide_a<F2, CONV, DIFF>(pw, g, pw.A3, pw.A35, pw.A5, F2(prev[0], prev[1]), ph);
-    else collide<F2, CONV, DIFF>(pw, g, pw.A3, pw.A35, pw.A5, ph);
+    else collide<F2, CONV, DIFF, false>(pw, g, pw.A3, pw.A35, pw.A5, ph);
 #pragma unroll
     for (int k = 0; k < 9; ++k) { f[0][k] = g[k].v.x; f[1][k] = g[k].v.y; }
     phi[0] = ph.v.x;

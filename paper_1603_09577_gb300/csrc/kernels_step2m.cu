@@ -168,14 +168,12 @@ __device__ __forceinline__ void march(const Params<float> &p, const typename Sto
             });
         {
             const long long own = (long long)yrow * p.pitch + xc;
-            float A3 = p.A3, A35 = p.A35, A5 = p.A5;
-            if (p.Afield) {
-                A3 = __ldg(p.Afield + own);
-                A35 = __ldg(p.Afield + P + own);
-                A5 = __ldg(p.Afield + 2 * P + own);
-            }
             float phi;
-            collide<float, CONV, DIFF>(p, G, A3, A35, A5, phi);
+            if (p.Afield)
+                collide<float, CONV, DIFF, true>(p, G, __ldg(p.Afield + own), __ldg(p.Afield + P + own),
+                                                 __ldg(p.Afield + 2 * P + own), phi);
+            else
+                collide<float, CONV, DIFF, false>(p, G, p.A3, p.A35, p.A5, phi);
         }
         // ---- step B: row yb = ya - 1 at time n+2 ------------------------------
         const int yb = ya - 1;
@@ -196,14 +194,12 @@ __device__ __forceinline__ void march(const Params<float> &p, const typename Sto
                 LBM_CHK(xs, p.nx, p.err, kErrX);
                 LBM_CHK(ys, p.ny, p.err, kErrY);
                 const long long own = (long long)ys * p.pitch + xs;
-                float A3 = p.A3, A35 = p.A35, A5 = p.A5;
-                if (p.Afield) {
-                    A3 = __ldg(p.Afield + own);
-                    A35 = __ldg(p.Afield + P + own);
-                    A5 = __ldg(p.Afield + 2 * P + own);
-                }
                 float phi;
-                collide<float, CONV, DIFF>(p, f, A3, A35, A5, phi);
+                if (p.Afield)
+                    collide<float, CONV, DIFF, true>(p, f, __ldg(p.Afield + own), __ldg(p.Afield + P + own),
+                                                     __ldg(p.Afield + 2 * P + own), phi);
+                else
+                    collide<float, CONV, DIFF, false>(p, f, p.A3, p.A35, p.A5, phi);
                 S::store_cell(dst, dst_h, P, own, f, phi);
             }
         }

@@ -189,7 +189,7 @@ __device__ __forceinline__ void two_steps_pair(const Params<float> &p, const typ
             A35 = F2(__ldg(p.Afield + P + o0), __ldg(p.Afield + P + o1));
             A5 = F2(__ldg(p.Afield + 2 * P + o0), __ldg(p.Afield + 2 * P + o1));
         }
-        collide<F2, CONV, DIFF>(pw, g, A3, A35, A5, ph);
+        collide<F2, CONV, DIFF, KF>(pw, g, A3, A35, A5, ph);
         const int c = hy * kPRX + 2 * lane;
         if (INTERIOR || (ok[0] && ok[1])) {
 #pragma unroll
@@ -254,7 +254,7 @@ __device__ __forceinline__ void two_steps_pair(const Params<float> &p, const typ
                 A35 = F2(__ldg(p.Afield + P + own), __ldg(p.Afield + P + o1));
                 A5 = F2(__ldg(p.Afield + 2 * P + own), __ldg(p.Afield + 2 * P + o1));
             }
-            collide<F2, CONV, DIFF>(pw, g, A3, A35, A5, ph);
+            collide<F2, CONV, DIFF, KF>(pw, g, A3, A35, A5, ph);
             store_pair<PREC>(p, dst, dst_h, own, g, ph, both);
         }
     }

@@ -229,8 +229,13 @@ k_step_v4(const Params<float> p, const typename VecIO<PREC>::T *__restrict__ src
     }
 
     float phi[4];
+    if (p.Afield) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) collide<float, CONV, DIFF>(p, f[c], A3[c], A35[c], A5[c], phi[c]);
+        for (int c = 0; c < 4; ++c) collide<float, CONV, DIFF, true>(p, f[c], A3[c], A35[c], A5[c], phi[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) collide<float, CONV, DIFF, false>(p, f[c], A3[c], A35[c], A5[c], phi[c]);
+    }
     if (active) IO::store(dst, dst_h, P, r0 + L.x0, f, phi);
 }
 

@@ -149,6 +149,7 @@ Params<C> make_params(const lbm_solver *s)
     double A3 = 1, A35 = 0, A5 = 1;
     relax_block(c.K, &A3, &A35, &A5);
     p.A3 = (C)A3; p.A35 = (C)A35; p.A5 = (C)A5;
+    set_scaled_rates<C>(c.s, A3, A35, A5, &p);
     p.ux = (C)c.u[0]; p.uy = (C)c.u[1];
     p.uxx = (C)(c.u[0] * c.u[0]); p.uxy = (C)(c.u[0] * c.u[1]); p.uyy = (C)(c.u[1] * c.u[1]);
     p.r0 = (C)c.r0; p.r1 = (C)c.r1;

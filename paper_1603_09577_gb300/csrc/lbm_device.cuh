@@ -51,6 +51,13 @@ struct Params {
     C s1, s2, s4, s6, s7, s8;
     C h1, h2, h4, h6;       // 1 - s_i / 2
     C A3, A35, A5;          // constant relaxation block (Eq. 17, 26)
+    // the rates and the constant block divided by the squared norms of M0's rows
+    // (36, 36, 12, 12, 4, 4 and 6), the collision's factors of the source (Eq. 34)
+    // likewise: collide<..., false> applies them without rescaling every change
+    C se1, se2, sq4, sq6, sp7, sp8;   // s1/36, s2/36, s4/12, s6/12, s7/4, s8/4
+    C he1, he2, hq4, hq6;             // -2 h1/36, h2/36, -h4/12, -h6/12
+    C a3s, a35s, a5s;                 // A3/6, A35/6, A5/6
+    C c3s, c35s, c5s;                 // 1/6 - A3/12, -A35/12, 1/6 - A5/12
     C ux, uy, uxx, uxy, uyy;
     C r0, r1, half_r0, inv_den, inv_post;   // inv_den = 1/(1 - r1/2), inv_post = 1/(1 + r1/2)
     int has_src;
@@ -257,17 +264,13 @@ struct Mom {
     }
 };
 
-// f += M0^-1 dm, M0^-1 = M0^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+// f += M0^-1 dm with the changes already divided by the squared row norms of M0
+// (M0^-1 = M0^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)): r = drho/9,
+// ee = de/36, pp = deps/36, jxn = djx/6, qxn = dqx/12, jyn = djy/6, qyn = dqy/12,
+// pxxn = dpxx/4, pxyn = dpxy/4.
 template <class C>
-__device__ __forceinline__ void add_moment_change(C f[9], C drho, C de, C deps, C djx, C dqx, C djy, C dqy, C dpxx,
-                                                  C dpxy)
+__device__ __forceinline__ void add_scaled_change(C f[9], C r, C ee, C pp, C jxn, C qxn, C jyn, C qyn, C pxxn, C pxyn)
 {
-    const C r = drho * C(1.0 / 9.0);
-    const C ee = de * C(1.0 / 36.0);
-    const C pp = deps * C(1.0 / 36.0);
-    const C jxn = djx * C(1.0 / 6.0), qxn = dqx * C(1.0 / 12.0);
-    const C jyn = djy * C(1.0 / 6.0), qyn = dqy * C(1.0 / 12.0);
-    const C pxxn = dpxx * C(0.25), pxyn = dpxy * C(0.25);
     f[0] += mad(C(4), pp - ee, r);
     const C base_a = mad(C(-2), pp, r - ee);
     const C X1 = mad(C(-2), qxn, jxn), Y1 = mad(C(-2), qyn, jyn);
@@ -286,7 +289,18 @@ __device__ __forceinline__ void add_moment_change(C f[9], C drho, C de, C deps, 
     f[8] += bd_m + XmY;
 }
 
-template <class C, int CONV, int DIFF>
+// f += M0^-1 dm for the unscaled changes dm = m* - m.
+template <class C>
+__device__ __forceinline__ void add_moment_change(C f[9], C drho, C de, C deps, C djx, C dqx, C djy, C dqy, C dpxx,
+                                                  C dpxy)
+{
+    add_scaled_change<C>(f, drho * C(1.0 / 9.0), de * C(1.0 / 36.0), deps * C(1.0 / 36.0), djx * C(1.0 / 6.0),
+                         dqx * C(1.0 / 12.0), djy * C(1.0 / 6.0), dqy * C(1.0 / 12.0), dpxx * C(0.25), dpxy * C(0.25));
+}
+
+// NODE_K: A3, A35, A5 are the node's block (per-node tensor field); otherwise
+// the block is the constant one of p and its prescaled forms are used.
+template <class C, int CONV, int DIFF, bool NODE_K = true>
 __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35, C A5, C &phi_out)
 {
     const Mom<C> mo(f);
@@ -306,33 +320,48 @@ __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35,
 
     // relaxation (Eq. 17) plus (I - S/2) M0 R (Eq. 34), M0 R = (R, -2R, R,
     // Bt_x R, -Bt_x R, Bt_y R, -Bt_y R, 0, 0) with Bt = B' (Scheme B), written
-    // as the change dm = m* - m of every moment. Adding M0^-1 dm to f (instead
-    // of rebuilding f from m*) keeps rounding proportional to the departure
-    // from equilibrium; with R = 0 the mass change is exactly zero.
-    C de = -p.s1 * (e - e_eq);
-    C deps = -p.s2 * (eps - eps_eq);
-    C dqx = -p.s4 * (qx + q.Bx);
-    C dqy = -p.s6 * (qy + q.By);
-    const C dpxx = -p.s7 * (pxx - pxx_eq);
-    const C dpxy = -p.s8 * (pxy - q.Cbxy);
+    // as the change dm = m* - m of every moment, each already divided by the
+    // squared norm of its row of M0 (the rates carry the factor). Adding
+    // M0^-1 dm to f (instead of rebuilding f from m*) keeps rounding
+    // proportional to the departure from equilibrium; with R = 0 the mass
+    // change is exactly zero.
+    C ee = -p.se1 * (e - e_eq);
+    C pp = -p.se2 * (eps - eps_eq);
+    C qxn = -p.sq4 * (qx + q.Bx);
+    C qyn = -p.sq6 * (qy + q.By);
+    const C pxxn = -p.sp7 * (pxx - pxx_eq);
+    const C pxyn = -p.sp8 * (pxy - q.Cbxy);
+    C a3, a35, a5;
+    if constexpr (NODE_K) {
+        a3 = A3 * C(1.0 / 6.0); a35 = A35 * C(1.0 / 6.0); a5 = A5 * C(1.0 / 6.0);
+    } else {
+        a3 = p.a3s; a35 = p.a35s; a5 = p.a5s;
+    }
     const C d3 = jx - q.Bx, d5 = jy - q.By;
-    C djx = -mad(A3, d3, A35 * d5);
-    C djy = -mad(A35, d3, A5 * d5);
-    C drho = C(0);
+    C jxn = -mad(a3, d3, a35 * d5);
+    C jyn = -mad(a35, d3, a5 * d5);
+    C r = C(0);
     if (p.has_src) {
         const C R = mad(p.r1, phi, p.r0);
         const C sx = q.Bpx * R, sy = q.Bpy * R;
-        drho = R;                                // rho* = phi + R/2 = rho + R for every s0
-        de = mad(C(-2) * p.h1, R, de);
-        deps = mad(p.h2, R, deps);
-        dqx = mad(-p.h4, sx, dqx);
-        dqy = mad(-p.h6, sy, dqy);
-        djx += sx - C(0.5) * mad(A3, sx, A35 * sy);
-        djy += sy - C(0.5) * mad(A35, sx, A5 * sy);
+        r = R * C(1.0 / 9.0);                    // rho* = phi + R/2 = rho + R for every s0
+        ee = mad(p.he1, R, ee);
+        pp = mad(p.he2, R, pp);
+        qxn = mad(p.hq4, sx, qxn);
+        qyn = mad(p.hq6, sy, qyn);
+        // (I - A/2) B' R of the flux block, divided by 6
+        C c3, c35, c5;
+        if constexpr (NODE_K) {
+            c3 = mad(C(-0.5), a3, C(1.0 / 6.0)); c35 = C(-0.5) * a35; c5 = mad(C(-0.5), a5, C(1.0 / 6.0));
+        } else {
+            c3 = p.c3s; c35 = p.c35s; c5 = p.c5s;
+        }
+        jxn = mad(c3, sx, mad(c35, sy, jxn));
+        jyn = mad(c35, sx, mad(c5, sy, jyn));
     }
 
     // f* = f + M0^-1 dm
-    add_moment_change<C>(f, drho, de, deps, djx, dqx, djy, dqy, dpxx, dpxy);
+    add_scaled_change<C>(f, r, ee, pp, jxn, qxn, jyn, qyn, pxxn, pxyn);
 }
 
 // Equilibrium populations of Eq. 3 (used only at initialisation).

@@ -16,6 +16,8 @@ struct __align__(16) EnsInst {
     long long phi_off;      // offset of this instance in the packed phi arrays
     int nx, ny;
     float A3, A35, A5;
+    float se1, se2, sq4, sq6, sp7, sp8, he1, he2, hq4, hq6;   // prescaled collision factors (Params)
+    float a3s, a35s, a5s, c3s, c35s, c5s;
     float ux, uy, uxx, uxy, uyy;
     float s1, s2, s4, s6, s7, s8, h1, h2, h4, h6;
     int *err;               // checked builds: shared index-fault word
@@ -29,6 +31,9 @@ __device__ __forceinline__ Params<float> ens_params(const EnsInst &I)
     p.s1 = I.s1; p.s2 = I.s2; p.s4 = I.s4; p.s6 = I.s6; p.s7 = I.s7; p.s8 = I.s8;
     p.h1 = I.h1; p.h2 = I.h2; p.h4 = I.h4; p.h6 = I.h6;
     p.A3 = I.A3; p.A35 = I.A35; p.A5 = I.A5;
+    p.se1 = I.se1; p.se2 = I.se2; p.sq4 = I.sq4; p.sq6 = I.sq6; p.sp7 = I.sp7; p.sp8 = I.sp8;
+    p.he1 = I.he1; p.he2 = I.he2; p.hq4 = I.hq4; p.hq6 = I.hq6;
+    p.a3s = I.a3s; p.a35s = I.a35s; p.a5s = I.a5s; p.c3s = I.c3s; p.c35s = I.c35s; p.c5s = I.c5s;
     p.ux = I.ux; p.uy = I.uy; p.uxx = I.uxx; p.uxy = I.uxy; p.uyy = I.uyy;
     p.r0 = 0.f; p.r1 = 0.f; p.half_r0 = 0.f; p.inv_den = 1.f; p.inv_post = 1.f;
     p.has_src = 0;

@@ -80,6 +80,21 @@ int cuda_check(cudaError_t e, const char *what);
 template <class C>
 Params<C> make_params(const lbm_solver *s);
 
+// the prescaled rates, source factors and block of the collision (Params),
+// from the rates s0..s8 and the block A (computed in double, rounded once)
+template <class C>
+inline void set_scaled_rates(const double s[9], double A3, double A35, double A5, Params<C> *p)
+{
+    const double h1 = 1.0 - 0.5 * s[1], h2 = 1.0 - 0.5 * s[2], h4 = 1.0 - 0.5 * s[4], h6 = 1.0 - 0.5 * s[6];
+    p->se1 = (C)(s[1] / 36.0); p->se2 = (C)(s[2] / 36.0);
+    p->sq4 = (C)(s[4] / 12.0); p->sq6 = (C)(s[6] / 12.0);
+    p->sp7 = (C)(s[7] / 4.0); p->sp8 = (C)(s[8] / 4.0);
+    p->he1 = (C)(-2.0 * h1 / 36.0); p->he2 = (C)(h2 / 36.0);
+    p->hq4 = (C)(-h4 / 12.0); p->hq6 = (C)(-h6 / 12.0);
+    p->a3s = (C)(A3 / 6.0); p->a35s = (C)(A35 / 6.0); p->a5s = (C)(A5 / 6.0);
+    p->c3s = (C)(1.0 / 6.0 - A3 / 12.0); p->c35s = (C)(-A35 / 12.0); p->c5s = (C)(1.0 / 6.0 - A5 / 12.0);
+}
+
 cudaError_t launch_init(const lbm_solver *s, const void *phi, int in_prec, cudaStream_t st);
 cudaError_t launch_step(const lbm_solver *s, int src, cudaStream_t st);
 cudaError_t launch_step2(const lbm_solver *s, int src, cudaStream_t st);
