@@ -91,14 +91,16 @@ template <int PREC>
 static cudaError_t step_p(const lbm_solver *s, const void *src, const float *src_h, void *dst, float *dst_h,
                           cudaStream_t st)
 {
-    const int key = s->c.conv * 3 + s->c.diff;
-    switch (key) {
+    switch (step_key(s)) {
     case 0: return step_t<PREC, 0, 0>(s, src, src_h, dst, dst_h, st);
     case 1: return step_t<PREC, 0, 1>(s, src, src_h, dst, dst_h, st);
     case 2: return step_t<PREC, 0, 2>(s, src, src_h, dst, dst_h, st);
     case 3: return step_t<PREC, 1, 0>(s, src, src_h, dst, dst_h, st);
     case 4: return step_t<PREC, 1, 1>(s, src, src_h, dst, dst_h, st);
     case 5: return step_t<PREC, 1, 2>(s, src, src_h, dst, dst_h, st);
+    case 6: return step_t<PREC, kConvNone, 0>(s, src, src_h, dst, dst_h, st);
+    case 7: return step_t<PREC, kConvNone, 1>(s, src, src_h, dst, dst_h, st);
+    case 8: return step_t<PREC, kConvNone, 2>(s, src, src_h, dst, dst_h, st);
     }
     return cudaErrorInvalidValue;
 }

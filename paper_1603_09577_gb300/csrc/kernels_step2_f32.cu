@@ -8,13 +8,16 @@ namespace lbm {
 template <int PREC>
 static cudaError_t step2_p(const lbm_solver *s, int src, cudaStream_t st)
 {
-    switch (s->c.conv * 3 + s->c.diff) {
+    switch (step_key(s)) {
     case 0: return step2_t<PREC, 0, 0>(s, src, st);
     case 1: return step2_t<PREC, 0, 1>(s, src, st);
     case 2: return step2_t<PREC, 0, 2>(s, src, st);
     case 3: return step2_t<PREC, 1, 0>(s, src, st);
     case 4: return step2_t<PREC, 1, 1>(s, src, st);
     case 5: return step2_t<PREC, 1, 2>(s, src, st);
+    case 6: return step2_t<PREC, kConvNone, 0>(s, src, st);
+    case 7: return step2_t<PREC, kConvNone, 1>(s, src, st);
+    case 8: return step2_t<PREC, kConvNone, 2>(s, src, st);
     }
     return cudaErrorInvalidValue;
 }

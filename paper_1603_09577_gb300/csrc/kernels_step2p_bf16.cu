@@ -6,13 +6,16 @@ namespace lbm {
 
 cudaError_t launch_step2p_bf16s(const lbm_solver *s, int src, cudaStream_t st)
 {
-    switch (s->c.conv * 3 + s->c.diff) {
+    switch (step_key(s)) {
     case 0: return step2p_t<LBM_BF16S, 0, 0>(s, src, st);
     case 1: return step2p_t<LBM_BF16S, 0, 1>(s, src, st);
     case 2: return step2p_t<LBM_BF16S, 0, 2>(s, src, st);
     case 3: return step2p_t<LBM_BF16S, 1, 0>(s, src, st);
     case 4: return step2p_t<LBM_BF16S, 1, 1>(s, src, st);
     case 5: return step2p_t<LBM_BF16S, 1, 2>(s, src, st);
+    case 6: return step2p_t<LBM_BF16S, kConvNone, 0>(s, src, st);
+    case 7: return step2p_t<LBM_BF16S, kConvNone, 1>(s, src, st);
+    case 8: return step2p_t<LBM_BF16S, kConvNone, 2>(s, src, st);
     }
     return cudaErrorInvalidValue;
 }

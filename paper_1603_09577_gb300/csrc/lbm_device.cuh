@@ -163,8 +163,13 @@ template <> struct Store<LBM_BF16S> {
 // CONV codes: 0 linear, 1 Burgers, 2 power law (Eq. 49-50), with C of Eq. 7;
 // 3 Buckley-Leverett (Eq. 54) and 4, 5, 6 = families 0, 1, 2 in the C-free
 // variant of Remark III (C = 0 in the equilibrium, Eq. 38).
+// kConvNone: no convective flux, B = 0 and C = 0 (the linear family with
+// u = 0), dispatched at run time so that the collision skips the flux terms,
+// which would only add zero products
+constexpr int kConvNone = -1;
 template <int CONV> constexpr int conv_family() { return CONV >= 4 ? CONV - 4 : CONV; }
 template <int CONV> constexpr bool conv_cfree() { return CONV >= 3; }
+template <int CONV> constexpr bool has_flux() { return CONV != kConvNone; }
 
 template <class C, int CONV, int DIFF>
 struct Coef {
@@ -184,6 +189,9 @@ struct Coef {
             const C h = mad(C(-5) * q, q, C(1));
             Bx = p.ux * f; By = p.uy * f * h;
             Bpx = p.ux * fp; Bpy = p.uy * mad(fp, h, f * C(10) * q);
+            Cxx = C(0); Cxy = C(0); Cyy = C(0);
+        } else if constexpr (FAM == kConvNone) {
+            Bx = C(0); By = C(0); Bpx = C(0); Bpy = C(0);
             Cxx = C(0); Cxy = C(0); Cyy = C(0);
         } else if constexpr (FAM == 0) {
             Bx = p.ux * phi; By = p.uy * phi;
@@ -218,7 +226,11 @@ struct Coef {
             else if (DIFF == 1) g = mad(C(0.5) * phi, phi, phi);
             else g = mad(phi * phi * third, phi, phi);
             const C cg = g * third;              // d c_s^2 g with d = 1
-            Cbxx = Cxx + cg; Cbyy = Cyy + cg; Cbxy = Cxy;
+            if constexpr (FAM == kConvNone) {
+                Cbxx = cg; Cbyy = cg; Cbxy = C(0);
+            } else {
+                Cbxx = Cxx + cg; Cbyy = Cyy + cg; Cbxy = Cxy;
+            }
         }
     }
 };
@@ -313,10 +325,10 @@ __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35,
     const Coef<C, CONV, DIFF> q(p, phi);
 
     // equilibrium moments (Eq. 16 with c = 1)
+    constexpr bool FLUX = has_flux<CONV>();
     const C C2 = q.Cbxx + q.Cbyy;
     const C e_eq = mad(C(3), C2, C(-4) * phi);
     const C eps_eq = C(3) * (phi - C2);
-    const C pxx_eq = q.Cbxx - q.Cbyy;
 
     // relaxation (Eq. 17) plus (I - S/2) M0 R (Eq. 34), M0 R = (R, -2R, R,
     // Bt_x R, -Bt_x R, Bt_y R, -Bt_y R, 0, 0) with Bt = B' (Scheme B), written
@@ -325,39 +337,54 @@ __device__ __forceinline__ void collide(const Params<C> &p, C f[9], C A3, C A35,
     // M0^-1 dm to f (instead of rebuilding f from m*) keeps rounding
     // proportional to the departure from equilibrium; with R = 0 the mass
     // change is exactly zero.
+    // (without flux B = 0, C = 0: the q and p moments relax toward zero)
     C ee = -p.se1 * (e - e_eq);
     C pp = -p.se2 * (eps - eps_eq);
-    C qxn = -p.sq4 * (qx + q.Bx);
-    C qyn = -p.sq6 * (qy + q.By);
-    const C pxxn = -p.sp7 * (pxx - pxx_eq);
-    const C pxyn = -p.sp8 * (pxy - q.Cbxy);
+    C qxn, qyn, pxxn, pxyn;
+    if constexpr (FLUX) {
+        qxn = -p.sq4 * (qx + q.Bx);
+        qyn = -p.sq6 * (qy + q.By);
+        pxxn = -p.sp7 * (pxx - (q.Cbxx - q.Cbyy));
+        pxyn = -p.sp8 * (pxy - q.Cbxy);
+    } else {
+        qxn = -p.sq4 * qx;
+        qyn = -p.sq6 * qy;
+        pxxn = -p.sp7 * pxx;
+        pxyn = -p.sp8 * pxy;
+    }
     C a3, a35, a5;
     if constexpr (NODE_K) {
         a3 = A3 * C(1.0 / 6.0); a35 = A35 * C(1.0 / 6.0); a5 = A5 * C(1.0 / 6.0);
     } else {
         a3 = p.a3s; a35 = p.a35s; a5 = p.a5s;
     }
-    const C d3 = jx - q.Bx, d5 = jy - q.By;
+    C d3 = jx, d5 = jy;
+    if constexpr (FLUX) {
+        d3 = jx - q.Bx;
+        d5 = jy - q.By;
+    }
     C jxn = -mad(a3, d3, a35 * d5);
     C jyn = -mad(a35, d3, a5 * d5);
     C r = C(0);
     if (p.has_src) {
         const C R = mad(p.r1, phi, p.r0);
-        const C sx = q.Bpx * R, sy = q.Bpy * R;
         r = R * C(1.0 / 9.0);                    // rho* = phi + R/2 = rho + R for every s0
         ee = mad(p.he1, R, ee);
         pp = mad(p.he2, R, pp);
-        qxn = mad(p.hq4, sx, qxn);
-        qyn = mad(p.hq6, sy, qyn);
-        // (I - A/2) B' R of the flux block, divided by 6
-        C c3, c35, c5;
-        if constexpr (NODE_K) {
-            c3 = mad(C(-0.5), a3, C(1.0 / 6.0)); c35 = C(-0.5) * a35; c5 = mad(C(-0.5), a5, C(1.0 / 6.0));
-        } else {
-            c3 = p.c3s; c35 = p.c35s; c5 = p.c5s;
+        if constexpr (FLUX) {
+            const C sx = q.Bpx * R, sy = q.Bpy * R;
+            qxn = mad(p.hq4, sx, qxn);
+            qyn = mad(p.hq6, sy, qyn);
+            // (I - A/2) B' R of the flux block, divided by 6
+            C c3, c35, c5;
+            if constexpr (NODE_K) {
+                c3 = mad(C(-0.5), a3, C(1.0 / 6.0)); c35 = C(-0.5) * a35; c5 = mad(C(-0.5), a5, C(1.0 / 6.0));
+            } else {
+                c3 = p.c3s; c35 = p.c35s; c5 = p.c5s;
+            }
+            jxn = mad(c3, sx, mad(c35, sy, jxn));
+            jyn = mad(c35, sx, mad(c5, sy, jyn));
         }
-        jxn = mad(c3, sx, mad(c35, sy, jxn));
-        jyn = mad(c35, sx, mad(c5, sy, jyn));
     }
 
     // f* = f + M0^-1 dm

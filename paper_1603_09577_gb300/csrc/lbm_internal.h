@@ -80,6 +80,16 @@ int cuda_check(cudaError_t e, const char *what);
 template <class C>
 Params<C> make_params(const lbm_solver *s);
 
+// Family key of the step launchers: conv * 3 + diff, or 6 + diff for the linear
+// family without a flux (conv 0 with u = 0), which runs the collision without
+// the flux terms (kConvNone).
+inline int step_key(const lbm_solver *s)
+{
+    if (s->c.conv == 0 && s->c.u[0] == 0.0 && s->c.u[1] == 0.0 && s->c.diff >= 0 && s->c.diff <= 2)
+        return 6 + s->c.diff;
+    return s->c.conv * 3 + s->c.diff;
+}
+
 // the prescaled rates, source factors and block of the collision (Params),
 // from the rates s0..s8 and the block A (computed in double, rounded once)
 template <class C>
