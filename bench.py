@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=None,
-                    help="grid side of the headline workload (default 4096; smaller sides serve profiler captures)")
+                    help="grid side (default: 4096 for the headline workload, 256 for gaussian3d; smaller sides serve profiler captures)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-records (BF16S, FP64, adjoint, ensemble, 1024^2 Burgers) of the default run")
     ap.add_argument("--ens-count", type=int, default=256, help="instances of the ensemble workload")
@@ -646,7 +646,7 @@ def run_gaussian3d(args):
 
     from paper_1603_09577_gb300 import Solver3
     prec = args.prec
-    n = 256
+    n = args.nx or 256
     lbm_steps = args.lbm_steps or 500
     K, u, sig = (0.02, 0.006, 0.004, 0.015, 0.003, 0.01), (0.02, 0.01, -0.015), 16.0
     x = torch.arange(n, dtype=torch.float64, device="cuda")
@@ -700,7 +700,7 @@ def run_gaussian3d(args):
     out = {"metric": "MLUPS", "value": cells * lbm_steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-           "config": {"workload": f"gaussian3d_256: D3Q19, linear anisotropic CDE with a full 3x3 K, 256^3 periodic, "
+           "config": {"workload": f"gaussian3d_{n}: D3Q19, linear anisotropic CDE with a full 3x3 K, {n}^3 periodic, "
                                   f"{lbm_steps} steps per job", "nx": n, "ny": n, "nz": n,
                       "l2": "inputs larger than L2 (two population buffers of 0.67 to 2.5 GB each)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -36,9 +36,9 @@ k_step3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__r
     if (x >= p.nx || y >= p.ny) return;
     T f[19];
     pull3_node<PREC, CONV, DIFF, WALLS>(p, src, src_h, x, y, z, f);
-    T phi;
-    collide3<CONV, DIFF, T>(p, f, phi);
-    S::store(dst, dst_h, p.plane, ((long long)z * p.ny + y) * p.pitch + x, f, phi);
+    T phi, mass;
+    collide3<CONV, DIFF, T>(p, f, phi, mass);
+    S::store(dst, dst_h, p.plane, ((long long)z * p.ny + y) * p.pitch + x, f, phi, mass);
 }
 
 template <int PREC, int CONV, int DIFF>
@@ -61,10 +61,10 @@ k_init3(const Params3<typename St3<PREC>::C> p, const void *__restrict__ phi_in,
 #pragma unroll
         for (int k = 0; k < 19; ++k) f[k] = q.feq(k, phi0) - T(0.5) * q.source(k);
     }
-    T phi;
-    collide3<CONV, DIFF, T>(p, f, phi);
+    T phi, mass;
+    collide3<CONV, DIFF, T>(p, f, phi, mass);
     const long long own = ((long long)z * p.ny + y) * p.pitch + x;
-    S::store(dst, dst_h, p.plane, own, f, phi);
+    S::store(dst, dst_h, p.plane, own, f, phi, mass);
 }
 
 // phi(t_n) = (sum fbar* - r0/2) / (1 + r1/2) into an FP64 or FP32 field

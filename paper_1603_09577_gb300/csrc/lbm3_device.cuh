@@ -38,13 +38,15 @@ __host__ __device__ constexpr int opp3(int k) { return k == 0 ? 0 : (k % 2 ? k +
 
 // Storage of the 19 planes: FP64, FP32, or BF16 deviations g_k = f*_k - w_k phi
 // plus an FP32 shift plane h = M* - sum_k g_k (as for D2Q9: the stored node
-// sums to its post-collision mass up to FP32 rounding).
+// sums to its post-collision mass M* up to FP32 rounding). M* is the mass the
+// collision hands over, rho + R.
 template <int PREC> struct St3;
 template <> struct St3<LBM_F64> {
     using T = double;
     using C = double;
     __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
-    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C)
+    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C,
+                                                 C)
     {
 #pragma unroll
         for (int k = 0; k < 19; ++k) __stcs(f + k * P + i, v[k]);
@@ -54,7 +56,8 @@ template <> struct St3<LBM_F32> {
     using T = float;
     using C = float;
     __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
-    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C)
+    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C,
+                                                 C)
     {
 #pragma unroll
         for (int k = 0; k < 19; ++k) __stcs(f + k * P + i, v[k]);
@@ -68,13 +71,12 @@ template <> struct St3<LBM_BF16S> {
         return fmaf(w, __ldg(h + i), __bfloat162float(f[i]));
     }
     __device__ static __forceinline__ void store(T *__restrict__ f, float *__restrict__ h, long long P, long long i,
-                                                 const C v[19], C phi)
+                                                 const C v[19], C phi, C mass)
     {
-        C mass = C(0), gsum = C(0);
+        C gsum = C(0);
 #pragma unroll
         for (int k = 0; k < 19; ++k) {
             const T g = __float2bfloat16_rn(fmaf(-w3<float>(k), phi, v[k]));
-            mass += v[k];
             gsum += __bfloat162float(g);
             f[k * P + i] = g;
         }
@@ -141,8 +143,24 @@ struct Coef3 {
     }
 };
 
+// Eq. 6 pairs each velocity with its opposite (k odd, k + 1); the sign pattern
+// the pair form of collide3 is written out for
+static_assert(c3x(1) == 1 && c3y(3) == 1 && c3z(5) == 1, "axis velocities");
+static_assert(c3x(7) == 1 && c3y(7) == 1 && c3x(9) == 1 && c3y(9) == -1 && c3z(7) == 0 && c3z(9) == 0, "xy");
+static_assert(c3x(11) == 1 && c3z(11) == 1 && c3x(13) == -1 && c3z(13) == 1 && c3y(11) == 0 && c3y(13) == 0, "xz");
+static_assert(c3y(15) == 1 && c3z(15) == 1 && c3y(17) == 1 && c3z(17) == -1 && c3x(15) == 0 && c3x(17) == 0, "yz");
+
+// The collision f_k - s_e (f_k - feq_k) - c_k.G + (1 - s_e/2) R_k of the moment
+// reading, regrouped over each pair (k, opp(k)): with
+//   X   = s_e (phi - 9/2 trQ/3) + (1 - s_e/2) R          (even, weight-free)
+//   U_w = 3 w (s_e B + (1 - s_e/2) R B') - G             (odd, one per weight)
+// the update is f'_k = (1 - s_e) f_k + e_k + c_k.U_w, e_k = w X + (9/2) s_e w c_k Q c_k,
+// and f'_opp(k) takes the same even part with the odd part negated. c_k has
+// one or two non-zero components, so each pair costs a few additions: the
+// zero products of the per-direction form, which IEEE arithmetic keeps, are
+// gone. The same arithmetic as Eq. 3 and Eq. 9 in another order of rounding.
 template <int CONV, int DIFF, class C>
-__device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_out)
+__device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_out, C &mass_out)
 {
     C rho = C(0), jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
@@ -161,13 +179,38 @@ __device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_ou
     const C Gx = (p.G[0] * vx + p.G[1] * vy + p.G[2] * vz) * C(0.1);
     const C Gy = (p.G[1] * vx + p.G[3] * vy + p.G[4] * vz) * C(0.1);
     const C Gz = (p.G[2] * vx + p.G[4] * vy + p.G[5] * vz) * C(0.1);
-#pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        const C cG = C(c3x(k)) * Gx + C(c3y(k)) * Gy + C(c3z(k)) * Gz;
-        C v = f[k] - p.se * (f[k] - q.feq(k, phi)) - cG;
-        if (p.has_src) v += p.hse * q.source(k);
-        f[k] = v;
-    }
+
+    const C omse = C(1) - p.se;
+    const C hR = p.has_src ? p.hse * q.R : C(0);
+    const C X = p.se * (phi - C(4.5) * q.tr3) + hR;
+    C SBx = p.se * q.Bx, SBy = p.se * q.By, SBz = p.se * q.Bz;
+    if (p.has_src) { SBx += hR * q.bpx; SBy += hR * q.bpy; SBz += hR * q.bpz; }
+    // 3 w: 1/6 for the axis weight 1/18, 1/12 for the diagonal weight 1/36
+    const C Ux = C(1.0 / 6.0) * SBx - Gx, Uy = C(1.0 / 6.0) * SBy - Gy, Uz = C(1.0 / 6.0) * SBz - Gz;
+    const C Vx = C(1.0 / 12.0) * SBx - Gx, Vy = C(1.0 / 12.0) * SBy - Gy, Vz = C(1.0 / 12.0) * SBz - Gz;
+    // (9/2) s_e w: s_e / 4 for w = 1/18 (also 2 (9/2) s_e / 36), s_e / 8 for w = 1/36
+    const C q18 = C(0.25) * p.se, q36 = C(0.125) * p.se;
+    const C b18 = X * C(1.0 / 18.0), b36 = X * C(1.0 / 36.0);
+
+    // the odd parts cancel over each pair, sum_k e_k = X + (9/2) s_e c_s^2 trQ,
+    // and rho - phi = -R/2 (Eq. 35): the node hands over rho + R
+    mass_out = p.has_src ? rho + q.R : rho;
+    f[0] = omse * f[0] + X * C(1.0 / 3.0);
+    C e, o;
+    // axis pairs: c Q c = Q_aa
+    e = q18 * q.Qxx + b18; f[1] = omse * f[1] + (e + Ux); f[2] = omse * f[2] + (e - Ux);
+    e = q18 * q.Qyy + b18; f[3] = omse * f[3] + (e + Uy); f[4] = omse * f[4] + (e - Uy);
+    e = q18 * q.Qzz + b18; f[5] = omse * f[5] + (e + Uz); f[6] = omse * f[6] + (e - Uz);
+    // diagonal pairs in the plane (a, b): c Q c = Q_aa + Q_bb + 2 c_a c_b Q_ab
+    C S = q36 * (q.Qxx + q.Qyy) + b36, D = q18 * q.Qxy;
+    e = S + D; o = Vx + Vy; f[7] = omse * f[7] + (e + o); f[8] = omse * f[8] + (e - o);
+    e = S - D; o = Vx - Vy; f[9] = omse * f[9] + (e + o); f[10] = omse * f[10] + (e - o);
+    S = q36 * (q.Qxx + q.Qzz) + b36; D = q18 * q.Qxz;
+    e = S + D; o = Vx + Vz; f[11] = omse * f[11] + (e + o); f[12] = omse * f[12] + (e - o);
+    e = S - D; o = Vz - Vx; f[13] = omse * f[13] + (e + o); f[14] = omse * f[14] + (e - o);
+    S = q36 * (q.Qyy + q.Qzz) + b36; D = q18 * q.Qyz;
+    e = S + D; o = Vy + Vz; f[15] = omse * f[15] + (e + o); f[16] = omse * f[16] + (e - o);
+    e = S - D; o = Vy - Vz; f[17] = omse * f[17] + (e + o); f[18] = omse * f[18] + (e - o);
 }
 
 // Pull the 19 populations of node (x, y, z) with periodic wrap; WALLS: then
