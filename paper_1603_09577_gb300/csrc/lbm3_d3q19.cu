@@ -23,10 +23,9 @@
 
 namespace lbm {
 
-template <int PREC, int CONV, int DIFF, bool WALLS>
+template <int PREC, int CONV, int DIFF, bool WALLS, bool OFF32>
 __global__ void __launch_bounds__(256)
-k_step3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__restrict__ src,
-        const float *__restrict__ src_h, typename St3<PREC>::T *__restrict__ dst, float *__restrict__ dst_h)
+k_step3(const Params3<typename St3<PREC>::C> p, const Planes3<typename St3<PREC>::T> pl)
 {
     using S = St3<PREC>;
     using T = typename S::C;
@@ -34,20 +33,20 @@ k_step3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *__r
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
+    const unsigned own = ((unsigned)z * (unsigned)p.ny + (unsigned)y) * (unsigned)p.pitch + (unsigned)x;
     T f[19];
-    pull3_node<PREC, CONV, DIFF, WALLS>(p, src, src_h, x, y, z, f);
+    pull3_node<PREC, CONV, DIFF, WALLS, OFF32>(p, pl, x, y, z, own, f);
     T phi, mass;
     collide3<CONV, DIFF, T>(p, f, phi, mass);
-    S::store(dst, dst_h, p.plane, ((long long)z * p.ny + y) * p.pitch + x, f, phi, mass);
+    store3<PREC, OFF32>(pl, own, f, phi, mass);
 }
 
 template <int PREC, int CONV, int DIFF>
 __global__ void __launch_bounds__(256)
 k_init3(const Params3<typename St3<PREC>::C> p, const void *__restrict__ phi_in, int in_prec,
-        typename St3<PREC>::T *__restrict__ dst, float *__restrict__ dst_h)
+        const Planes3<typename St3<PREC>::T> pl)
 {
-    using S = St3<PREC>;
-    using T = typename S::C;
+    using T = typename St3<PREC>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -63,8 +62,8 @@ k_init3(const Params3<typename St3<PREC>::C> p, const void *__restrict__ phi_in,
     }
     T phi, mass;
     collide3<CONV, DIFF, T>(p, f, phi, mass);
-    const long long own = ((long long)z * p.ny + y) * p.pitch + x;
-    S::store(dst, dst_h, p.plane, own, f, phi, mass);
+    const unsigned own = ((unsigned)z * (unsigned)p.ny + (unsigned)y) * (unsigned)p.pitch + (unsigned)x;
+    store3<PREC, false>(pl, own, f, phi, mass);
 }
 
 // phi(t_n) = (sum fbar* - r0/2) / (1 + r1/2) into an FP64 or FP32 field
@@ -82,7 +81,7 @@ k_get_phi3(const Params3<typename St3<PREC>::C> p, const typename St3<PREC>::T *
     const long long own = ((long long)z * p.ny + y) * p.pitch + x;
     T s = T(0);
 #pragma unroll
-    for (int k = 0; k < 19; ++k) s += S::ld(f + k * p.plane, own, h, w3<T>(k));
+    for (int k = 0; k < 19; ++k) s += S::ld(f + k * p.plane, own, h, own, w3<T>(k));
     const double v = (double)((s - p.half_r0) * p.inv_post);
     const long long o = ((long long)z * p.ny + y) * p.nx + x;
     if (out_prec == LBM_F64) ((double *)out)[o] = v;
@@ -117,6 +116,9 @@ int check_desc3(const lbm3_desc *d)
     if (!d) return fail(LBM_EINVAL, "null lbm3_desc");
     if (d->nx < 2 || d->ny < 2 || d->nz < 2) return fail(LBM_EINVAL, "nx, ny and nz must be >= 2");
     if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) return fail(LBM_EINVAL, "grid larger than 2^31 nodes");
+    // node indices within a plane (rows padded to the pitch) are 32-bit
+    const long long pitch = ((long long)d->nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+    if (pitch * d->ny * d->nz > (1LL << 31) - 1) return fail(LBM_EINVAL, "population plane larger than 2^31 - 1 elements");
     if (d->prec != LBM_F64 && d->prec != LBM_F32 && d->prec != LBM_BF16S)
         return fail(LBM_EINVAL, "D3Q19 storage is LBM_F64, LBM_F32 or LBM_BF16S");
     const int b = d->block_rows;
@@ -176,8 +178,25 @@ Params3<T> params3(const lbm3_solver *s)
     p.pitch = s->pitch; p.plane = s->plane;
     p.se = (T)s->c.se;
     p.hse = (T)(1.0 - 0.5 * s->c.se);
-    for (int i = 0; i < 6; ++i) p.G[i] = (T)s->G[i];
-    p.ux = (T)s->c.u[0]; p.uy = (T)s->c.u[1]; p.uz = (T)s->c.u[2];
+    p.omse = (T)(1.0 - s->c.se);
+    p.q18 = (T)(0.25 * s->c.se);
+    p.q36 = (T)(0.125 * s->c.se);
+    for (int i = 0; i < 6; ++i) p.G[i] = (T)(0.1 * s->G[i]);
+    const double *u = s->c.u;
+    p.ux = (T)u[0]; p.uy = (T)u[1]; p.uz = (T)u[2];
+    p.uu[0] = (T)(u[0] * u[0]); p.uu[1] = (T)(u[0] * u[1]); p.uu[2] = (T)(u[0] * u[2]);
+    p.uu[3] = (T)(u[1] * u[1]); p.uu[4] = (T)(u[1] * u[2]); p.uu[5] = (T)(u[2] * u[2]);
+    p.u2_3 = (T)((u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / 3.0);
+    const double q18 = 0.25 * s->c.se, q36 = 0.125 * s->c.se;
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};   // planes xy, xz, yz
+    for (int a = 0; a < 3; ++a) {
+        p.u6[a] = (T)(u[a] / 6.0);
+        p.u12[a] = (T)(u[a] / 12.0);
+        p.ea[a] = (T)(q18 * u[a] * u[a]);
+        const double sq = u[pa[a]] * u[pa[a]] + u[pb[a]] * u[pb[a]], cr = u[pa[a]] * u[pb[a]];
+        p.ep[a] = (T)(q36 * sq + q18 * cr);
+        p.em[a] = (T)(q36 * sq - q18 * cr);
+    }
     p.r0 = (T)s->c.r0; p.r1 = (T)s->c.r1;
     p.half_r0 = (T)(0.5 * s->c.r0);
     p.inv_den = (T)(1.0 / (1.0 - 0.5 * s->c.r1));
@@ -197,19 +216,43 @@ dim3 grid3(const lbm3_solver *s)
     return dim3((s->d.nx + 31) / 32, (s->d.ny + b.y - 1) / b.y, s->d.nz);
 }
 
+template <class T>
+Planes3<T> planes3(const lbm3_solver *s)
+{
+    Planes3<T> pl;
+    const T *src = (const T *)s->pop[s->cur];
+    T *dst = (T *)s->pop[s->cur ^ 1];
+    for (int k = 0; k < 19; ++k) {
+        pl.src[k] = src + k * s->plane;
+        pl.dst[k] = dst + k * s->plane;
+        pl.poff[k] = (unsigned)(k * s->plane);   // used only when 19 * plane < 2^32
+    }
+    pl.src0 = src;
+    pl.dst0 = dst;
+    pl.src_h = s->hpl[s->cur];
+    pl.dst_h = s->hpl[s->cur ^ 1];
+    return pl;
+}
+
 template <int PREC, int CONV, int DIFF>
 cudaError_t launch3_t(const lbm3_solver *s, const void *phi0, int in_prec, cudaStream_t st)
 {
     using T = typename St3<PREC>::T;
     const auto p = params3<typename St3<PREC>::C>(s);
-    if (phi0)
-        k_init3<PREC, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, phi0, in_prec, (T *)s->pop[s->cur], s->hpl[s->cur]);
-    else if (p.any_abb)
-        k_step3<PREC, CONV, DIFF, true><<<grid3(s), block3(s), 0, st>>>(p, (const T *)s->pop[s->cur], s->hpl[s->cur],
-                                                                        (T *)s->pop[s->cur ^ 1], s->hpl[s->cur ^ 1]);
-    else
-        k_step3<PREC, CONV, DIFF, false><<<grid3(s), block3(s), 0, st>>>(p, (const T *)s->pop[s->cur], s->hpl[s->cur],
-                                                                         (T *)s->pop[s->cur ^ 1], s->hpl[s->cur ^ 1]);
+    if (phi0) {
+        // the initial state goes to the current buffer
+        Planes3<T> pl = planes3<T>(s);
+        for (int k = 0; k < 19; ++k) pl.dst[k] = (T *)pl.src[k];
+        pl.dst_h = s->hpl[s->cur];
+        k_init3<PREC, CONV, DIFF><<<grid3(s), block3(s), 0, st>>>(p, phi0, in_prec, pl);
+    } else {
+        const bool off32 = 19 * s->plane < (1LL << 32);
+        const Planes3<T> pl = planes3<T>(s);
+        if (p.any_abb && off32) k_step3<PREC, CONV, DIFF, true, true><<<grid3(s), block3(s), 0, st>>>(p, pl);
+        else if (p.any_abb) k_step3<PREC, CONV, DIFF, true, false><<<grid3(s), block3(s), 0, st>>>(p, pl);
+        else if (off32) k_step3<PREC, CONV, DIFF, false, true><<<grid3(s), block3(s), 0, st>>>(p, pl);
+        else k_step3<PREC, CONV, DIFF, false, false><<<grid3(s), block3(s), 0, st>>>(p, pl);
+    }
     return cudaGetLastError();
 }
 

@@ -39,58 +39,85 @@ __host__ __device__ constexpr int opp3(int k) { return k == 0 ? 0 : (k % 2 ? k +
 // Storage of the 19 planes: FP64, FP32, or BF16 deviations g_k = f*_k - w_k phi
 // plus an FP32 shift plane h = M* - sum_k g_k (as for D2Q9: the stored node
 // sums to its post-collision mass M* up to FP32 rounding). M* is the mass the
-// collision hands over, rho + R.
+// collision hands over, rho + R. A node is addressed by its index within a
+// plane (at most 2^31 - 1, checked when the solver is created).
 template <int PREC> struct St3;
 template <> struct St3<LBM_F64> {
     using T = double;
     using C = double;
-    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
-    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C,
-                                                 C)
-    {
-#pragma unroll
-        for (int k = 0; k < 19; ++k) __stcs(f + k * P + i, v[k]);
-    }
+    template <class I>
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, I i, const float *, I, C) { return __ldg(f + i); }
 };
 template <> struct St3<LBM_F32> {
     using T = float;
     using C = float;
-    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *, C) { return __ldg(f + i); }
-    __device__ static __forceinline__ void store(T *__restrict__ f, float *, long long P, long long i, const C v[19], C,
-                                                 C)
-    {
-#pragma unroll
-        for (int k = 0; k < 19; ++k) __stcs(f + k * P + i, v[k]);
-    }
+    template <class I>
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, I i, const float *, I, C) { return __ldg(f + i); }
 };
 template <> struct St3<LBM_BF16S> {
     using T = __nv_bfloat16;
     using C = float;
-    __device__ static __forceinline__ C ld(const T *__restrict__ f, long long i, const float *__restrict__ h, C w)
+    template <class I>
+    __device__ static __forceinline__ C ld(const T *__restrict__ f, I i, const float *__restrict__ h, I hi, C w)
     {
-        return fmaf(w, __ldg(h + i), __bfloat162float(f[i]));
-    }
-    __device__ static __forceinline__ void store(T *__restrict__ f, float *__restrict__ h, long long P, long long i,
-                                                 const C v[19], C phi, C mass)
-    {
-        C gsum = C(0);
-#pragma unroll
-        for (int k = 0; k < 19; ++k) {
-            const T g = __float2bfloat16_rn(fmaf(-w3<float>(k), phi, v[k]));
-            gsum += __bfloat162float(g);
-            f[k * P + i] = g;
-        }
-        h[i] = mass - gsum;
+        return fmaf(w, __ldg(h + hi), __bfloat162float(f[i]));
     }
 };
+
+// The two population buffers of one launch (and the BF16S shift planes), a
+// kernel argument. Plane k is reached either through its own 64-bit pointer
+// (any lattice) or, when 19 planes hold fewer than 2^32 elements, through the
+// buffer's pointer and the 32-bit offset k * plane, so that a pull costs 32-bit
+// index additions and one address computation from one base register.
+template <class T>
+struct Planes3 {
+    const T *src[19];
+    T *dst[19];
+    const T *src0;
+    T *dst0;
+    unsigned poff[19];
+    const float *src_h;
+    float *dst_h;
+};
+
+// store node i's post-collision populations v (and the BF16S shift)
+template <int PREC, bool OFF32>
+__device__ __forceinline__ void store3(const Planes3<typename St3<PREC>::T> &pl, unsigned i,
+                                       const typename St3<PREC>::C v[19], typename St3<PREC>::C phi,
+                                       typename St3<PREC>::C mass)
+{
+    if constexpr (PREC == LBM_BF16S) {
+        float gsum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+            const __nv_bfloat16 g = __float2bfloat16_rn(fmaf(-w3<float>(k), phi, v[k]));
+            gsum += __bfloat162float(g);
+            if constexpr (OFF32) pl.dst0[i + pl.poff[k]] = g;
+            else pl.dst[k][i] = g;
+        }
+        pl.dst_h[i] = mass - gsum;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+            if constexpr (OFF32) __stcs(pl.dst0 + (i + pl.poff[k]), v[k]);
+            else __stcs(pl.dst[k] + i, v[k]);
+        }
+    }
+}
 
 template <class C>
 struct Params3 {
     int nx, ny, nz;
     long long pitch, plane;          // plane = pitch * ny * nz
     C se, hse;                       // s_e and 1 - s_e/2
-    C G[6];                          // A - s_e I: xx, xy, xz, yy, yz, zz
+    C omse, q18, q36;                // 1 - s_e, s_e/4, s_e/8 (the pair form of the collision)
+    C G[6];                          // (A - s_e I)/10 (Pi_j = c c^T / 10): xx, xy, xz, yy, yz, zz
     C ux, uy, uz;
+    C uu[6];                         // u u^T: xx, xy, xz, yy, yz, zz
+    C u2_3;                          // |u|^2 / 3
+    C u6[3], u12[3];                 // u/6, u/12
+    C ea[3];                         // s_e/4 u_a u_a (a = x, y, z)
+    C ep[3], em[3];                  // s_e/8 (u_a u_a + u_b u_b) +/- s_e/4 u_a u_b, (a, b) = xy, xz, yz
     C r0, r1, half_r0, inv_den, inv_post;
     int has_src;
     int abb[3];                      // 1: anti-bounce-back walls on axis x, y, z
@@ -117,14 +144,14 @@ struct Coef3 {
             bpx = p.ux * phi; bpy = p.uy * phi; bpz = p.uz * phi;
             cphi = phi * phi * phi * C(1.0 / 3.0);
         }
-        C g;
-        if (DIFF == 0) g = phi;
-        else if (DIFF == 1) g = phi + C(0.5) * phi * phi;
-        else g = phi + phi * phi * phi * C(1.0 / 3.0);
-        const C diag = (g - phi) * C(1.0 / 3.0);
-        Qxx = p.ux * p.ux * cphi + diag; Qyy = p.uy * p.uy * cphi + diag; Qzz = p.uz * p.uz * cphi + diag;
-        Qxy = p.ux * p.uy * cphi; Qxz = p.ux * p.uz * cphi; Qyz = p.uy * p.uz * cphi;
-        tr3 = (Qxx + Qyy + Qzz) * C(1.0 / 3.0);
+        Qxx = p.uu[0] * cphi; Qyy = p.uu[3] * cphi; Qzz = p.uu[5] * cphi;
+        Qxy = p.uu[1] * cphi; Qxz = p.uu[2] * cphi; Qyz = p.uu[4] * cphi;
+        tr3 = p.u2_3 * cphi;
+        // the isotropic part c_s^2 (g - phi) I (none for g = phi)
+        if constexpr (DIFF != 0) {
+            const C diag = DIFF == 1 ? C(0.5) * phi * phi * C(1.0 / 3.0) : phi * phi * phi * C(1.0 / 9.0);
+            Qxx += diag; Qyy += diag; Qzz += diag; tr3 += diag;
+        }
         R = p.has_src ? p.r1 * phi + p.r0 : C(0);
     }
     // feq_k = w_k [phi + 3 c.B + 4.5 (c Q c - trQ/3)] (Eq. 3)
@@ -162,65 +189,77 @@ static_assert(c3y(15) == 1 && c3z(15) == 1 && c3y(17) == 1 && c3z(17) == -1 && c
 template <int CONV, int DIFF, class C>
 __device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_out, C &mass_out)
 {
-    C rho = C(0), jx = C(0), jy = C(0), jz = C(0);
+    // rho and j from the pair sums and differences d_m = f_(2m+1) - f_(2m+2)
+    C rho = f[0], d[9];
 #pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        rho += f[k];
-        if (c3x(k)) jx += C(c3x(k)) * f[k];
-        if (c3y(k)) jy += C(c3y(k)) * f[k];
-        if (c3z(k)) jz += C(c3z(k)) * f[k];
+    for (int m = 0; m < 9; ++m) {
+        rho += f[2 * m + 1] + f[2 * m + 2];
+        d[m] = f[2 * m + 1] - f[2 * m + 2];
     }
+    const C jx = (d[0] + d[3]) + (d[4] + d[5]) - d[6];
+    const C jy = (d[1] + d[3]) - d[4] + (d[7] + d[8]);
+    const C jz = (d[2] + d[5]) + (d[6] + d[7]) - d[8];
     const C phi = (rho + p.half_r0) * p.inv_den;                 // Eq. 35
     phi_out = phi;
-    const Coef3<CONV, DIFF, C> q(p, phi);
-    // G = (A - s_e I) [(j - B) + B' R / 2]
-    const C vx = (jx - q.Bx) + C(0.5) * q.bpx * q.R, vy = (jy - q.By) + C(0.5) * q.bpy * q.R;
-    const C vz = (jz - q.Bz) + C(0.5) * q.bpz * q.R;
-    const C Gx = (p.G[0] * vx + p.G[1] * vy + p.G[2] * vz) * C(0.1);
-    const C Gy = (p.G[1] * vx + p.G[3] * vy + p.G[4] * vz) * C(0.1);
-    const C Gz = (p.G[2] * vx + p.G[4] * vy + p.G[5] * vz) * C(0.1);
-
-    const C omse = C(1) - p.se;
-    const C hR = p.has_src ? p.hse * q.R : C(0);
-    const C X = p.se * (phi - C(4.5) * q.tr3) + hR;
-    C SBx = p.se * q.Bx, SBy = p.se * q.By, SBz = p.se * q.Bz;
-    if (p.has_src) { SBx += hR * q.bpx; SBy += hR * q.bpy; SBz += hR * q.bpz; }
-    // 3 w: 1/6 for the axis weight 1/18, 1/12 for the diagonal weight 1/36
-    const C Ux = C(1.0 / 6.0) * SBx - Gx, Uy = C(1.0 / 6.0) * SBy - Gy, Uz = C(1.0 / 6.0) * SBz - Gz;
-    const C Vx = C(1.0 / 12.0) * SBx - Gx, Vy = C(1.0 / 12.0) * SBy - Gy, Vz = C(1.0 / 12.0) * SBz - Gz;
-    // (9/2) s_e w: s_e / 4 for w = 1/18 (also 2 (9/2) s_e / 36), s_e / 8 for w = 1/36
-    const C q18 = C(0.25) * p.se, q36 = C(0.125) * p.se;
-    const C b18 = X * C(1.0 / 18.0), b36 = X * C(1.0 / 36.0);
+    // Eq. 7 families: B = u beta, B' = u beta', C = u u cphi with beta = phi,
+    // beta' = 1, cphi = phi (conv 0) or beta = phi^2/2, beta' = phi, cphi = phi^3/3
+    C beta, cphi;
+    if constexpr (CONV == 0) { beta = phi; cphi = phi; }
+    else { beta = C(0.5) * phi * phi; cphi = phi * phi * phi * C(1.0 / 3.0); }
+    const C R = p.has_src ? p.r1 * phi + p.r0 : C(0);
+    const C hR = p.has_src ? p.hse * R : C(0);
+    // G = (A - s_e I)/10 [(j - B) + B' R / 2], (j - B) + B' R/2 = j - u sv
+    C sv = beta, t = p.se * beta;              // s_e B + (1 - s_e/2) R B' = u t
+    if (p.has_src) {
+        if constexpr (CONV == 0) { sv -= C(0.5) * R; t += hR; }
+        else { sv -= C(0.5) * R * phi; t += hR * phi; }
+    }
+    const C vx = jx - p.ux * sv, vy = jy - p.uy * sv, vz = jz - p.uz * sv;
+    const C Gx = p.G[0] * vx + p.G[1] * vy + p.G[2] * vz;
+    const C Gy = p.G[1] * vx + p.G[3] * vy + p.G[4] * vz;
+    const C Gz = p.G[2] * vx + p.G[4] * vy + p.G[5] * vz;
+    // U_w = 3 w u t - G: u/6 for the axis weight 1/18, u/12 for the diagonal weight 1/36
+    const C Ux = p.u6[0] * t - Gx, Uy = p.u6[1] * t - Gy, Uz = p.u6[2] * t - Gz;
+    const C Vx = p.u12[0] * t - Gx, Vy = p.u12[1] * t - Gy, Vz = p.u12[2] * t - Gz;
+    // Q = u u cphi + c_s^2 (g - phi) I; trQ/3 = |u|^2 cphi/3 + the isotropic part
+    C tr3 = p.u2_3 * cphi, iso = C(0);
+    if constexpr (DIFF == 1) iso = C(0.5) * phi * phi * C(1.0 / 3.0);
+    else if constexpr (DIFF == 2) iso = phi * phi * phi * C(1.0 / 9.0);
+    if constexpr (DIFF != 0) tr3 += iso;
+    const C X = p.se * (phi - C(4.5) * tr3) + hR;
+    // even parts: w X + (9/2) s_e w c Q c. Axis: (s_e/4) Q_aa + X/18; diagonal in
+    // (a, b): (s_e/8)(Q_aa + Q_bb) +/- (s_e/4) Q_ab + X/36. The products of u u
+    // with these factors come from the host (ea, ep, em); the isotropic part
+    // adds (s_e/4) iso to both
+    C b18 = X * C(1.0 / 18.0), b36 = X * C(1.0 / 36.0);
+    if constexpr (DIFF != 0) { b18 += p.q18 * iso; b36 += p.q18 * iso; }
+    const C omse = p.omse;
 
     // the odd parts cancel over each pair, sum_k e_k = X + (9/2) s_e c_s^2 trQ,
     // and rho - phi = -R/2 (Eq. 35): the node hands over rho + R
-    mass_out = p.has_src ? rho + q.R : rho;
+    mass_out = p.has_src ? rho + R : rho;
     f[0] = omse * f[0] + X * C(1.0 / 3.0);
     C e, o;
-    // axis pairs: c Q c = Q_aa
-    e = q18 * q.Qxx + b18; f[1] = omse * f[1] + (e + Ux); f[2] = omse * f[2] + (e - Ux);
-    e = q18 * q.Qyy + b18; f[3] = omse * f[3] + (e + Uy); f[4] = omse * f[4] + (e - Uy);
-    e = q18 * q.Qzz + b18; f[5] = omse * f[5] + (e + Uz); f[6] = omse * f[6] + (e - Uz);
-    // diagonal pairs in the plane (a, b): c Q c = Q_aa + Q_bb + 2 c_a c_b Q_ab
-    C S = q36 * (q.Qxx + q.Qyy) + b36, D = q18 * q.Qxy;
-    e = S + D; o = Vx + Vy; f[7] = omse * f[7] + (e + o); f[8] = omse * f[8] + (e - o);
-    e = S - D; o = Vx - Vy; f[9] = omse * f[9] + (e + o); f[10] = omse * f[10] + (e - o);
-    S = q36 * (q.Qxx + q.Qzz) + b36; D = q18 * q.Qxz;
-    e = S + D; o = Vx + Vz; f[11] = omse * f[11] + (e + o); f[12] = omse * f[12] + (e - o);
-    e = S - D; o = Vz - Vx; f[13] = omse * f[13] + (e + o); f[14] = omse * f[14] + (e - o);
-    S = q36 * (q.Qyy + q.Qzz) + b36; D = q18 * q.Qyz;
-    e = S + D; o = Vy + Vz; f[15] = omse * f[15] + (e + o); f[16] = omse * f[16] + (e - o);
-    e = S - D; o = Vy - Vz; f[17] = omse * f[17] + (e + o); f[18] = omse * f[18] + (e - o);
+    e = p.ea[0] * cphi + b18; f[1] = omse * f[1] + (e + Ux); f[2] = omse * f[2] + (e - Ux);
+    e = p.ea[1] * cphi + b18; f[3] = omse * f[3] + (e + Uy); f[4] = omse * f[4] + (e - Uy);
+    e = p.ea[2] * cphi + b18; f[5] = omse * f[5] + (e + Uz); f[6] = omse * f[6] + (e - Uz);
+    e = p.ep[0] * cphi + b36; o = Vx + Vy; f[7] = omse * f[7] + (e + o); f[8] = omse * f[8] + (e - o);
+    e = p.em[0] * cphi + b36; o = Vx - Vy; f[9] = omse * f[9] + (e + o); f[10] = omse * f[10] + (e - o);
+    e = p.ep[1] * cphi + b36; o = Vx + Vz; f[11] = omse * f[11] + (e + o); f[12] = omse * f[12] + (e - o);
+    e = p.em[1] * cphi + b36; o = Vz - Vx; f[13] = omse * f[13] + (e + o); f[14] = omse * f[14] + (e - o);
+    e = p.ep[2] * cphi + b36; o = Vy + Vz; f[15] = omse * f[15] + (e + o); f[16] = omse * f[16] + (e - o);
+    e = p.em[2] * cphi + b36; o = Vy - Vz; f[17] = omse * f[17] + (e + o); f[18] = omse * f[18] + (e - o);
 }
 
 // Pull the 19 populations of node (x, y, z) with periodic wrap; WALLS: then
 // replace the links that cross an anti-bounce-back wall (at wall nodes only).
-// A lattice without walls compiles without the wall code.
-template <int PREC, int CONV, int DIFF, bool WALLS>
+// A lattice without walls compiles without the wall code. The source of
+// direction k is the node's own index plus the offsets of its neighbour on
+// each axis, in 32-bit arithmetic (a plane holds fewer than 2^31 elements).
+template <int PREC, int CONV, int DIFF, bool WALLS, bool OFF32>
 __device__ __forceinline__ void pull3_node(const Params3<typename St3<PREC>::C> &p,
-                                           const typename St3<PREC>::T *__restrict__ src,
-                                           const float *__restrict__ src_h, int x, int y, int z,
-                                           typename St3<PREC>::C f[19])
+                                           const Planes3<typename St3<PREC>::T> &pl, int x, int y, int z,
+                                           unsigned own, typename St3<PREC>::C f[19])
 {
     using S = St3<PREC>;
     using T = typename S::C;
@@ -233,17 +272,22 @@ __device__ __forceinline__ void pull3_node(const Params3<typename St3<PREC>::C> 
     LBM_CHK(yp, p.ny, p.err, kErrY);
     LBM_CHK(zm, p.nz, p.err, kErrIndex);
     LBM_CHK(zp, p.nz, p.err, kErrIndex);
-    const long long P = p.plane;
+    // offsets of the neighbours x -/+ 1, y -/+ 1, z -/+ 1 (wrapped)
+    const int rowp = (int)p.pitch, slab = (int)p.pitch * p.ny;
+    const unsigned ox[2] = {(unsigned)(xm - x), (unsigned)(xp - x)};
+    const unsigned oy[2] = {(unsigned)((ym - y) * rowp), (unsigned)((yp - y) * rowp)};
+    const unsigned oz[2] = {(unsigned)((zm - z) * slab), (unsigned)((zp - z) * slab)};
 #pragma unroll
     for (int k = 0; k < 19; ++k) {
         // source node x - c_k
-        const int xs = c3x(k) > 0 ? xm : (c3x(k) < 0 ? xp : x);
-        const int ys = c3y(k) > 0 ? ym : (c3y(k) < 0 ? yp : y);
-        const int zs = c3z(k) > 0 ? zm : (c3z(k) < 0 ? zp : z);
-        f[k] = S::ld(src + k * P, ((long long)zs * p.ny + ys) * p.pitch + xs, src_h, w3<T>(k));
+        unsigned i = own;
+        if (c3x(k)) i += ox[c3x(k) > 0 ? 0 : 1];
+        if (c3y(k)) i += oy[c3y(k) > 0 ? 0 : 1];
+        if (c3z(k)) i += oz[c3z(k) > 0 ? 0 : 1];
+        if constexpr (OFF32) f[k] = S::ld(pl.src0, i + pl.poff[k], pl.src_h, i, w3<T>(k));
+        else f[k] = S::ld(pl.src[k], i, pl.src_h, i, w3<T>(k));
     }
     if constexpr (WALLS) {
-        const long long own = ((long long)z * p.ny + y) * p.pitch + x;
         const bool wall = (p.abb[0] && (x == 0 || x == p.nx - 1)) || (p.abb[1] && (y == 0 || y == p.ny - 1)) ||
                           (p.abb[2] && (z == 0 || z == p.nz - 1));
         if (wall) {
@@ -262,7 +306,9 @@ __device__ __forceinline__ void pull3_node(const Params3<typename St3<PREC>::C> 
                 if (cnt) {
                     const T phiw = cnt == 1 ? tot : tot / T(cnt);
                     const Coef3<CONV, DIFF, T> q(p, phiw);
-                    f[k] = q.feq(k, phiw) + q.feq(opp3(k), phiw) - S::ld(src + opp3(k) * P, own, src_h, w3<T>(opp3(k)));
+                    const T back = OFF32 ? S::ld(pl.src0, own + pl.poff[opp3(k)], pl.src_h, own, w3<T>(opp3(k)))
+                                         : S::ld(pl.src[opp3(k)], own, pl.src_h, own, w3<T>(opp3(k)));
+                    f[k] = q.feq(k, phiw) + q.feq(opp3(k), phiw) - back;
                 }
             }
         }

@@ -154,3 +154,28 @@ def test_d3q19_channel_slip_on_the_gpu():
     exact = yb * (2 - yb) + (se * s3 - 8 * (se + s3) + 16) / (12 * N ** 2 * se * s3)
     assert np.abs(phi - exact[None, :, None]).max() < 1e-12
 
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16s"])
+@pytest.mark.parametrize("walls", [False, True], ids=["periodic", "y-walls"])
+def test_d3q19_large_plane_addressing(prec, walls):
+    """A lattice whose 19 planes hold more than 2^32 elements (2 x 54 x 65472 with
+    rows padded to 64 elements: 19 x 226,271,232) is addressed through 64-bit
+    plane pointers, a small one through 32-bit offsets from the buffer. A field of
+    period 64 along z stays periodic, so the large lattice must repeat the
+    64-layer lattice's result bit for bit in every period."""
+    nx, ny, nz, per = 2, 54, 65472, 64
+    coef = dict(conv=1, u=(0.03, -0.05, 0.04), diff=2, K=(0.02, 0.003, -0.002, 0.03, 0.004, 0.025), se=1.1,
+                r0=0.001, r1=-0.02)
+    bc = ("periodic", "abb", "periodic") if walls else ("periodic",) * 3
+    extra = dict(bc=bc, phi_wall=(0.0, 0.0, 0.3, 0.7, 0.0, 0.0)) if walls else {}
+    rng = np.random.default_rng(64)
+    small0 = torch.from_numpy(rng.uniform(0.2, 0.8, (per, ny, nx))).cuda()
+    s = Solver3(nx, ny, per, prec=prec, **extra).set_coeffs(**coef).set_phi(small0).step(7)
+    want = s.phi()
+    del s
+    big = Solver3(nx, ny, nz, prec=prec, **extra).set_coeffs(**coef).set_phi(small0.repeat(nz // per, 1, 1)).step(7)
+    got = big.phi().view(nz // per, per, ny, nx)
+    del big
+    torch.cuda.empty_cache()
+    assert torch.equal(got, want.expand_as(got))
