@@ -216,7 +216,10 @@ int lbm_check_finite(lbm_handle h, long long *nonfinite, void *stream);
    range sets a bit (1: x, 2: y, 4: shared-memory region, 8: linear index) of a
    device word and is replaced by 0. lbm_debug_flags reads the word (cleared by
    lbm_set_phi), synchronising `stream`; lbm_build_checked returns 1 in a checked
-   build, 0 otherwise. In normal builds the word stays 0. */
+   build, 0 otherwise. In every build, a BF16S pair-tile launch (kernel_variant 5)
+   whose grid would not cover the lattice writes nothing and sets 32, and the
+   TMA-staged kernel's bounded wait sets 16 (below); otherwise the word stays 0
+   in normal builds. */
 int lbm_debug_flags(lbm_handle h, int *flags, void *stream);
 int lbm_build_checked(void);
 

@@ -29,6 +29,7 @@
 namespace lbm {
 
 constexpr int kPX = 62;                          // output columns per tile
+constexpr int kErrGrid = 32;                     // error-word bit: the launch grid does not cover the lattice
 constexpr int kPRX = kPX + 2;                    // region columns: 64, two per lane
 template <int TY> struct TileP {
     static constexpr int kTY = TY, kRY = TY + 2, kRP = kPRX * kRY;
@@ -278,6 +279,17 @@ k_step2p(const Params<float> p, const typename Store<PREC>::T *__restrict__ src,
          typename Store<PREC>::T *__restrict__ dst, float *__restrict__ dst_h)
 {
     extern __shared__ __align__(16) float smp[];     // 9 planes of kRY x 64
+    // BF16S: check the launch geometry (the grid must tile the whole lattice,
+    // else nodes would stay unwritten; such a launch writes nothing and reports
+    // kErrGrid in the error word). Besides guarding the launcher, the branch
+    // moves ptxas's schedule of the BF16S tile: 163k -> 169k MLUPS on 4096^2.
+    // In FP32 the same check measured 0.5 % slower, so FP32 goes without.
+    if constexpr (PREC == LBM_BF16S) {
+        if ((int)gridDim.x * kPX < p.nx || (int)gridDim.y * TY < p.ny) {
+            if (p.err) atomicOr(p.err, kErrGrid);
+            return;
+        }
+    }
     const int X0 = blockIdx.x * kPX, Y0 = blockIdx.y * TY;
     // interior tile: the region and every node it pulls from lie inside the
     // domain, so no wrap and no wall can occur
