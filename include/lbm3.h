@@ -65,7 +65,12 @@ typedef struct {
     double r0, r1;          /* source R = r0 + r1 phi (|r1| < 2)                  */
 } lbm3_coeffs;
 
-/* Bytes of device workspace for this description. */
+/* Bytes of device workspace for this description. LBM_EINVAL for a lattice of
+   more than 2^31 nodes, or whose population plane (rows padded to a multiple of
+   64 elements) holds more than 2^31 - 1 elements: the kernels index a node
+   within a plane in 32-bit arithmetic. A lattice whose 19 planes hold 2^32
+   elements or more is addressed through one 64-bit pointer per plane, a
+   smaller one through 32-bit offsets from one base pointer (same results). */
 int lbm3_workspace_size(const lbm3_desc *desc, size_t *bytes);
 /* Create a solver on a caller-owned device workspace (kept until destroy). */
 int lbm3_create(lbm3_handle *h, const lbm3_desc *desc, void *dev_workspace, size_t bytes);

@@ -240,6 +240,10 @@ def test_d3q19_descriptions_and_coefficients():
     assert L.lbm3_workspace_size(ctypes.byref(d3(prec=C.LBM_BF16S)), ctypes.byref(n)) == 0
     for bad in (dict(nz=1), dict(prec=7), dict(block_rows=3)):
         assert L.lbm3_workspace_size(ctypes.byref(d3(**bad)), ctypes.byref(n)) == C.LBM_EINVAL
+    # node indices within a plane are 32-bit: rows padded to 64 elements, so
+    # 2 x 1024 x 32768 nodes (2^26) make a plane of 2^31 elements, one too many
+    assert L.lbm3_workspace_size(ctypes.byref(d3(nx=2, ny=1024, nz=32767)), ctypes.byref(n)) == 0
+    assert L.lbm3_workspace_size(ctypes.byref(d3(nx=2, ny=1024, nz=32768)), ctypes.byref(n)) == C.LBM_EINVAL
     walled = d3()
     walled.bc[:] = [1, 0, 1]
     walled.phi_wall[:] = [0.1, 0.2, 0.0, 0.0, 0.5, 0.6]
