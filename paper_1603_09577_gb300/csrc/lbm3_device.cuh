@@ -87,15 +87,28 @@ __device__ __forceinline__ void store3(const Planes3<typename St3<PREC>::T> &pl,
                                        typename St3<PREC>::C mass)
 {
     if constexpr (PREC == LBM_BF16S) {
-        float gsum = 0.f;
+        // g_k = f*_k - w_k phi; the two directions of a pair share w_k, so their
+        // shifts, bf16 roundings and sums go two at a time
+        const __nv_bfloat16 g0 = __float2bfloat16_rn(fmaf(-w3<float>(0), phi, v[0]));
+        if constexpr (OFF32) pl.dst0[i] = g0;
+        else pl.dst[0][i] = g0;
+        const F2 s18(-w3<float>(1) * phi), s36(-w3<float>(7) * phi);
+        F2 gsum(0.f);
 #pragma unroll
-        for (int k = 0; k < 19; ++k) {
-            const __nv_bfloat16 g = __float2bfloat16_rn(fmaf(-w3<float>(k), phi, v[k]));
-            gsum += __bfloat162float(g);
-            if constexpr (OFF32) pl.dst0[i + pl.poff[k]] = g;
-            else pl.dst[k][i] = g;
+        for (int m = 0; m < 9; ++m) {
+            const int k = 2 * m + 1;
+            const F2 gp = F2(v[k], v[k + 1]) + (k < 7 ? s18 : s36);
+            const __nv_bfloat162 g = __floats2bfloat162_rn(gp.v.x, gp.v.y);
+            gsum = gsum + F2(__low2float(g), __high2float(g));
+            if constexpr (OFF32) {
+                pl.dst0[i + pl.poff[k]] = __low2bfloat16(g);
+                pl.dst0[i + pl.poff[k + 1]] = __high2bfloat16(g);
+            } else {
+                pl.dst[k][i] = __low2bfloat16(g);
+                pl.dst[k + 1][i] = __high2bfloat16(g);
+            }
         }
-        pl.dst_h[i] = mass - gsum;
+        pl.dst_h[i] = mass - (__bfloat162float(g0) + (gsum.v.x + gsum.v.y));
     } else {
 #pragma unroll
         for (int k = 0; k < 19; ++k) {
@@ -170,6 +183,21 @@ struct Coef3 {
     }
 };
 
+// f'_k = (1 - s_e) f_k + (e + o) and f'_opp = (1 - s_e) f_opp + (e - o): in FP32
+// the two as one packed FP32x2 multiply-add
+template <class C>
+__device__ __forceinline__ void pair_update(C &a, C &b, C omse, C e, C o)
+{
+    if constexpr (sizeof(C) == 4) {
+        const F2 r = mad(F2(a, b), F2(omse), F2(e + o, e - o));
+        a = r.v.x;
+        b = r.v.y;
+    } else {
+        a = omse * a + (e + o);
+        b = omse * b + (e - o);
+    }
+}
+
 // Eq. 6 pairs each velocity with its opposite (k odd, k + 1); the sign pattern
 // the pair form of collide3 is written out for
 static_assert(c3x(1) == 1 && c3y(3) == 1 && c3z(5) == 1, "axis velocities");
@@ -190,12 +218,20 @@ template <int CONV, int DIFF, class C>
 __device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_out, C &mass_out)
 {
     // rho and j from the pair sums and differences d_m = f_(2m+1) - f_(2m+2)
-    C rho = f[0], d[9];
+    C rho, d[9];
+    if constexpr (sizeof(C) == 4) {
+        // FP32: the pair sums accumulate as one packed FP32x2 sum
+        F2 s2 = F2(f[1], f[2]);
 #pragma unroll
-    for (int m = 0; m < 9; ++m) {
-        rho += f[2 * m + 1] + f[2 * m + 2];
-        d[m] = f[2 * m + 1] - f[2 * m + 2];
+        for (int m = 1; m < 9; ++m) s2 = s2 + F2(f[2 * m + 1], f[2 * m + 2]);
+        rho = f[0] + (s2.v.x + s2.v.y);
+    } else {
+        rho = f[0];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) rho += f[2 * m + 1] + f[2 * m + 2];
     }
+#pragma unroll
+    for (int m = 0; m < 9; ++m) d[m] = f[2 * m + 1] - f[2 * m + 2];
     const C jx = (d[0] + d[3]) + (d[4] + d[5]) - d[6];
     const C jy = (d[1] + d[3]) - d[4] + (d[7] + d[8]);
     const C jz = (d[2] + d[5]) + (d[6] + d[7]) - d[8];
@@ -239,16 +275,15 @@ __device__ __forceinline__ void collide3(const Params3<C> &p, C f[19], C &phi_ou
     // and rho - phi = -R/2 (Eq. 35): the node hands over rho + R
     mass_out = p.has_src ? rho + R : rho;
     f[0] = omse * f[0] + X * C(1.0 / 3.0);
-    C e, o;
-    e = p.ea[0] * cphi + b18; f[1] = omse * f[1] + (e + Ux); f[2] = omse * f[2] + (e - Ux);
-    e = p.ea[1] * cphi + b18; f[3] = omse * f[3] + (e + Uy); f[4] = omse * f[4] + (e - Uy);
-    e = p.ea[2] * cphi + b18; f[5] = omse * f[5] + (e + Uz); f[6] = omse * f[6] + (e - Uz);
-    e = p.ep[0] * cphi + b36; o = Vx + Vy; f[7] = omse * f[7] + (e + o); f[8] = omse * f[8] + (e - o);
-    e = p.em[0] * cphi + b36; o = Vx - Vy; f[9] = omse * f[9] + (e + o); f[10] = omse * f[10] + (e - o);
-    e = p.ep[1] * cphi + b36; o = Vx + Vz; f[11] = omse * f[11] + (e + o); f[12] = omse * f[12] + (e - o);
-    e = p.em[1] * cphi + b36; o = Vz - Vx; f[13] = omse * f[13] + (e + o); f[14] = omse * f[14] + (e - o);
-    e = p.ep[2] * cphi + b36; o = Vy + Vz; f[15] = omse * f[15] + (e + o); f[16] = omse * f[16] + (e - o);
-    e = p.em[2] * cphi + b36; o = Vy - Vz; f[17] = omse * f[17] + (e + o); f[18] = omse * f[18] + (e - o);
+    pair_update(f[1], f[2], omse, p.ea[0] * cphi + b18, Ux);
+    pair_update(f[3], f[4], omse, p.ea[1] * cphi + b18, Uy);
+    pair_update(f[5], f[6], omse, p.ea[2] * cphi + b18, Uz);
+    pair_update(f[7], f[8], omse, p.ep[0] * cphi + b36, Vx + Vy);
+    pair_update(f[9], f[10], omse, p.em[0] * cphi + b36, Vx - Vy);
+    pair_update(f[11], f[12], omse, p.ep[1] * cphi + b36, Vx + Vz);
+    pair_update(f[13], f[14], omse, p.em[1] * cphi + b36, Vz - Vx);
+    pair_update(f[15], f[16], omse, p.ep[2] * cphi + b36, Vy + Vz);
+    pair_update(f[17], f[18], omse, p.em[2] * cphi + b36, Vy - Vz);
 }
 
 // Pull the 19 populations of node (x, y, z) with periodic wrap; WALLS: then
@@ -277,15 +312,36 @@ __device__ __forceinline__ void pull3_node(const Params3<typename St3<PREC>::C> 
     const unsigned ox[2] = {(unsigned)(xm - x), (unsigned)(xp - x)};
     const unsigned oy[2] = {(unsigned)((ym - y) * rowp), (unsigned)((yp - y) * rowp)};
     const unsigned oz[2] = {(unsigned)((zm - z) * slab), (unsigned)((zp - z) * slab)};
-#pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        // source node x - c_k
+    // source node x - c_k of direction k
+    auto src_of = [&](int k) {
         unsigned i = own;
         if (c3x(k)) i += ox[c3x(k) > 0 ? 0 : 1];
         if (c3y(k)) i += oy[c3y(k) > 0 ? 0 : 1];
         if (c3z(k)) i += oz[c3z(k) > 0 ? 0 : 1];
-        if constexpr (OFF32) f[k] = S::ld(pl.src0, i + pl.poff[k], pl.src_h, i, w3<T>(k));
-        else f[k] = S::ld(pl.src[k], i, pl.src_h, i, w3<T>(k));
+        return i;
+    };
+    if constexpr (PREC == LBM_BF16S) {
+        // f_k = g_k + w_k h at the source; a pair (k, opp(k)) shares w_k, so the
+        // two reconstructions are one packed multiply-add
+        f[0] = OFF32 ? S::ld(pl.src0, own, pl.src_h, own, w3<T>(0)) : S::ld(pl.src[0], own, pl.src_h, own, w3<T>(0));
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int k = 2 * m + 1;
+            const unsigned ia = src_of(k), ib = src_of(k + 1);
+            const __nv_bfloat16 ga = OFF32 ? pl.src0[ia + pl.poff[k]] : pl.src[k][ia];
+            const __nv_bfloat16 gb = OFF32 ? pl.src0[ib + pl.poff[k + 1]] : pl.src[k + 1][ib];
+            const F2 r = mad(F2(__ldg(pl.src_h + ia), __ldg(pl.src_h + ib)), F2(w3<float>(k)),
+                             F2(__bfloat162float(ga), __bfloat162float(gb)));
+            f[k] = r.v.x;
+            f[k + 1] = r.v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+            const unsigned i = src_of(k);
+            if constexpr (OFF32) f[k] = S::ld(pl.src0, i + pl.poff[k], pl.src_h, i, w3<T>(k));
+            else f[k] = S::ld(pl.src[k], i, pl.src_h, i, w3<T>(k));
+        }
     }
     if constexpr (WALLS) {
         const bool wall = (p.abb[0] && (x == 0 || x == p.nx - 1)) || (p.abb[1] && (y == 0 || y == p.ny - 1)) ||
